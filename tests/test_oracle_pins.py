@@ -1,0 +1,551 @@
+"""Pins for the CPU oracle: each oracle function checked against something
+other than itself -- library routines, closed forms, hand-derived values,
+brute force on tiny inputs, and the paper's theorems as invariants.
+
+Nothing here needs a GPU.
+"""
+import itertools
+import json
+import math
+import os
+from collections import Counter
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy.optimize import linear_sum_assignment, linprog
+from scipy.sparse import csr_matrix
+from scipy.sparse.csgraph import shortest_path
+
+from paper_2110_14734_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+SQ2 = math.sqrt(2.0)
+
+
+# --------------------------------------------------------------------------
+# exact integer roots and rounded-up costs (vs Python's math.isqrt)
+# --------------------------------------------------------------------------
+
+def test_isqrt_and_ceil_sqrt_vs_math_isqrt(orc):
+    rng = np.random.default_rng(1)
+    vals = [0, 1, 2, 3, 4, 15, 16, 17, 2**32 - 1, 2**32, 2**62, 2**63 - 1, 2**64 - 1,
+            (2**32 - 1) ** 2, (2**32 - 1) ** 2 - 1]
+    vals += [int(v) for v in rng.integers(0, 2**63, 300, dtype=np.uint64)]
+    vals += [int(v) ** 2 + d for v in rng.integers(0, 2**31, 100) for d in (-1, 0, 1) if int(v) ** 2 + d >= 0]
+    for v in vals:
+        r = math.isqrt(v)
+        assert orc.isqrt(v) == r
+        assert orc.ceil_sqrt(v) == (r if r * r == v else r + 1)
+
+
+def test_costs_are_rounded_up_l2_and_diagonal_distance(orc):
+    rng = np.random.default_rng(2)
+    for _ in range(500):
+        x1, y1, x2, y2 = (int(v) for v in rng.integers(-(2**29), 2**29, 4))
+        d2 = (x1 - x2) ** 2 + (y1 - y2) ** 2
+        c = orc.cost(x1, y1, x2, y2)
+        assert (c - 1) ** 2 < d2 <= c * c or (d2 == 0 and c == 0)
+        t = abs(y1 - x1)
+        cd = orc.cdiag(x1, y1)
+        # smallest integer >= t / sqrt(2)
+        assert Fraction(cd) ** 2 * 2 >= t * t and (cd == 0 or Fraction(cd - 1) ** 2 * 2 < t * t)
+    assert orc.cdiag(0, 2) == 2 and orc.cdiag(0, 3) == 3 and orc.cdiag(0, 4) == 3 and orc.cdiag(5, 5) == 0
+
+
+# --------------------------------------------------------------------------
+# quantisation
+# --------------------------------------------------------------------------
+
+def test_quantize_known_values(orc):
+    q = 2.0 ** -20
+    A = np.array([[0.5, 0.25], [1 / 256, 0.0], [2.5 * q, 0.75], [3.5 * q, 0.75], [0.3, 0.3]], np.float32)
+    X, Y = orc.quantize(A, "f32", 20)
+    # 0.5 -> 2^19; half-quantum values round to even; the diagonal point is dropped
+    assert list(X) == [2**19, 4096, 2, 4] and list(Y) == [2**18, 0, 3 * 2**18, 3 * 2**18]
+    U = np.array([[255, 0], [3, 3], [0, 7]], np.uint8)
+    X, Y = orc.quantize(U, "u8", 12)
+    assert list(X) == [255 * 4096, 0] and list(Y) == [0, 7 * 4096]
+    with pytest.raises(ValueError):
+        orc.quantize(np.array([[np.nan, 1.0]], np.float32), "f32", 20)
+    with pytest.raises(ValueError):
+        orc.quantize(np.array([[600.0, 1.0]], np.float32), "f32", 20)  # 600 * 2^20 >= 2^29
+
+
+# --------------------------------------------------------------------------
+# 0-condensation (vs collections.Counter)
+# --------------------------------------------------------------------------
+
+def test_condense0_matches_counter(orc):
+    rng = np.random.default_rng(3)
+    X = rng.integers(-5, 5, 2000).astype(np.int32)
+    Y = rng.integers(-5, 5, 2000).astype(np.int32)
+    UX, UY, cnt = orc.condense0(X, Y)
+    ref = Counter(zip(X.tolist(), Y.tolist()))
+    assert dict(zip(zip(UX.tolist(), UY.tolist()), cnt.tolist())) == ref
+    assert list(zip(UX.tolist(), UY.tolist())) == sorted(ref)
+
+
+# --------------------------------------------------------------------------
+# RWMD (Algorithm 1 + the diagonal arc)
+# --------------------------------------------------------------------------
+
+def _brute_rwmd(P, Q):
+    def side(P, Q):
+        L = 0
+        for x, y, c in zip(*P):
+            best = math.isqrt(((abs(int(y) - int(x)) ** 2) + 1) // 2)
+            if 2 * best * best < (int(y) - int(x)) ** 2:
+                best += 1
+            for u, v in zip(Q[0], Q[1]):
+                d2 = (int(x) - int(u)) ** 2 + (int(y) - int(v)) ** 2
+                r = math.isqrt(d2)
+                r += r * r < d2
+                best = min(best, r)
+            L += int(c) * best
+        return L
+    return side(P, Q), side(Q, P)
+
+
+def test_rwmd_brute_force_and_closed_forms(orc):
+    rng = np.random.default_rng(4)
+    for trial in range(5):
+        P = (rng.integers(0, 200, 30).astype(np.int32), rng.integers(0, 200, 30).astype(np.int32),
+             rng.integers(1, 4, 30).astype(np.int64))
+        Q = (rng.integers(0, 200, 25).astype(np.int32), rng.integers(0, 200, 25).astype(np.int32),
+             rng.integers(1, 4, 25).astype(np.int64))
+        LA, LB, L = orc.rwmd(P, Q)
+        assert (LA, LB) == _brute_rwmd(P, Q) and L == max(LA, LB)
+    # B empty: L_A is the closed-form sum of diagonal distances, L_B = 0
+    LA, LB, L = orc.rwmd(P, (np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int64)))
+    assert LA == sum(int(c) * orc.cdiag(int(x), int(y)) for x, y, c in zip(*P)) and LB == 0
+    # identical diagrams: every node has a partner at distance 0
+    assert orc.rwmd(P, P) == (0, 0, 0)
+
+
+def test_rwmd_needs_the_diagonal_option(orc):
+    # A = {(0, 0.1)}, B = {(100, 100.1)} in units of 0.1: RWMD without the
+    # diagonal would be ~1414 > W1 ~ 1.41; with it RWMD <= W1.
+    P = (np.array([0], np.int32), np.array([1], np.int32), np.array([1], np.int64))
+    Q = (np.array([1000], np.int32), np.array([1001], np.int32), np.array([1], np.int64))
+    LA, LB, L = orc.rwmd(P, Q)
+    w1 = orc.w1_exact(np.array([[0, 1]]), np.array([[1000, 1001]]))
+    assert L <= math.ceil(w1) and L == 1
+
+
+# --------------------------------------------------------------------------
+# eps -> s (tighter bound from the Experiments) and delta (Algorithm 2)
+# --------------------------------------------------------------------------
+
+def test_s_from_eps(orc):
+    for eps, s in [(0.1, 167), (0.05, 327), (0.01, 1607)]:
+        assert orc.s_from_eps(eps) == s
+        assert orc.bound(s) <= 1 + eps < orc.bound(s - 1)
+    # the paper's own pairings satisfy the bound: s = 40 for 0.5, s = 93 for 0.2
+    assert orc.bound(40) <= 1.5 and orc.bound(93) <= 1.2
+    assert orc.eps_c(12) == 1.0 and orc.eps_c(11) == 1.0 and orc.eps_c(20) == 0.5
+
+
+def test_delta_params_satisfy_the_proposition(orc):
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        FA, FB = (int(v) for v in rng.integers(0, 10**6, 2))
+        LA, LB = (int(v) for v in rng.integers(0, 10**12, 2))
+        s = int(rng.integers(3, 2000))
+        delta, G, P = orc.delta_params(LA, LB, FA, FB, s)
+        Llo = max(LA - FA, LB - FB, 0)
+        ec = 8.0 / (s - 4) if s >= 12 else 1.0
+        if FA + FB > 0:
+            # sqrt(2) (|A|+|B|)/2 * delta <= eps_c * L_lo  (Proposition, delta-condensation)
+            assert SQ2 * (FA + FB) / 2 * delta <= ec * Llo * (1 + 1e-12) + 1e-9
+        assert G >= 1 and 0 <= P and 2 * P < G
+        assert G == 1 or G <= 0.99 * delta
+        assert P <= 0.005 * delta
+
+
+def test_splitmix_finaliser_published_vector(orc):
+    # SplitMix64 from state 0: first output = finaliser(0x9E3779B97F4A7C15)
+    assert orc.mix64(0x9E3779B97F4A7C15) == 0xE220A8397B1DCDAF
+
+
+def test_perturbation_range_and_determinism(orc):
+    seen = Counter()
+    for cx in range(-30, 30):
+        for cy in range(0, 30):
+            dx, dy = orc.perturb(7, cx, cy, 3)
+            assert -3 <= dx <= 3 and -3 <= dy <= 3
+            assert (dx, dy) == orc.perturb(7, cx, cy, 3)
+            seen[dx] += 1
+    assert len(seen) == 7 and min(seen.values()) > 150
+    assert orc.perturb(7, 1, 2, 0) == (0, 0)
+
+
+def test_morton_known_values(orc):
+    assert [orc.morton(1, 0), orc.morton(0, 1), orc.morton(1, 1), orc.morton(2, 0), orc.morton(3, 3)] == \
+        [1, 2, 3, 4, 15]
+    assert orc.morton(0xFFFFFFFF, 0) == 0x5555555555555555
+    assert orc.morton(0, 0xFFFFFFFF) == 0xAAAAAAAAAAAAAAAA
+
+
+def _rand_hat(rng, n, lo, hi, cmax=3):
+    X = rng.integers(lo, hi, n).astype(np.int32)
+    Y = rng.integers(lo, hi, n).astype(np.int32)
+    keep = X != Y
+    return (X[keep], Y[keep], rng.integers(1, cmax + 1, keep.sum()).astype(np.int64))
+
+
+def test_condense_delta_snaps_to_nearest_lattice_point(orc):
+    rng = np.random.default_rng(6)
+    Ah = orc.condense0(*_rand_hat(rng, 400, -300, 300)[:2])
+    Bh = orc.condense0(*_rand_hat(rng, 400, -300, 300)[:2])
+    for G, P in [(1, 0), (7, 0), (10, 3), (25, 12)]:
+        nodes = orc.condense_delta(Ah, Bh, G, P, 99)
+        X, Y = nodes["X"].astype(np.int64), nodes["Y"].astype(np.int64)
+        assert nodes["cntA"].sum() == Ah[2].sum() and nodes["cntB"].sum() == Bh[2].sum()
+        assert len(set(zip(X.tolist(), Y.tolist()))) == len(X)
+        # every input node is at the node of its nearest lattice point (ties round up)
+        where = {}
+        for x, y in zip(X.tolist(), Y.tolist()):
+            cx = math.floor(Fraction(x, G) + Fraction(1, 2))
+            cy = math.floor(Fraction(y, G) + Fraction(1, 2))
+            assert abs(x - G * cx) <= P and abs(y - G * cy) <= P
+            where[(cx, cy)] = (x, y)
+        totA, totB = Counter(), Counter()
+        for (hx, hy, hc), tot in ((Ah, totA), (Bh, totB)):
+            for x, y, c in zip(hx.tolist(), hy.tolist(), hc.tolist()):
+                cell = (math.floor(Fraction(x, G) + Fraction(1, 2)), math.floor(Fraction(y, G) + Fraction(1, 2)))
+                tot[where[cell]] += c
+        assert totA == Counter({k: v for k, v in zip(zip(X.tolist(), Y.tolist()), nodes["cntA"].tolist()) if v})
+        assert totB == Counter({k: v for k, v in zip(zip(X.tolist(), Y.tolist()), nodes["cntB"].tolist()) if v})
+        # Morton order of (X - min X, Y - min Y), strictly increasing
+        mx, my = X.min(), Y.min()
+        codes = [orc.morton(int(x - mx), int(y - my)) for x, y in zip(X, Y)]
+        assert codes == [int(c) for c in nodes["code"]] and all(a < b for a, b in zip(codes, codes[1:]))
+        if G == 1 and P == 0:
+            union = Counter(zip(Ah[0].tolist(), Ah[1].tolist())) | Counter(zip(Bh[0].tolist(), Bh[1].tolist()))
+            assert set(zip(X.tolist(), Y.tolist())) == set(union)
+
+
+# --------------------------------------------------------------------------
+# hierarchical tree (radix tree over Morton codes)
+# --------------------------------------------------------------------------
+
+def _nodes_from_points(orc, X, Y):
+    XY = np.unique(np.stack([X, Y], 1), axis=0)
+    X, Y = XY[:, 0].astype(np.int32), XY[:, 1].astype(np.int32)
+    c = np.ones(len(X), np.int64)
+    z = (np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int64))
+    return orc.condense_delta((X, Y, c), z, 1, 0, 0)
+
+
+@pytest.mark.parametrize("clustered", [False, True])
+def test_radix_tree_structure(orc, clustered):
+    rng = np.random.default_rng(7 + clustered)
+    if clustered:
+        ctr = rng.integers(0, 10**6, (8, 2))
+        pts = np.concatenate([c + rng.integers(0, 50, (60, 2)) for c in ctr])
+    else:
+        pts = rng.integers(0, 5000, (500, 2))
+    nodes = _nodes_from_points(orc, pts[:, 0], pts[:, 1])
+    N = len(nodes["X"])
+    t = orc.radix_tree(nodes)
+    code = [int(c) for c in nodes["code"]]
+    X, Y = nodes["X"], nodes["Y"]
+    leaf_seen = Counter()
+    internal_seen = Counter()
+    for w in range(N - 1):
+        lo, hi = int(t["lo"][w]), int(t["hi"][w])
+        assert w in (lo, hi)
+        d = (code[lo] ^ code[hi]).bit_length() - 1
+        ranges = []
+        for ch in (int(t["left"][w]), int(t["right"][w])):
+            if ch < 0:
+                leaf_seen[~ch] += 1
+                ranges.append((~ch, ~ch))
+            else:
+                internal_seen[ch] += 1
+                ranges.append((int(t["lo"][ch]), int(t["hi"][ch])))
+        (a0, a1), (b0, b1) = ranges
+        assert a0 == lo and a1 + 1 == b0 and b1 == hi
+        assert all(not (code[i] >> d) & 1 for i in range(a0, a1 + 1))
+        assert all((code[i] >> d) & 1 for i in range(b0, b1 + 1))
+        sl = slice(lo, hi + 1)
+        assert list(t["bb"][w]) == [X[sl].min(), X[sl].max(), Y[sl].min(), Y[sl].max()]
+        r = min(range(lo, hi + 1), key=lambda i: (int(X[i]), int(Y[i])))
+        assert int(t["rep"][w]) == r
+    assert sorted(leaf_seen) == list(range(N)) and max(leaf_seen.values()) == 1
+    assert sorted(internal_seen) == list(range(1, N - 1)) and max(internal_seen.values()) == 1
+
+
+# --------------------------------------------------------------------------
+# s-WSPD: definition checked by brute force
+# --------------------------------------------------------------------------
+
+def _members(t, ref):
+    if ref < 0:
+        return range(~ref, ~ref + 1)
+    return range(int(t["lo"][ref]), int(t["hi"][ref]) + 1)
+
+
+def _ws_exact(X, Y, U, V, s):
+    """Balls of a common radius d around the two boxes' circumscribed circles
+    at distance >= s d, in exact rational arithmetic."""
+    def circ(S):
+        xs = [int(X[i]) for i in S]
+        ys = [int(Y[i]) for i in S]
+        cx, cy = Fraction(min(xs) + max(xs), 2), Fraction(min(ys) + max(ys), 2)
+        r2 = Fraction((max(xs) - min(xs)) ** 2 + (max(ys) - min(ys)) ** 2, 4)
+        return cx, cy, r2
+    ax, ay, ar2 = circ(U)
+    bx, by, br2 = circ(V)
+    r2 = max(ar2, br2)
+    dist2 = (ax - bx) ** 2 + (ay - by) ** 2
+    # |c_u - c_v| - 2 d >= s d  <=>  |c_u - c_v| >= (s + 2) d
+    return dist2 >= (s + 2) ** 2 * r2
+
+
+@pytest.mark.parametrize("s,clustered", [(2, False), (5, True), (13, False), (40, True)])
+def test_wspd_is_a_well_separated_pair_decomposition(orc, s, clustered):
+    rng = np.random.default_rng(11 + s)
+    if clustered:
+        ctr = rng.integers(0, 20000, (6, 2))
+        pts = np.concatenate([c + rng.integers(0, 300, (40, 2)) for c in ctr])
+    else:
+        pts = rng.integers(0, 3000, (220, 2))
+    nodes = _nodes_from_points(orc, pts[:, 0], pts[:, 1])
+    X, Y = nodes["X"], nodes["Y"]
+    N = len(X)
+    t = orc.radix_tree(nodes)
+    pu, pv = orc.wspd_pairs(nodes, t, s)
+    cover = Counter()
+    for u, v in zip(pu.tolist(), pv.tolist()):
+        U, V = _members(t, u), _members(t, v)
+        assert _ws_exact(X, Y, U, V, s)
+        for p in U:
+            for q in V:
+                cover[(min(p, q), max(p, q))] += 1
+    # every unordered pair of distinct points is covered by exactly one pair
+    assert len(cover) == N * (N - 1) // 2 and set(cover.values()) == {1}
+    tails, heads = orc.wspd(nodes, t, s)
+    rep = lambda r: ~r if r < 0 else int(t["rep"][r])
+    expect = Counter()
+    for u, v in zip(pu.tolist(), pv.tolist()):
+        assert rep(u) in _members(t, u) and rep(v) in _members(t, v)
+        expect[(rep(u), rep(v))] += 1
+        expect[(rep(v), rep(u))] += 1
+    got = Counter(zip(tails.tolist(), heads.tolist()))
+    assert got == expect and set(got.values()) == {1}  # biarcs, no duplicates
+
+
+@pytest.mark.parametrize("s", [8, 13, 20])
+def test_wspd_spanner_stretch(orc, s):
+    rng = np.random.default_rng(20 + s)
+    pts = rng.integers(0, 10**5, (600, 2))
+    nodes = _nodes_from_points(orc, pts[:, 0], pts[:, 1])
+    X, Y = nodes["X"].astype(float), nodes["Y"].astype(float)
+    N = len(X)
+    t = orc.radix_tree(nodes)
+    tails, heads = orc.wspd(nodes, t, s)
+    w = np.hypot(X[tails] - X[heads], Y[tails] - Y[heads])
+    D = shortest_path(csr_matrix((w, (tails, heads)), shape=(N, N)), method="D")
+    E = np.hypot(X[:, None] - X[None, :], Y[:, None] - Y[None, :])
+    iu = np.triu_indices(N, 1)
+    stretch = (D[iu] / E[iu]).max()
+    assert stretch <= 1 + 4 / s + 4 / (s - 2) + 1e-9
+
+
+# --------------------------------------------------------------------------
+# min-cost flow: network simplex vs an LP solver and vs the Hungarian method
+# --------------------------------------------------------------------------
+
+def test_network_simplex_matches_linprog(orc):
+    rng = np.random.default_rng(30)
+    for trial in range(12):
+        n = int(rng.integers(5, 40))
+        arcs = set()
+        for u in range(n - 1):  # a path both ways keeps it feasible
+            arcs.add((u, u + 1))
+            arcs.add((u + 1, u))
+        for _ in range(3 * n):
+            u, v = (int(x) for x in rng.integers(0, n, 2))
+            if u != v:
+                arcs.add((u, v))
+        arcs = sorted(arcs)
+        t = np.array([a[0] for a in arcs], np.int32)
+        h = np.array([a[1] for a in arcs], np.int32)
+        c = rng.integers(0, 50, len(arcs)).astype(np.int64)
+        sup = rng.integers(-5, 6, n).astype(np.int64)
+        sup[-1] -= sup.sum()
+        st, opt, flow, pot = orc.mcf_arcs(n, t, h, c, sup)
+        assert st == 0
+        A = np.zeros((n, len(arcs)))
+        A[t, np.arange(len(arcs))] += 1
+        A[h, np.arange(len(arcs))] -= 1
+        lp = linprog(c.astype(float), A_eq=A, b_eq=sup.astype(float), bounds=(0, None), method="highs")
+        assert lp.status == 0 and round(lp.fun) == opt
+        assert np.array_equal(A @ flow, sup) and (flow >= 0).all() and int(c @ flow) == opt
+        # dual feasibility: no arc with negative reduced cost
+        assert (c - pot[t] + pot[h] >= 0).all()
+
+
+def _augmented(A, B, cost, diag):
+    """Perfect matching on Bi(A,B): A + B-projections vs B + A-projections."""
+    na, nb = len(A), len(B)
+    INF = 1e18
+    M = np.full((na + nb, nb + na), INF)
+    for i, a in enumerate(A):
+        for j, b in enumerate(B):
+            M[i, j] = cost(a, b)
+        M[i, nb + i] = diag(a)
+    for j, b in enumerate(B):
+        M[na + j, j] = diag(b)
+        M[na + j, nb:] = 0.0
+    r, c = linear_sum_assignment(M)
+    return M[r, c].sum()
+
+
+def test_exact_w1_matches_hungarian(orc):
+    rng = np.random.default_rng(31)
+    for trial in range(8):
+        A = synth.uniform_exp(int(rng.integers(1, 60)), 500 + trial).astype(np.float64)
+        B = synth.uniform_exp(int(rng.integers(1, 60)), 600 + trial).astype(np.float64)
+        A = A[A[:, 0] != A[:, 1]]
+        B = B[B[:, 0] != B[:, 1]]
+        ref = _augmented(A, B, lambda a, b: math.hypot(a[0] - b[0], a[1] - b[1]),
+                         lambda a: abs(a[1] - a[0]) / SQ2)
+        assert abs(orc.w1_exact(A, B) - ref) <= 1e-9 * max(1.0, ref)
+
+
+def test_integer_dense_optimum_matches_hungarian(orc):
+    rng = np.random.default_rng(32)
+    icost = lambda a, b: float(orc.cost(int(a[0]), int(a[1]), int(b[0]), int(b[1])))
+    idiag = lambda a: float(orc.cdiag(int(a[0]), int(a[1])))
+    for trial in range(6):
+        A = rng.integers(0, 400, (int(rng.integers(1, 40)), 2))
+        B = rng.integers(0, 400, (int(rng.integers(1, 40)), 2))
+        A = A[A[:, 0] != A[:, 1]]
+        B = B[B[:, 0] != B[:, 1]]
+        P = orc.condense0(A[:, 0].astype(np.int32), A[:, 1].astype(np.int32))
+        Q = orc.condense0(B[:, 0].astype(np.int32), B[:, 1].astype(np.int32))
+        assert orc.dense_opt_int(P, Q) == round(_augmented(A, B, icost, idiag))
+
+
+def test_hungarian_reference_against_permutations(orc):
+    # the augmented-matrix reference itself, against all bijections (n <= 6)
+    rng = np.random.default_rng(33)
+    A = rng.random((3, 2)) * [1, 0] + rng.random((3, 2)) * [0, 1]
+    B = rng.random((3, 2))
+    pts = [tuple(p) for p in A] + [tuple(p) for p in B]
+    na = nb = 3
+    best = math.inf
+    # bijection between A + B-projections and B + A-projections
+    for perm in itertools.permutations(range(na + nb)):
+        tot = 0.0
+        for i, j in enumerate(perm):
+            if i < na and j < nb:
+                tot += math.dist(A[i], B[j])
+            elif i < na:
+                tot += abs(A[i][1] - A[i][0]) / SQ2 if j - nb == i else math.inf
+            elif j < nb:
+                tot += abs(B[j][1] - B[j][0]) / SQ2 if i - na == j else math.inf
+        best = min(best, tot)
+    ref = _augmented(A, B, lambda a, b: math.dist(a, b), lambda a: abs(a[1] - a[0]) / SQ2)
+    assert abs(ref - best) < 1e-12
+    assert abs(orc.w1_exact(A, B) - best) < 1e-9
+
+
+def test_hand_derived_examples(orc):
+    cases = json.load(open(os.path.join(GOLDEN, "hand_examples.json")))["cases"]
+    for cs in cases:
+        A = np.array(cs["A"], np.float64)
+        B = np.array(cs["B"], np.float64)
+        assert abs(orc.w1_exact(A, B) - cs["w1"]) < 1e-12, cs["name"]
+        r = orc.w1_approx(A.astype(np.uint8), B.astype(np.uint8), "u8", k=0, s_override=10**6,
+                          condense=False)
+        assert r["opt"] == cs["opt_int"], cs["name"]
+
+
+def test_w1_closed_forms(orc):
+    A = synth.uniform_exp(300, 41).astype(np.float64)
+    A = A[A[:, 0] != A[:, 1]]
+    B = synth.uniform_exp(250, 42).astype(np.float64)
+    B = B[B[:, 0] != B[:, 1]]
+    # empty diagram: sum of distances to the diagonal
+    assert abs(orc.w1_exact(A, np.zeros((0, 2))) - np.abs(A[:, 1] - A[:, 0]).sum() / SQ2) < 1e-9
+    assert orc.w1_exact(A, A) == 0.0
+    w = orc.w1_exact(A, B)
+    assert abs(orc.w1_exact(B, A) - w) < 1e-9
+    # translation along (t, t) and scaling by 2
+    assert abs(orc.w1_exact(A + 3.0, B + 3.0) - w) < 1e-9
+    assert abs(orc.w1_exact(2 * A, 2 * B) - 2 * w) < 1e-9
+    # single points: min(|a - b|, d(a) + d(b))
+    for a, b in [((0.0, 1.0), (0.1, 1.2)), ((0.0, 0.2), (5.0, 5.3))]:
+        ref = min(math.dist(a, b), (a[1] - a[0]) / SQ2 + (b[1] - b[0]) / SQ2)
+        assert abs(orc.w1_exact(np.array([a]), np.array([b])) - ref) < 1e-12
+
+
+def test_far_from_diagonal_reduces_to_emd(orc):
+    # Conditional lower bound section: far from the diagonal, W1 is the EMD
+    rng = np.random.default_rng(43)
+    A = rng.random((40, 2)) + [0.0, 1000.0]
+    B = rng.random((40, 2)) + [0.0, 1000.0]
+    D = np.hypot(A[:, None, 0] - B[None, :, 0], A[:, None, 1] - B[None, :, 1])
+    r, c = linear_sum_assignment(D)
+    assert abs(orc.w1_exact(A, B) - D[r, c].sum()) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# the whole pipeline: the paper's chain of bounds, exactly in integers
+# --------------------------------------------------------------------------
+
+def _small_pair(n, seed):
+    return synth.uniform_exp(n, seed), synth.uniform_exp(n, seed + 1)
+
+
+@pytest.mark.parametrize("eps,seed", [(0.1, 100), (0.5, 102), (1.0, 104)])
+def test_pipeline_bound_chain(orc, eps, seed):
+    A, B = _small_pair(400, seed)
+    r = orc.w1_approx(A, B, "f32", eps=eps, k=16)
+    # RWMD_0 <= OPT(G_0)
+    opt0 = orc.dense_opt_int(r["Ahat"], r["Bhat"])
+    assert r["rwmd"] <= opt0
+    # RWMD_delta <= OPT(G_delta) <= OPT(WS)  (Theorem, spanner approximation, left side)
+    nd = r["nodes"]
+    ia, ib = nd["cntA"] > 0, nd["cntB"] > 0
+    Pd = (nd["X"][ia], nd["Y"][ia], nd["cntA"][ia])
+    Qd = (nd["X"][ib], nd["Y"][ib], nd["cntB"][ib])
+    optd = orc.dense_opt_int(Pd, Qd)
+    assert orc.rwmd(Pd, Qd)[2] <= optd <= r["opt"]
+    # OPT(WS) <= (1 + 4/s + 4/(s-2)) OPT(G_delta) + rounding slack (right side)
+    assert r["opt"] <= (1 + 4 / r["s"] + 4 / (r["s"] - 2)) * optd + r["slack"]
+    # (1 - eps) W1 <= W1_approx <= (1 + eps) W1 + slack   vs exact FP64 W1
+    w = orc.w1_exact(A.astype(np.float64), B.astype(np.float64))
+    q = 2.0 ** -r["k"]
+    qerr = (r["FA"] + r["FB"]) * q  # input quantisation moves each point by < q/sqrt(2)
+    assert (1 - eps) * w - qerr <= r["w1"] <= (1 + eps) * w + r["slack"] * q + qerr
+
+
+def test_pipeline_identity_symmetry_and_dense_limit(orc):
+    A, B = _small_pair(300, 200)
+    assert orc.w1_approx(A, A, "f32", eps=0.1)["opt"] == 0
+    rab = orc.w1_approx(A, B, "f32", eps=0.1, seed=5)
+    rba = orc.w1_approx(B, A, "f32", eps=0.1, seed=5)
+    assert rab["opt"] == rba["opt"]
+    # s -> infinity without condensation: the WSPD is the complete graph and
+    # OPT(WS) equals the dense integer optimum on G_0
+    r = orc.w1_approx(A, B, "f32", s_override=10**7, condense=False)
+    assert len(r["ws_tails"]) == len(r["nodes"]["X"]) * (len(r["nodes"]["X"]) - 1)
+    assert r["opt"] == orc.dense_opt_int(r["Ahat"], r["Bhat"])
+
+
+def test_pipeline_empty_and_one_sided(orc):
+    A, _ = _small_pair(200, 300)
+    E = np.zeros((0, 2), np.float32)
+    r = orc.w1_approx(A, E, "f32", eps=0.1)
+    Ah = r["Ahat"]
+    closed = sum(int(c) * orc.cdiag(int(x), int(y)) for x, y, c in zip(*Ah))
+    assert r["rwmd"] == closed  # RWMD(B = empty) == W1 exactly
+    # with no B mass every A unit goes straight to the diagonal
+    r0 = orc.w1_approx(A, E, "f32", eps=0.1, condense=False)
+    assert r0["opt"] == closed
+    assert orc.w1_approx(E, E, "f32", eps=0.1)["opt"] == 0
