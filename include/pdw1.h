@@ -1,0 +1,202 @@
+/*
+ * pdw1.h -- C ABI of the GB300 (sm_103a) library for the approximate
+ * 1-Wasserstein distance between persistence diagrams by graph
+ * sparsification (Dey & Zhang, arXiv 2110.14734).
+ *
+ * Every step runs in hand-written CUDA kernels on one GPU.  Plain C types
+ * only: pointers, sizes, a CUDA stream as an opaque pointer.
+ *
+ * Conventions (all entry points):
+ *   - Device pointers are on the context's device.  Diagram inputs may also be
+ *     host pointers (pd_diagram.on_host = 1); the library then copies them to
+ *     the device on the given stream.
+ *   - Device outputs (pd_nodes, pd_network) are owned by the context and stay
+ *     valid until the next call on the same context.  The caller never frees
+ *     them.
+ *   - Host outputs are written only when the call returns PD_OK.  Entry points
+ *     with host outputs synchronise their stream before returning.
+ *   - Calls are ordered on the stream passed in (NULL = legacy default
+ *     stream).  One context must not be used from two streams at once.
+ *   - No C++ exception crosses the ABI.  On an error the context stays usable;
+ *     pd_last_error() describes the error.
+ *
+ * Units: coordinates are quantised to q = 2^-k (k = coord_shift); every cost
+ * is an integer number of quanta, rounded UP (so rounded costs keep the
+ * triangle inequality); W1 ~= opt_quanta * q.
+ */
+#ifndef PDW1_H
+#define PDW1_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PD_OK = 0,
+    PD_EINVAL = 1,      /* bad argument or a non-finite / out-of-range coordinate */
+    PD_ENOMEM = 2,      /* device allocation failed or the context's byte cap was reached */
+    PD_ECUDA = 3,       /* a CUDA runtime call failed */
+    PD_ETIMEOUT = 4,    /* the solver's round cap or a bounded device wait ran out */
+    PD_ECAPACITY = 5,   /* a size limit of the library was exceeded (stated in the message) */
+    PD_EOVERFLOW = 6,   /* an integer quantity left its 64-bit range */
+    PD_EINFEASIBLE = 7  /* the network has no feasible flow */
+} pd_status;
+
+typedef struct pd_ctx pd_ctx;
+
+/* Create a context on CUDA device `device`.  arena_bytes caps the device
+ * memory the context may hold at once (0 = no cap).  Allocates lazily. */
+pd_status pd_create(pd_ctx** out, int device, size_t arena_bytes);
+void pd_destroy(pd_ctx* ctx);
+/* Message of the last error on this context ("" after success). */
+const char* pd_last_error(const pd_ctx* ctx);
+
+typedef enum { PD_F32 = 0, PD_U8 = 1 } pd_dtype;
+
+/* A persistence diagram: n points stored as interleaved (birth, death) pairs,
+ * float32 (PD_F32) or uint8 (PD_U8).  Points with birth == death (after
+ * quantisation) lie on the diagonal and are ignored (Problem Formulation). */
+typedef struct {
+    const void* bd;
+    int64_t n;
+    int32_t dtype;
+    int32_t on_host; /* 1: bd is host memory (pinned or pageable) */
+} pd_diagram;
+
+/* Options.  pd_opts_default() fills the defaults; a NULL pd_opts* means
+ * defaults everywhere. */
+typedef struct {
+    int32_t coord_shift; /* k of the quantum 2^-k; -1 = 20 for PD_F32, 12 for PD_U8 */
+    int32_t s_override;  /* WSPD parameter s; 0 = derived from eps (see pd_w1_approx) */
+    int32_t condense;    /* 1 = delta-condensation (Algorithm 2); 0 = only merge coincident points */
+    int32_t perturb;     /* 1 = random shift of condensed nodes (Algorithm 2); 0 = none */
+    uint64_t seed;       /* seed of the shift (a pure function of seed and lattice cell) */
+    int32_t alpha;       /* cost-scaling divisor of the solver, >= 2 (default 8) */
+    int32_t verify;      /* 1 = certify optimality of the final flow on the device */
+    int64_t max_rounds;  /* solver watchdog: push/relabel rounds over all phases (0 = default) */
+    int64_t time_limit_ms;  /* solver watchdog: device wall-clock limit of one solve (0 = 60000) */
+    int64_t update_every;   /* relabels between global price updates (0 = number of nodes, -1 = never) */
+    int32_t seq_threshold;  /* at most this many active nodes: one block finishes them (-1 = default 64) */
+    int32_t reserved;
+} pd_opts;
+
+void pd_opts_default(pd_opts* opts);
+
+/* Condensed nodes, device memory owned by the context, ordered by the 64-bit
+ * Morton code of (X - min X, Y - min Y) (bit i of x -> bit 2i, of y -> 2i+1). */
+typedef struct {
+    int64_t n_nodes;
+    int32_t* X;
+    int32_t* Y;
+    int64_t* cntA; /* multiplicity of diagram A at the node */
+    int64_t* cntB; /* multiplicity of diagram B at the node */
+    uint64_t* morton;
+} pd_nodes;
+
+/* Sparse transshipment network in CSR form, device memory owned by the
+ * context.  Node ids: 0..N-1 the condensed nodes (Morton rank), N = ā (A's
+ * diagonal node), N+1 = b̄ (B's diagonal node); n_nodes = N + 2.  Rows are
+ * sorted by head.  cost in quanta; supply[u] = cntA - cntB, supply[ā] = -|A|,
+ * supply[b̄] = |B|. */
+typedef struct {
+    int64_t n_nodes;
+    int64_t n_arcs;
+    int64_t* row_ptr; /* n_nodes + 1 entries */
+    int32_t* head;    /* n_arcs */
+    int64_t* cost;    /* n_arcs */
+    int64_t* supply;  /* n_nodes */
+} pd_network;
+
+typedef struct {
+    double w1;              /* opt_quanta * 2^-coord_shift */
+    int64_t opt_quanta;     /* optimum of the sparse network (exact, integer) */
+    int64_t rwmd_quanta;    /* RWMD of the 0-condensed diagrams, max(L_A, L_B) */
+    int64_t rwmd_A;         /* L_A */
+    int64_t rwmd_B;         /* L_B */
+    int64_t slack_quanta;   /* total flow: bound on the cost rounding, W1 <= w1 + slack*q */
+    int64_t mass_A;         /* |A| after dropping diagonal points */
+    int64_t mass_B;         /* |B| */
+    int32_t s;              /* WSPD parameter used */
+    int32_t coord_shift;    /* k used */
+    double delta;           /* delta of Algorithm 2, in quanta */
+    int64_t cell_quanta;    /* lattice spacing G = max(1, floor(0.99 delta)) */
+    int64_t shift_quanta;   /* shift bound P = floor(0.005 delta) */
+    int64_t n_nodes;        /* condensed nodes N (without ā, b̄) */
+    int64_t n_arcs;         /* arcs of the sparse network */
+    int32_t phases;         /* solver: cost-scaling phases */
+    int32_t verified;       /* 1 if the device optimality certificate passed */
+    int64_t rounds;         /* solver: push/relabel rounds */
+    int64_t pushes;         /* solver: push operations */
+    int64_t relabels;       /* solver: relabel operations */
+    int64_t repair_passes;  /* solver: price-repair passes */
+    int64_t price_updates;  /* solver: global price updates */
+    int64_t update_passes;  /* solver: relaxation passes of the global price updates */
+    float stage_ms[8];      /* quantize+0-condense, RWMD, delta-condense, tree, WSPD, CSR, solve, total */
+} pd_result;
+
+/*
+ * delta-condensation (Algorithm 2, snapping and aggregation): quantise A and B,
+ * merge coincident points, snap every node to the common lattice
+ * cell_quanta * Z^2 (nearest lattice point, ties up), aggregate the
+ * multiplicities per cell, shift each cell's node by a pseudo-random offset
+ * in [-shift_quanta, shift_quanta]^2 (a pure function of opts->seed and the
+ * cell), and order the nodes by Morton code.  cell_quanta = 1 and
+ * shift_quanta = 0 give the 0-condensation of A united with B.
+ * Requires cell_quanta >= 1, 0 <= 2 * shift_quanta < cell_quanta.
+ */
+pd_status pd_condense(pd_ctx* ctx, pd_diagram A, pd_diagram B, int64_t cell_quanta,
+                      int64_t shift_quanta, const pd_opts* opts, pd_nodes* out, void* stream);
+
+/*
+ * RWMD lower bound (Algorithm 1) of the 0-condensed diagrams with rounded-up
+ * costs: L_A = sum_u cntA(u) * min(d_diag(u), min_v c(u, v)) over A's nodes,
+ * v over B's nodes (the relaxed min-cost flow also lets a unit go to its
+ * diagonal node), L_B symmetric.  out3[0] = L_A, out3[1] = L_B,
+ * out3[2] = max(L_A, L_B), host memory, in quanta.
+ */
+pd_status pd_rwmd_lower_bound(pd_ctx* ctx, pd_diagram A, pd_diagram B, const pd_opts* opts,
+                              int64_t* out3, void* stream);
+
+/*
+ * Sparse network WS_s^PD (WSPD section, Algorithms 6-9): a binary radix tree
+ * (compressed quadtree) over the Morton-ordered nodes, every s-well-separated
+ * pair of the s-WSPD as the biarc between the leftmost points of the two sets,
+ * the diagonal arcs u -> ā (u holds A mass), b̄ -> v (v holds B mass) and
+ * b̄ -> ā at cost 0, assembled into CSR.  `nodes` is device memory laid out as
+ * pd_nodes (unique coordinates, ascending Morton code, |X|,|Y| < 2^30).
+ */
+pd_status pd_wspd_sparsify(pd_ctx* ctx, const pd_nodes* nodes, int32_t s, pd_network* out,
+                           void* stream);
+
+/*
+ * Exact integer min-cost flow on an uncapacitated network (the min-cost flow
+ * of the transshipment network definition), by cost scaling with push/relabel
+ * rounds in one persistent kernel.  `net` is device memory in pd_network
+ * layout: unique (tail, head) arcs, rows sorted by head, costs in [0, 2^31),
+ * supplies summing to 0.  *opt_out (host) receives the optimum; stats (host,
+ * may be NULL) receives the solver counters.
+ */
+pd_status pd_mcf_solve(pd_ctx* ctx, const pd_network* net, const pd_opts* opts, int64_t* opt_out,
+                       pd_result* stats, void* stream);
+
+/*
+ * Approximate W1 (Algorithm 4): delta-condensation with delta from the RWMD
+ * (Algorithm 2), the sparse network (pd_wspd_sparsify) and its exact optimum
+ * (pd_mcf_solve; the solver contracts the zero-cost arc b̄ -> ā into one
+ * diagonal node of supply |B| - |A|, which leaves the optimum unchanged).  s is the smallest integer >= 13 with
+ * (1 + 4/s + 4/(s-2)) (1 + 8/(s-4)) <= 1 + eps (the tighter bound of the
+ * paper's experiments) unless opts->s_override is set; eps_c = 8/(s-4)
+ * (1 for s < 12), delta = 2 eps_c L_lo / (sqrt(2) (|A| + |B|)) with
+ * L_lo = max(L_A - |A|, L_B - |B|, 0).  Result (host) in *out.
+ */
+pd_status pd_w1_approx(pd_ctx* ctx, pd_diagram A, pd_diagram B, double eps, const pd_opts* opts,
+                       pd_result* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDW1_H */

@@ -1,0 +1,109 @@
+// Internal (C++) interface between the entry points and the stages.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/pdw1.h"
+
+namespace pd {
+
+// Named device buffers held by a context; each grows on demand.
+enum Buf : int {
+    B_IN_A, B_IN_B,                 // staged host diagrams
+    B_QX, B_QY, B_QKEY, B_QKEY2, B_QVAL, B_QVAL2, B_FLAG, B_IDX,
+    B_HAT_X, B_HAT_Y, B_HAT_C,      // 0-condensed nodes of A then B
+    B_CKEY, B_CKEY2, B_CVAL, B_CVAL2, B_CIDX, B_CX, B_CY, B_CA, B_CB,
+    B_NX, B_NY, B_NCA, B_NCB, B_NCODE,  // output nodes
+    B_T_LEFT, B_T_RIGHT, B_T_BB, B_T_REP, B_T_PARENT, B_T_LPARENT, B_T_VISIT,
+    B_F0, B_F1, B_WSFLAG, B_WSOFF,  // WSPD frontier
+    B_ARCKEY, B_ARCKEY2,            // arc keys (tail << hb | head)
+    B_ROWPTR, B_HEAD, B_COST, B_SUPPLY,
+    B_S_ROWPTR, B_S_HEAD, B_S_CW, B_S_TWIN, B_S_X, B_S_PAIR, B_S_XKEY, B_S_XKEY2, B_S_XVAL,
+    B_S_XVAL2, B_S_XPTR, B_S_XPOS, B_S_TAIL,
+    B_S_E, B_S_P, B_S_D, B_S_CUR, B_S_RELAB, B_S_CTL, B_S_Q,
+    B_RS_COUNTS, B_RS_PART, B_SCAN_PART,
+    B_M_ROWPTR, B_M_SUPPLY,
+    B_SMALL,                        // small device scalars
+    B_COUNT
+};
+
+struct Ctx {
+    int device = 0;
+    size_t cap = 0;
+    size_t held = 0;
+    std::string err;
+    void* ptr[B_COUNT] = {};
+    size_t bytes[B_COUNT] = {};
+    int64_t* h_small = nullptr;  // pinned host mirror of small scalars
+    pd_nodes nodes{};
+    pd_network net{};
+    int sm_count = 0;
+};
+
+// Returns a device buffer of at least `bytes` bytes (contents undefined), or
+// nullptr (ctx->err set) when allocation fails or the cap is reached.
+void* buf(Ctx* c, Buf id, size_t bytes);
+
+template <typename T>
+T* bufT(Ctx* c, Buf id, int64_t n) {
+    return (T*)buf(c, id, sizeof(T) * (size_t)(n > 0 ? n : 1));
+}
+
+pd_status fail(Ctx* c, pd_status st, const std::string& msg);
+pd_status cuda_fail(Ctx* c, cudaError_t e, const char* where);
+
+#define PD_TRY_CUDA(c, expr)                                    \
+    do {                                                        \
+        cudaError_t _e = (expr);                                \
+        if (_e != cudaSuccess) return cuda_fail((c), _e, #expr); \
+    } while (0)
+
+#define PD_TRY(expr)                       \
+    do {                                   \
+        pd_status _s = (expr);             \
+        if (_s != PD_OK) return _s;        \
+    } while (0)
+
+// Quantised diagram points already on the device.
+struct DevDiag {
+    const void* bd;
+    int64_t n;
+    int dtype;
+};
+
+// 0-condensed nodes of A (first nA) and B (next nB): device X, Y, cnt.
+struct Hats {
+    int32_t* X;
+    int32_t* Y;
+    int64_t* cnt;
+    int64_t nA, nB;  // node counts
+    int64_t FA, FB;  // masses (points kept)
+};
+
+struct SolveStats {
+    int64_t opt = 0, slack = 0, rounds = 0, pushes = 0, relabels = 0, repairs = 0, updates = 0, update_passes = 0;
+    int32_t phases = 0, verified = 0;
+};
+
+pd_status stage_condense0(Ctx* c, const DevDiag& A, const DevDiag& B, int k, Hats* out, cudaStream_t st);
+pd_status stage_rwmd(Ctx* c, const Hats& h, int64_t L[3], cudaStream_t st);
+pd_status stage_condense_delta(Ctx* c, const Hats& h, int64_t G, int64_t P, uint64_t seed, pd_nodes* out,
+                               cudaStream_t st);
+pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* out, float* ms_tree,
+                        float* ms_wspd, float* ms_csr, cudaStream_t st);
+pd_status merge_diagonal(Ctx* c, const pd_network& net, int64_t N, pd_network* out, cudaStream_t st);
+pd_status stage_solve(Ctx* c, const pd_network& net, const pd_opts& o, SolveStats* out, cudaStream_t st);
+
+pd_status validate_nodes(Ctx* c, const pd_nodes& nodes, cudaStream_t st);
+pd_status validate_network(Ctx* c, const pd_network& net, cudaStream_t st);
+
+__global__ void k_row_ptr(const uint64_t* key, int64_t m, int hb, int64_t nrows, int64_t* row_ptr);
+
+// radix sort / scan with context scratch
+pd_status sort_u64(Ctx* c, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n,
+                   int bits, cudaStream_t st);
+pd_status scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev, cudaStream_t st);
+
+}  // namespace pd

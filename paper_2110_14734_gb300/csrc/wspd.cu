@@ -1,0 +1,439 @@
+// Hierarchical tree (binary radix tree over Morton order), s-WSPD biarcs
+// (Algorithms 6-8 as a level-synchronous pair frontier), diagonal arcs
+// (Algorithm 9) and the CSR network.
+#include "internal.h"
+#include "prims.cuh"
+
+namespace pd {
+
+// ---------------------------------------------------------------------------
+// radix tree (Karras 2012) and bottom-up bounding boxes
+// ---------------------------------------------------------------------------
+
+PD_D int code_delta(const uint64_t* __restrict__ code, int64_t N, int64_t i, int64_t j) {
+    if (j < 0 || j >= N) return -1;
+    return __clzll((long long)(code[i] ^ code[j]));
+}
+
+// Internal node i covers [lo, hi] with i at one end; its split is the last
+// index below the highest bit where the range's codes differ.  Children:
+// c >= 0 internal c, c < 0 leaf ~c.
+__global__ void k_karras(const uint64_t* __restrict__ code, int64_t N, int32_t* __restrict__ left,
+                         int32_t* __restrict__ right, int32_t* __restrict__ par_int, int32_t* __restrict__ par_leaf) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N - 1) return;
+    int d = (code_delta(code, N, i, i + 1) - code_delta(code, N, i, i - 1)) > 0 ? 1 : -1;
+    int dmin = code_delta(code, N, i, i - d);
+    int64_t lmax = 2;
+    while (code_delta(code, N, i, i + lmax * d) > dmin) lmax <<= 1;
+    int64_t l = 0;
+    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+        if (code_delta(code, N, i, i + (l + t) * d) > dmin) l += t;
+    int64_t j = i + l * d;
+    int dnode = code_delta(code, N, i, j);
+    int64_t s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (code_delta(code, N, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+    int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    if (lo == gamma) {
+        left[i] = ~(int32_t)gamma;
+        par_leaf[gamma] = (int32_t)i;
+    } else {
+        left[i] = (int32_t)gamma;
+        par_int[gamma] = (int32_t)i;
+    }
+    if (hi == gamma + 1) {
+        right[i] = ~(int32_t)(gamma + 1);
+        par_leaf[gamma + 1] = (int32_t)i;
+    } else {
+        right[i] = (int32_t)(gamma + 1);
+        par_int[gamma + 1] = (int32_t)i;
+    }
+    if (i == 0) par_int[0] = -1;
+}
+
+// Each leaf climbs; the second child to arrive at a node computes the node's
+// tight box and leftmost member (min X, then min Y) from its two children.
+__global__ void k_bbox(int64_t N, const int32_t* __restrict__ X, const int32_t* __restrict__ Y,
+                       const int32_t* __restrict__ left, const int32_t* __restrict__ right,
+                       const int32_t* __restrict__ par_int, const int32_t* __restrict__ par_leaf, int4* bb,
+                       int32_t* rep, int32_t* visit) {
+    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= N) return;
+    int32_t cur = par_leaf[l];
+    for (int depth = 0; cur >= 0 && depth < 130; depth++) {  // a radix tree over 64-bit codes is < 65 deep
+        __threadfence();
+        if (atomicAdd(&visit[cur], 1) == 0) return;
+        int4 b[2];
+        int32_t r[2];
+        int32_t ch[2] = {left[cur], right[cur]};
+        for (int q = 0; q < 2; q++) {
+            int32_t c = ch[q];
+            if (c < 0) {
+                int32_t p = ~c;
+                b[q] = make_int4(X[p], X[p], Y[p], Y[p]);
+                r[q] = p;
+            } else {
+                b[q] = __ldcg(&bb[c]);
+                r[q] = __ldcg(&rep[c]);
+            }
+        }
+        int4 u = make_int4(min(b[0].x, b[1].x), max(b[0].y, b[1].y), min(b[0].z, b[1].z), max(b[0].w, b[1].w));
+        int32_t rr = (X[r[1]] < X[r[0]] || (X[r[1]] == X[r[0]] && Y[r[1]] < Y[r[0]])) ? r[1] : r[0];
+        __stcg(&bb[cur], u);
+        __stcg(&rep[cur], rr);
+        cur = par_int[cur];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// s-WSPD as a pair frontier
+// ---------------------------------------------------------------------------
+
+struct TNode {
+    int32_t mnx, mxx, mny, mxy, rep, l, r;
+};
+
+PD_D TNode load_tnode(int32_t ref, const int32_t* __restrict__ X, const int32_t* __restrict__ Y,
+                      const int4* __restrict__ bb, const int32_t* __restrict__ rep, const int32_t* __restrict__ left,
+                      const int32_t* __restrict__ right) {
+    TNode t;
+    if (ref < 0) {
+        int32_t p = ~ref;
+        t.mnx = t.mxx = X[p];
+        t.mny = t.mxy = Y[p];
+        t.rep = p;
+        t.l = t.r = 0;
+    } else {
+        int4 b = bb[ref];
+        t.mnx = b.x;
+        t.mxx = b.y;
+        t.mny = b.z;
+        t.mxy = b.w;
+        t.rep = rep[ref];
+        t.l = left[ref];
+        t.r = right[ref];
+    }
+    return t;
+}
+
+// s-well-separated with circumscribed circles of the tight boxes and the
+// larger radius for both: in doubled coordinates |C_u - C_v| >= (s+2) D,
+// D the larger box diagonal; exact in 128-bit integers.
+PD_D bool well_separated(const TNode& a, const TNode& b, int64_t s) {
+    int64_t dx = ((int64_t)a.mnx + a.mxx) - ((int64_t)b.mnx + b.mxx);
+    int64_t dy = ((int64_t)a.mny + a.mxy) - ((int64_t)b.mny + b.mxy);
+    uint64_t ax = (uint64_t)(dx < 0 ? -dx : dx), ay = (uint64_t)(dy < 0 ? -dy : dy);
+    unsigned __int128 D2 = (unsigned __int128)ax * ax + (unsigned __int128)ay * ay;
+    uint64_t awx = (uint64_t)((int64_t)a.mxx - a.mnx), awy = (uint64_t)((int64_t)a.mxy - a.mny);
+    uint64_t bwx = (uint64_t)((int64_t)b.mxx - b.mnx), bwy = (uint64_t)((int64_t)b.mxy - b.mny);
+    uint64_t ra = awx * awx + awy * awy, rb = bwx * bwx + bwy * bwy;
+    uint64_t R2 = ra > rb ? ra : rb;
+    uint64_t k = (uint64_t)(s + 2) * (uint64_t)(s + 2);
+    return D2 >= (unsigned __int128)k * R2;
+}
+
+PD_D int64_t max_side(const TNode& a) {
+    int64_t wx = (int64_t)a.mxx - a.mnx, wy = (int64_t)a.mxy - a.mny;
+    return wx > wy ? wx : wy;
+}
+
+__global__ void k_frontier_init(int64_t N, const int32_t* __restrict__ left, const int32_t* __restrict__ right,
+                                int2* __restrict__ F) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N - 1) F[i] = make_int2(left[i], right[i]);
+}
+
+__global__ void k_ws_classify(const int2* __restrict__ F, int64_t nf, const int32_t* __restrict__ X,
+                              const int32_t* __restrict__ Y, const int4* __restrict__ bb,
+                              const int32_t* __restrict__ rep, const int32_t* __restrict__ left,
+                              const int32_t* __restrict__ right, int64_t s, int64_t* __restrict__ flag,
+                              int64_t* __restrict__ off) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    int2 p = F[i];
+    TNode u = load_tnode(p.x, X, Y, bb, rep, left, right);
+    TNode v = load_tnode(p.y, X, Y, bb, rep, left, right);
+    int64_t w = well_separated(u, v, s) ? 1 : 0;
+    flag[i] = w;
+    off[i] = w;
+}
+
+// Well-separated pair -> two directed arcs between the representatives;
+// otherwise split the node with the larger box side (ties split v) into two
+// pairs of the next frontier.
+__global__ void k_ws_expand(const int2* __restrict__ F, int64_t nf, const int64_t* __restrict__ flag,
+                            const int64_t* __restrict__ off, const int32_t* __restrict__ X,
+                            const int32_t* __restrict__ Y, const int4* __restrict__ bb,
+                            const int32_t* __restrict__ rep, const int32_t* __restrict__ left,
+                            const int32_t* __restrict__ right, int hb, uint64_t* __restrict__ arcs,
+                            int2* __restrict__ Fn) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    int2 p = F[i];
+    TNode u = load_tnode(p.x, X, Y, bb, rep, left, right);
+    TNode v = load_tnode(p.y, X, Y, bb, rep, left, right);
+    int64_t o = off[i];
+    if (flag[i]) {
+        arcs[2 * o] = ((uint64_t)u.rep << hb) | (uint64_t)v.rep;
+        arcs[2 * o + 1] = ((uint64_t)v.rep << hb) | (uint64_t)u.rep;
+    } else {
+        int64_t j = i - o;
+        if (max_side(u) > max_side(v)) {
+            Fn[2 * j] = make_int2(u.l, p.y);
+            Fn[2 * j + 1] = make_int2(u.r, p.y);
+        } else {
+            Fn[2 * j] = make_int2(p.x, v.l);
+            Fn[2 * j + 1] = make_int2(p.x, v.r);
+        }
+    }
+}
+
+// Diagonal arcs: u -> ā if u holds A mass, b̄ -> u if u holds B mass, and
+// b̄ -> ā; absent arcs become the all-ones key, which sorts last.
+__global__ void k_diag_arcs(int64_t N, const int64_t* __restrict__ cntA, const int64_t* __restrict__ cntB, int hb,
+                            uint64_t sent, uint64_t* __restrict__ arcs, unsigned long long* __restrict__ counts) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u > N) return;
+    if (u == N) {
+        arcs[2 * N] = ((uint64_t)(N + 1) << hb) | (uint64_t)N;
+        return;
+    }
+    bool a = cntA[u] > 0, b = cntB[u] > 0;
+    arcs[2 * u] = a ? (((uint64_t)u << hb) | (uint64_t)N) : sent;
+    arcs[2 * u + 1] = b ? (((uint64_t)(N + 1) << hb) | (uint64_t)u) : sent;
+    unsigned ma = __ballot_sync(__activemask(), a), mb = __ballot_sync(__activemask(), b);
+    if ((threadIdx.x & 31) == (__ffs(__activemask()) - 1)) {
+        atomicAdd(&counts[0], (unsigned long long)__popc(ma));
+        atomicAdd(&counts[1], (unsigned long long)__popc(mb));
+    }
+}
+
+// row_ptr from arc keys sorted by (tail, head).
+__global__ void k_row_ptr(const uint64_t* __restrict__ key, int64_t m, int hb, int64_t nrows,
+                          int64_t* __restrict__ row_ptr) {
+    int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= m) return;
+    int64_t t = (int64_t)(key[a] >> hb);
+    int64_t tp = a == 0 ? -1 : (int64_t)(key[a - 1] >> hb);
+    for (int64_t r = tp + 1; r <= t; r++) row_ptr[r] = a;
+    if (a == m - 1)
+        for (int64_t r = t + 1; r <= nrows; r++) row_ptr[r] = m;
+}
+
+__global__ void k_head_cost(const uint64_t* __restrict__ key, int64_t m, int hb, int64_t N,
+                            const int32_t* __restrict__ X, const int32_t* __restrict__ Y, int32_t* __restrict__ head,
+                            int64_t* __restrict__ cost) {
+    int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= m) return;
+    uint64_t k = key[a];
+    int64_t t = (int64_t)(k >> hb), h = (int64_t)(k & ((1ull << hb) - 1));
+    head[a] = (int32_t)h;
+    int64_t c = 0;
+    if (t < N && h < N)
+        c = cost_l2(X[t], Y[t], X[h], Y[h]);
+    else if (t < N && h == N)
+        c = cost_diag(X[t], Y[t]);
+    else if (t == N + 1 && h < N)
+        c = cost_diag(X[h], Y[h]);
+    cost[a] = c;
+}
+
+__global__ void k_supply(int64_t N, const int64_t* __restrict__ cntA, const int64_t* __restrict__ cntB, int64_t FA,
+                         int64_t FB, int64_t* __restrict__ sup) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < N) sup[u] = cntA[u] - cntB[u];
+    if (u == N) sup[N] = -FA;
+    if (u == N + 1) sup[N + 1] = FB;
+}
+
+__global__ void k_mass(int64_t N, const int64_t* __restrict__ cntA, const int64_t* __restrict__ cntB,
+                       unsigned long long* __restrict__ out) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long a = 0, b = 0;
+    if (u < N) {
+        a = (unsigned long long)cntA[u];
+        b = (unsigned long long)cntB[u];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (a) atomicAdd(&out[2], a);
+        if (b) atomicAdd(&out[3], b);
+    }
+}
+
+__global__ void k_check_nodes(const uint64_t* __restrict__ code, const int32_t* __restrict__ X,
+                              const int32_t* __restrict__ Y, const int64_t* __restrict__ cntA,
+                              const int64_t* __restrict__ cntB, int64_t N, unsigned long long* __restrict__ bad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int32_t lim = 1 << 30;
+    bool b = (i + 1 < N && !(code[i] < code[i + 1])) || X[i] <= -lim || X[i] >= lim || Y[i] <= -lim || Y[i] >= lim ||
+             cntA[i] < 0 || cntB[i] < 0;
+    if (b) atomicAdd(bad, 1ull);
+}
+
+pd_status validate_nodes(Ctx* c, const pd_nodes& nodes, cudaStream_t st) {
+    int64_t N = nodes.n_nodes;
+    if (N <= 0) return PD_OK;
+    unsigned long long* sm = bufT<unsigned long long>(c, B_SMALL, 64);
+    if (!sm) return PD_ENOMEM;
+    PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, sizeof(unsigned long long), st));
+    k_check_nodes<<<grid_for(N, 256), 256, 0, st>>>(nodes.morton, nodes.X, nodes.Y, nodes.cntA, nodes.cntB, N, sm);
+    PD_TRY_CUDA(c, cudaGetLastError());
+    PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    if (c->h_small[0])
+        return fail(c, PD_EINVAL,
+                    "nodes need strictly increasing Morton codes, |X|,|Y| < 2^30 and non-negative multiplicities");
+    return PD_OK;
+}
+
+__global__ void k_merge_diag(const int64_t* __restrict__ rp, const int64_t* __restrict__ sup, int64_t N, int64_t m,
+                             int64_t* __restrict__ mrp, int64_t* __restrict__ msup) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= N) mrp[i] = rp[i];
+    if (i == N + 1) mrp[N + 1] = m - 1;
+    if (i < N) msup[i] = sup[i];
+    if (i == N) msup[N] = sup[N] + sup[N + 1];
+}
+
+// Network of nodes 0..N-1 plus one diagonal node N: rows 0..N-1 unchanged
+// (their arcs to ā now point to N), row N = b̄'s row without its last arc
+// b̄ -> ā (ā = N is the largest head of b̄'s row and ā's own row is empty).
+pd_status merge_diagonal(Ctx* c, const pd_network& net, int64_t N, pd_network* out, cudaStream_t st) {
+    int64_t* mrp = bufT<int64_t>(c, B_M_ROWPTR, N + 2);
+    int64_t* msup = bufT<int64_t>(c, B_M_SUPPLY, N + 1);
+    if (!mrp || !msup) return PD_ENOMEM;
+    k_merge_diag<<<grid_for(N + 2, 256), 256, 0, st>>>(net.row_ptr, net.supply, N, net.n_arcs, mrp, msup);
+    PD_TRY_CUDA(c, cudaGetLastError());
+    out->n_nodes = N + 1;
+    out->n_arcs = net.n_arcs - 1;
+    out->row_ptr = mrp;
+    out->head = net.head;
+    out->cost = net.cost;
+    out->supply = msup;
+    return PD_OK;
+}
+
+pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* out, float* ms_tree,
+                        float* ms_wspd, float* ms_csr, cudaStream_t st) {
+    int64_t N = nodes.n_nodes;
+    if (N >= (int64_t(1) << 31) - 4) return fail(c, PD_ECAPACITY, "more than 2^31 - 4 condensed nodes");
+    if (s < 1) return fail(c, PD_EINVAL, "WSPD parameter s must be >= 1");
+    cudaEvent_t ev[4];
+    for (int q = 0; q < 4; q++) PD_TRY_CUDA(c, cudaEventCreate(&ev[q]));
+    PD_TRY_CUDA(c, cudaEventRecord(ev[0], st));
+    int64_t M = N > 1 ? N - 1 : 1;
+    int32_t* left = bufT<int32_t>(c, B_T_LEFT, M);
+    int32_t* right = bufT<int32_t>(c, B_T_RIGHT, M);
+    int4* bb = bufT<int4>(c, B_T_BB, M);
+    int32_t* rep = bufT<int32_t>(c, B_T_REP, M);
+    int32_t* par_int = bufT<int32_t>(c, B_T_PARENT, M);
+    int32_t* par_leaf = bufT<int32_t>(c, B_T_LPARENT, N);
+    int32_t* visit = bufT<int32_t>(c, B_T_VISIT, M);
+    unsigned long long* cnts = bufT<unsigned long long>(c, B_SMALL, 64);
+    if (!left || !right || !bb || !rep || !par_int || !par_leaf || !visit || !cnts) return PD_ENOMEM;
+    if (N >= 2) {
+        k_karras<<<grid_for(N - 1, 256), 256, 0, st>>>(nodes.morton, N, left, right, par_int, par_leaf);
+        PD_TRY_CUDA(c, cudaMemsetAsync(visit, 0, sizeof(int32_t) * M, st));
+        k_bbox<<<grid_for(N, 256), 256, 0, st>>>(N, nodes.X, nodes.Y, left, right, par_int, par_leaf, bb, rep, visit);
+        PD_TRY_CUDA(c, cudaGetLastError());
+    }
+    PD_TRY_CUDA(c, cudaEventRecord(ev[1], st));
+
+    int hb = bits_for((uint64_t)(N + 2));
+    int kb = 2 * hb;
+    uint64_t sent = (kb >= 64) ? ~0ull : ((1ull << kb) - 1);
+    // WSPD frontier, one level at a time
+    int64_t nf = N >= 2 ? N - 1 : 0;
+    int64_t fcap = nf > 0 ? nf : 1;
+    int2* F = bufT<int2>(c, B_F0, fcap);
+    if (!F) return PD_ENOMEM;
+    if (nf > 0) k_frontier_init<<<grid_for(nf, 256), 256, 0, st>>>(N, left, right, F);
+    int64_t narcs = 0;
+    int64_t acap = 0;
+    uint64_t* arcs = nullptr;
+    int fb = 0;
+    int64_t* h = c->h_small;
+    while (nf > 0) {
+        int64_t* flag = bufT<int64_t>(c, B_WSFLAG, nf);
+        int64_t* off = bufT<int64_t>(c, B_WSOFF, nf);
+        if (!flag || !off) return PD_ENOMEM;
+        k_ws_classify<<<grid_for(nf, 256), 256, 0, st>>>(F, nf, nodes.X, nodes.Y, bb, rep, left, right, s, flag, off);
+        PD_TRY(scan_i64(c, off, off, nf, (int64_t*)cnts + 8, st));
+        PD_TRY_CUDA(c, cudaMemcpyAsync(h, (int64_t*)cnts + 8, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+        int64_t nws = h[0];
+        int64_t need = narcs + 2 * nws + 2 * N + 1;
+        if (need > acap) {
+            // grow the arc buffer, keeping what is there
+            int64_t ncap = need + need / 2 + 1024;
+            uint64_t* tmp = bufT<uint64_t>(c, B_ARCKEY2, ncap);
+            if (!tmp) return PD_ENOMEM;
+            if (narcs) PD_TRY_CUDA(c, cudaMemcpyAsync(tmp, arcs, sizeof(uint64_t) * narcs, cudaMemcpyDeviceToDevice, st));
+            uint64_t* na = bufT<uint64_t>(c, B_ARCKEY, ncap);
+            if (!na) return PD_ENOMEM;
+            if (narcs) PD_TRY_CUDA(c, cudaMemcpyAsync(na, tmp, sizeof(uint64_t) * narcs, cudaMemcpyDeviceToDevice, st));
+            arcs = na;
+            acap = ncap;
+        }
+        int64_t nn = 2 * (nf - nws);
+        int2* Fn = bufT<int2>(c, fb ? B_F0 : B_F1, nn > 0 ? nn : 1);
+        if (!Fn) return PD_ENOMEM;
+        // F may have moved if its buffer grew: it did not (only Fn's buffer is resized here)
+        k_ws_expand<<<grid_for(nf, 256), 256, 0, st>>>(F, nf, flag, off, nodes.X, nodes.Y, bb, rep, left, right, hb,
+                                                        arcs + narcs, Fn);
+        PD_TRY_CUDA(c, cudaGetLastError());
+        narcs += 2 * nws;
+        nf = nn;
+        F = Fn;
+        fb ^= 1;
+    }
+    PD_TRY_CUDA(c, cudaEventRecord(ev[2], st));
+    if (!arcs) {
+        acap = 2 * N + 1;
+        arcs = bufT<uint64_t>(c, B_ARCKEY, acap);
+        if (!arcs) return PD_ENOMEM;
+    }
+    // diagonal arcs + masses
+    PD_TRY_CUDA(c, cudaMemsetAsync(cnts, 0, 8 * sizeof(unsigned long long), st));
+    k_diag_arcs<<<grid_for(N + 1, 256), 256, 0, st>>>(N, nodes.cntA, nodes.cntB, hb, sent, arcs + narcs, cnts);
+    k_mass<<<grid_for(N, 256), 256, 0, st>>>(N, nodes.cntA, nodes.cntB, cnts);
+    PD_TRY_CUDA(c, cudaGetLastError());
+    PD_TRY_CUDA(c, cudaMemcpyAsync(h, cnts, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    int64_t ntot = narcs + 2 * N + 1;
+    uint64_t* alt = bufT<uint64_t>(c, B_ARCKEY2, ntot);
+    if (!alt) return PD_ENOMEM;
+    PD_TRY(sort_u64(c, arcs, alt, nullptr, nullptr, ntot, kb, st));
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    int64_t na = h[0], nb = h[1], FA = h[2], FB = h[3];
+    int64_t m = narcs + na + nb + 1;
+    int64_t nrows = N + 2;
+    out->n_nodes = nrows;
+    out->n_arcs = m;
+    out->row_ptr = bufT<int64_t>(c, B_ROWPTR, nrows + 1);
+    out->head = bufT<int32_t>(c, B_HEAD, m);
+    out->cost = bufT<int64_t>(c, B_COST, m);
+    out->supply = bufT<int64_t>(c, B_SUPPLY, nrows);
+    if (!out->row_ptr || !out->head || !out->cost || !out->supply) return PD_ENOMEM;
+    k_row_ptr<<<grid_for(m, 256), 256, 0, st>>>(arcs, m, hb, nrows, out->row_ptr);
+    k_head_cost<<<grid_for(m, 256), 256, 0, st>>>(arcs, m, hb, N, nodes.X, nodes.Y, out->head, out->cost);
+    k_supply<<<grid_for(N + 2, 256), 256, 0, st>>>(N, nodes.cntA, nodes.cntB, FA, FB, out->supply);
+    PD_TRY_CUDA(c, cudaGetLastError());
+    PD_TRY_CUDA(c, cudaEventRecord(ev[3], st));
+    PD_TRY_CUDA(c, cudaEventSynchronize(ev[3]));
+    if (ms_tree) cudaEventElapsedTime(ms_tree, ev[0], ev[1]);
+    if (ms_wspd) cudaEventElapsedTime(ms_wspd, ev[1], ev[2]);
+    if (ms_csr) cudaEventElapsedTime(ms_csr, ev[2], ev[3]);
+    for (int q = 0; q < 4; q++) cudaEventDestroy(ev[q]);
+    return PD_OK;
+}
+
+}  // namespace pd

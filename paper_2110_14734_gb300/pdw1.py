@@ -1,0 +1,255 @@
+"""Thin Python binding of the libpdw1 C ABI (include/pdw1.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+PyTorch supplies device memory and the current stream.  If the compiled
+library is missing this module raises at import: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpdw1.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libpdw1.so is not built (%s); run paper_2110_14734_gb300/build.py" % LIB_PATH)
+
+_lib = C.CDLL(LIB_PATH)
+
+PD_OK, PD_EINVAL, PD_ENOMEM, PD_ECUDA, PD_ETIMEOUT, PD_ECAPACITY, PD_EOVERFLOW, PD_EINFEASIBLE = range(8)
+STATUS_NAMES = ["PD_OK", "PD_EINVAL", "PD_ENOMEM", "PD_ECUDA", "PD_ETIMEOUT", "PD_ECAPACITY", "PD_EOVERFLOW",
+                "PD_EINFEASIBLE"]
+PD_F32, PD_U8 = 0, 1
+
+
+class pd_diagram(C.Structure):
+    _fields_ = [("bd", C.c_void_p), ("n", C.c_int64), ("dtype", C.c_int32), ("on_host", C.c_int32)]
+
+
+class pd_opts(C.Structure):
+    _fields_ = [("coord_shift", C.c_int32), ("s_override", C.c_int32), ("condense", C.c_int32),
+                ("perturb", C.c_int32), ("seed", C.c_uint64), ("alpha", C.c_int32), ("verify", C.c_int32),
+                ("max_rounds", C.c_int64), ("time_limit_ms", C.c_int64), ("update_every", C.c_int64),
+                ("seq_threshold", C.c_int32), ("reserved", C.c_int32)]
+
+
+class pd_nodes(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("X", C.c_void_p), ("Y", C.c_void_p), ("cntA", C.c_void_p),
+                ("cntB", C.c_void_p), ("morton", C.c_void_p)]
+
+
+class pd_network(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_arcs", C.c_int64), ("row_ptr", C.c_void_p), ("head", C.c_void_p),
+                ("cost", C.c_void_p), ("supply", C.c_void_p)]
+
+
+class pd_result(C.Structure):
+    _fields_ = [("w1", C.c_double), ("opt_quanta", C.c_int64), ("rwmd_quanta", C.c_int64),
+                ("rwmd_A", C.c_int64), ("rwmd_B", C.c_int64), ("slack_quanta", C.c_int64),
+                ("mass_A", C.c_int64), ("mass_B", C.c_int64), ("s", C.c_int32), ("coord_shift", C.c_int32),
+                ("delta", C.c_double), ("cell_quanta", C.c_int64), ("shift_quanta", C.c_int64),
+                ("n_nodes", C.c_int64), ("n_arcs", C.c_int64), ("phases", C.c_int32), ("verified", C.c_int32),
+                ("rounds", C.c_int64), ("pushes", C.c_int64), ("relabels", C.c_int64),
+                ("repair_passes", C.c_int64), ("price_updates", C.c_int64), ("update_passes", C.c_int64),
+                ("stage_ms", C.c_float * 8)]
+
+    def to_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "stage_ms"}
+        d["stage_ms"] = list(self.stage_ms)
+        return d
+
+
+_lib.pd_create.restype = C.c_int
+_lib.pd_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_size_t]
+_lib.pd_destroy.restype = None
+_lib.pd_destroy.argtypes = [C.c_void_p]
+_lib.pd_last_error.restype = C.c_char_p
+_lib.pd_last_error.argtypes = [C.c_void_p]
+_lib.pd_opts_default.restype = None
+_lib.pd_opts_default.argtypes = [C.POINTER(pd_opts)]
+_lib.pd_condense.restype = C.c_int
+_lib.pd_condense.argtypes = [C.c_void_p, pd_diagram, pd_diagram, C.c_int64, C.c_int64, C.POINTER(pd_opts),
+                             C.POINTER(pd_nodes), C.c_void_p]
+_lib.pd_rwmd_lower_bound.restype = C.c_int
+_lib.pd_rwmd_lower_bound.argtypes = [C.c_void_p, pd_diagram, pd_diagram, C.POINTER(pd_opts),
+                                     C.POINTER(C.c_int64), C.c_void_p]
+_lib.pd_wspd_sparsify.restype = C.c_int
+_lib.pd_wspd_sparsify.argtypes = [C.c_void_p, C.POINTER(pd_nodes), C.c_int32, C.POINTER(pd_network), C.c_void_p]
+_lib.pd_mcf_solve.restype = C.c_int
+_lib.pd_mcf_solve.argtypes = [C.c_void_p, C.POINTER(pd_network), C.POINTER(pd_opts), C.POINTER(C.c_int64),
+                              C.POINTER(pd_result), C.c_void_p]
+_lib.pd_w1_approx.restype = C.c_int
+_lib.pd_w1_approx.argtypes = [C.c_void_p, pd_diagram, pd_diagram, C.c_double, C.POINTER(pd_opts),
+                              C.POINTER(pd_result), C.c_void_p]
+
+_cudart = None
+
+
+def _memcpy_d2d(dst: int, src: int, nbytes: int, stream: int):
+    """cudaMemcpyAsync from the CUDA runtime the library itself links."""
+    global _cudart
+    if _cudart is None:
+        for name in ("libcudart.so.13", "libcudart.so"):
+            try:
+                _cudart = C.CDLL(name)
+                break
+            except OSError:
+                continue
+        if _cudart is None:
+            raise OSError("libcudart not found")
+        _cudart.cudaMemcpyAsync.restype = C.c_int
+        _cudart.cudaMemcpyAsync.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p]
+    if nbytes:
+        r = _cudart.cudaMemcpyAsync(C.c_void_p(dst), C.c_void_p(src), nbytes, 3, C.c_void_p(stream))
+        if r != 0:
+            raise RuntimeError("cudaMemcpyAsync failed: %d" % r)
+
+
+class PDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status, msg))
+        self.status = status
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def opts(**kw) -> pd_opts:
+    o = pd_opts()
+    _lib.pd_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def diagram(bd) -> tuple:
+    """(pd_diagram, keepalive) from a torch tensor (cuda or cpu) or numpy array
+    of shape (n, 2), float32 or uint8."""
+    if isinstance(bd, np.ndarray):
+        bd = torch.from_numpy(np.ascontiguousarray(bd))
+    if bd.dtype == torch.float32:
+        dt = PD_F32
+    elif bd.dtype == torch.uint8:
+        dt = PD_U8
+    else:
+        raise TypeError("diagram must be float32 or uint8")
+    bd = bd.contiguous()
+    n = bd.shape[0] if bd.dim() == 2 and bd.numel() else 0
+    d = pd_diagram(C.c_void_p(bd.data_ptr() if n else 0), n, dt, 0 if bd.is_cuda else 1)
+    return d, bd
+
+
+class Context:
+    """Owns a pd_ctx (device buffers live until close())."""
+
+    def __init__(self, device: int = 0, arena_bytes: int = 0):
+        self.ptr = C.c_void_p()
+        self.device = device
+        st = _lib.pd_create(C.byref(self.ptr), device, arena_bytes)
+        if st != PD_OK:
+            raise PDError(st, "pd_create failed")
+
+    def check(self, st):
+        if st != PD_OK:
+            raise PDError(st, _lib.pd_last_error(self.ptr).decode())
+
+    def close(self):
+        if self.ptr:
+            _lib.pd_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pd_create(device: int = 0, arena_bytes: int = 0) -> Context:
+    return Context(device, arena_bytes)
+
+
+def _copy_out(ptr, n, dtype, device, stream):
+    t = torch.empty(max(n, 0), dtype=dtype, device=device)
+    if n > 0:
+        _memcpy_d2d(t.data_ptr(), ptr, n * t.element_size(), stream)
+    return t
+
+
+def pd_condense(ctx: Context, A, B, cell_quanta: int = 1, shift_quanta: int = 0, o: pd_opts | None = None,
+                stream=None) -> dict:
+    """Condensed nodes (copied into torch tensors on the context's device)."""
+    da, ka = diagram(A)
+    db, kb = diagram(B)
+    out = pd_nodes()
+    s = _stream(stream)
+    ctx.check(_lib.pd_condense(ctx.ptr, da, db, cell_quanta, shift_quanta, C.byref(o) if o else None,
+                               C.byref(out), C.c_void_p(s)))
+    dev = torch.device("cuda", ctx.device)
+    N = out.n_nodes
+    res = dict(n_nodes=N, X=_copy_out(out.X, N, torch.int32, dev, s), Y=_copy_out(out.Y, N, torch.int32, dev, s),
+               cntA=_copy_out(out.cntA, N, torch.int64, dev, s), cntB=_copy_out(out.cntB, N, torch.int64, dev, s),
+               morton=_copy_out(out.morton, N, torch.int64, dev, s))
+    return res
+
+
+def pd_rwmd_lower_bound(ctx: Context, A, B, o: pd_opts | None = None, stream=None):
+    da, ka = diagram(A)
+    db, kb = diagram(B)
+    out = (C.c_int64 * 3)()
+    ctx.check(_lib.pd_rwmd_lower_bound(ctx.ptr, da, db, C.byref(o) if o else None, out,
+                                       C.c_void_p(_stream(stream))))
+    return int(out[0]), int(out[1]), int(out[2])
+
+
+def pd_wspd_sparsify(ctx: Context, nodes: dict, s: int, stream=None) -> dict:
+    """nodes: dict of cuda tensors X, Y (int32), cntA, cntB (int64), morton (int64)."""
+    N = int(nodes["X"].numel())
+    keep = [nodes[k].contiguous() for k in ("X", "Y", "cntA", "cntB", "morton")]
+    nd = pd_nodes(N, *[C.c_void_p(t.data_ptr() if N else 0) for t in keep])
+    out = pd_network()
+    st = _stream(stream)
+    ctx.check(_lib.pd_wspd_sparsify(ctx.ptr, C.byref(nd), int(s), C.byref(out), C.c_void_p(st)))
+    dev = torch.device("cuda", ctx.device)
+    n, m = out.n_nodes, out.n_arcs
+    return dict(n_nodes=n, n_arcs=m, row_ptr=_copy_out(out.row_ptr, n + 1, torch.int64, dev, st),
+                head=_copy_out(out.head, m, torch.int32, dev, st), cost=_copy_out(out.cost, m, torch.int64, dev, st),
+                supply=_copy_out(out.supply, n, torch.int64, dev, st))
+
+
+def pd_mcf_solve(ctx: Context, net: dict, o: pd_opts | None = None, stream=None):
+    """net: dict of cuda tensors row_ptr, head, cost, supply (int64 / int32).
+    Returns (OPT, stats dict)."""
+    keep = [net["row_ptr"].contiguous(), net["head"].contiguous(), net["cost"].contiguous(),
+            net["supply"].contiguous()]
+    n = int(keep[0].numel()) - 1
+    m = int(keep[1].numel())
+    nw = pd_network(n, m, *[C.c_void_p(t.data_ptr()) for t in keep])
+    opt = C.c_int64()
+    res = pd_result()
+    ctx.check(_lib.pd_mcf_solve(ctx.ptr, C.byref(nw), C.byref(o) if o else None, C.byref(opt), C.byref(res),
+                                C.c_void_p(_stream(stream))))
+    return int(opt.value), res.to_dict()
+
+
+def pd_w1_approx(ctx: Context, A, B, eps: float, o: pd_opts | None = None, stream=None) -> dict:
+    da, ka = diagram(A)
+    db, kb = diagram(B)
+    res = pd_result()
+    ctx.check(_lib.pd_w1_approx(ctx.ptr, da, db, float(eps), C.byref(o) if o else None, C.byref(res),
+                                C.c_void_p(_stream(stream))))
+    return res.to_dict()
+
+
+def pd_w1_approx_raw(ctx: Context, da: pd_diagram, db: pd_diagram, eps: float, o, res: pd_result, stream: int):
+    """Allocation-free call for timing loops: prebuilt structs, result in res."""
+    return _lib.pd_w1_approx(ctx.ptr, da, db, eps, C.byref(o) if o else None, C.byref(res), C.c_void_p(stream))

@@ -1,0 +1,276 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer results must be bit-exact: condensed nodes and multiplicities, RWMD,
+the CSR network (rows, heads, costs, supplies) and the optimum of the sparse
+network.  Runs on a GPU only.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2110_14734_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pd():
+    from paper_2110_14734_gb300 import build
+    build.build()
+    from paper_2110_14734_gb300 import pdw1
+    return pdw1
+
+
+@pytest.fixture(scope="module")
+def ctx(pd):
+    c = pd.pd_create(0)
+    yield c
+    c.close()
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _np(t):
+    return t.cpu().numpy()
+
+
+def _oracle_hats(A, B, dtype, k):
+    XA, YA = oracle.quantize(A, dtype, k)
+    XB, YB = oracle.quantize(B, dtype, k)
+    return oracle.condense0(XA, YA), oracle.condense0(XB, YB)
+
+
+def _assert_nodes(got, exp):
+    assert got["n_nodes"] == len(exp["X"])
+    np.testing.assert_array_equal(_np(got["X"]), exp["X"])
+    np.testing.assert_array_equal(_np(got["Y"]), exp["Y"])
+    np.testing.assert_array_equal(_np(got["cntA"]), exp["cntA"])
+    np.testing.assert_array_equal(_np(got["cntB"]), exp["cntB"])
+    np.testing.assert_array_equal(_np(got["morton"]).view(np.uint64), exp["code"])
+
+
+PAIRS = {
+    "uniform2k": lambda: (synth.uniform_exp(2000, 1000), synth.uniform_exp(2000, 1001), "f32"),
+    "lowerstar20k": lambda: (synth.lowerstar_u8(20000, 1000), synth.lowerstar_u8(20000, 1001), "u8"),
+    "mixture5k": lambda: (synth.mixture_f32(5000, 7), synth.mixture_f32(4000, 8), "f32"),
+    "ragged": lambda: (synth.uniform_exp(4097, 11), synth.uniform_exp(33, 12), "f32"),
+}
+
+
+@pytest.mark.parametrize("name", list(PAIRS))
+def test_condense_matches_oracle(pd, ctx, name):
+    A, B, dt = PAIRS[name]()
+    k = oracle.default_shift(dt)
+    Ah, Bh = _oracle_hats(A, B, dt, k)
+    for (G, P, seed) in [(1, 0, 0), (4096, 0, 0), (5000, 20, 3), (77777, 300, 12345)]:
+        got = pd.pd_condense(ctx, _cuda(A), _cuda(B), G, P, pd.opts(seed=seed))
+        exp = oracle.condense_delta(Ah, Bh, G, P, seed)
+        _assert_nodes(got, exp)
+
+
+def test_condense_host_inputs_and_one_sided(pd, ctx):
+    A = synth.uniform_exp(3000, 21)
+    E = np.zeros((0, 2), np.float32)
+    Ah, Bh = _oracle_hats(A, E, "f32", 20)
+    got = pd.pd_condense(ctx, A, E, 1, 0)  # numpy -> host pointers
+    _assert_nodes(got, oracle.condense_delta(Ah, Bh, 1, 0, 0))
+    got = pd.pd_condense(ctx, _cuda(E), _cuda(A), 1, 0)
+    _assert_nodes(got, oracle.condense_delta(Bh, Ah, 1, 0, 0))
+    got = pd.pd_condense(ctx, _cuda(E), _cuda(E), 1, 0)
+    assert got["n_nodes"] == 0
+    D = np.array([[0.25, 0.25], [0.5, 0.5]], np.float32)  # only diagonal points
+    assert pd.pd_condense(ctx, _cuda(D), _cuda(D), 1, 0)["n_nodes"] == 0
+
+
+def test_invalid_inputs_are_rejected(pd, ctx):
+    A = synth.uniform_exp(100, 1)
+    bad = A.copy()
+    bad[5, 1] = np.nan
+    with pytest.raises(pd.PDError) as e:
+        pd.pd_condense(ctx, _cuda(bad), _cuda(A), 1, 0)
+    assert e.value.status == pd.PD_EINVAL
+    big = A.copy()
+    big[3, 0] = 1000.0  # 1000 * 2^20 >= 2^29
+    with pytest.raises(pd.PDError):
+        pd.pd_rwmd_lower_bound(ctx, _cuda(big), _cuda(A))
+    with pytest.raises(pd.PDError):
+        pd.pd_condense(ctx, _cuda(A), _cuda(A), 10, 5)  # 2P >= G
+    # the context is still usable after errors
+    assert pd.pd_rwmd_lower_bound(ctx, _cuda(A), _cuda(A)) == (0, 0, 0)
+
+
+@pytest.mark.parametrize("name", list(PAIRS))
+def test_rwmd_matches_oracle(pd, ctx, name):
+    A, B, dt = PAIRS[name]()
+    Ah, Bh = _oracle_hats(A, B, dt, oracle.default_shift(dt))
+    assert pd.pd_rwmd_lower_bound(ctx, _cuda(A), _cuda(B)) == oracle.rwmd(Ah, Bh)
+    E = np.zeros((0, 2), A.dtype)
+    Eh = (np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int64))
+    assert pd.pd_rwmd_lower_bound(ctx, _cuda(A), _cuda(E)) == oracle.rwmd(Ah, Eh)
+
+
+def _upload_nodes(nodes):
+    return dict(X=_cuda(nodes["X"]), Y=_cuda(nodes["Y"]), cntA=_cuda(nodes["cntA"]), cntB=_cuda(nodes["cntB"]),
+                morton=_cuda(nodes["code"].view(np.int64)))
+
+
+def _assert_network(got, exp):
+    np.testing.assert_array_equal(_np(got["row_ptr"]), exp["row_ptr"])
+    np.testing.assert_array_equal(_np(got["head"]), exp["head"])
+    np.testing.assert_array_equal(_np(got["cost"]), exp["cost"])
+    np.testing.assert_array_equal(_np(got["supply"]), exp["supply"])
+
+
+@pytest.mark.parametrize("s", [1, 2, 5, 13, 40, 167])
+def test_wspd_network_matches_oracle(pd, ctx, s):
+    A, B = synth.uniform_exp(1500, 31), synth.uniform_exp(1400, 32)
+    Ah, Bh = _oracle_hats(A, B, "f32", 20)
+    nodes = oracle.condense_delta(Ah, Bh, 600, 2, 9)
+    tree = oracle.radix_tree(nodes)
+    exp = oracle.build_network(nodes, *oracle.wspd(nodes, tree, s))
+    got = pd.pd_wspd_sparsify(ctx, _upload_nodes(nodes), s)
+    _assert_network(got, exp)
+
+
+def test_wspd_network_clustered_and_tiny(pd, ctx):
+    rng = np.random.default_rng(5)
+    ctr = rng.integers(0, 2**24, (10, 2))
+    pts = np.concatenate([c + rng.integers(0, 3000, (200, 2)) for c in ctr])
+    pts = np.unique(pts, axis=0)
+    Xs, Ys = pts[:, 0].astype(np.int32), pts[:, 1].astype(np.int32)
+    cnt = rng.integers(1, 4, len(Xs)).astype(np.int64)
+    half = len(Xs) // 2
+    Ah = (Xs[:half], Ys[:half], cnt[:half])
+    Bh = (Xs[half:], Ys[half:], cnt[half:])
+    empty = (np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int64))
+    for nodes in [oracle.condense_delta(Ah, Bh, 1, 0, 0),
+                  oracle.condense_delta((Xs[:1], Ys[:1], cnt[:1]), empty, 1, 0, 0),
+                  oracle.condense_delta((Xs[:2], Ys[:2], cnt[:2]), (Xs[2:3], Ys[2:3], cnt[2:3]), 1, 0, 0)]:
+        for s in (3, 20):
+            tree = oracle.radix_tree(nodes)
+            exp = oracle.build_network(nodes, *oracle.wspd(nodes, tree, s))
+            got = pd.pd_wspd_sparsify(ctx, _upload_nodes(nodes), s)
+            _assert_network(got, exp)
+
+
+def _random_network(rng, n, extra):
+    arcs = set()
+    for u in range(n - 1):
+        arcs.add((u, u + 1))
+        arcs.add((u + 1, u))
+    for _ in range(extra):
+        u, v = (int(x) for x in rng.integers(0, n, 2))
+        if u != v:
+            arcs.add((u, v))
+    arcs = sorted(arcs)
+    t = np.array([a[0] for a in arcs], np.int64)
+    h = np.array([a[1] for a in arcs], np.int32)
+    cost = {}
+    for (u, v) in arcs:  # antiparallel pairs: sometimes equal cost, sometimes not
+        if (v, u) in cost and rng.random() < 0.5:
+            cost[(u, v)] = cost[(v, u)]
+        else:
+            cost[(u, v)] = int(rng.integers(0, 1000))
+    c = np.array([cost[a] for a in arcs], np.int64)
+    rp = np.zeros(n + 1, np.int64)
+    np.add.at(rp, t + 1, 1)
+    rp = np.cumsum(rp)
+    sup = rng.integers(-20, 21, n).astype(np.int64)
+    sup[-1] -= sup.sum()
+    return dict(row_ptr=rp, head=h, cost=c, supply=sup, tails=t.astype(np.int32))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_mcf_random_networks_match_network_simplex(pd, ctx, seed):
+    rng = np.random.default_rng(100 + seed)
+    net = _random_network(rng, int(rng.integers(5, 300)), int(rng.integers(10, 3000)))
+    st, opt, flow, pot = oracle.mcf_arcs(len(net["supply"]), net["tails"], net["head"], net["cost"], net["supply"])
+    assert st == 0
+    for alpha in (2, 8, 16):
+        got, stats = pd.pd_mcf_solve(ctx, {k: _cuda(v) for k, v in net.items() if k != "tails"},
+                                     pd.opts(alpha=alpha, verify=1))
+        assert got == opt and stats["verified"] == 1
+
+
+@pytest.mark.parametrize("name", ["uniform2k", "mixture5k", "ragged"])
+def test_mcf_on_w1_networks(pd, ctx, name):
+    A, B, dt = PAIRS[name]()
+    r = oracle.w1_approx(A, B, dt, eps=0.5)
+    net = {k: _cuda(r["net"][k]) for k in ("row_ptr", "head", "cost", "supply")}
+    got, stats = pd.pd_mcf_solve(ctx, net, pd.opts(verify=1))
+    assert got == r["opt"] and stats["verified"] == 1
+
+
+def _check_w1(pd, ctx, A, B, dt, eps, **kw):
+    r = oracle.w1_approx(A, B, dt, eps=eps, **{k: v for k, v in kw.items() if k in ("k", "s_override", "perturb",
+                                                                                     "seed", "condense")})
+    o = pd.opts(verify=1, s_override=kw.get("s_override", 0), perturb=int(kw.get("perturb", True)),
+                seed=kw.get("seed", 0), condense=int(kw.get("condense", True)),
+                coord_shift=kw.get("k", -1) if kw.get("k") is not None else -1)
+    g = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), eps, o)
+    assert (g["rwmd_A"], g["rwmd_B"]) == (r["LA"], r["LB"])
+    assert g["s"] == r["s"] and g["cell_quanta"] == r["G"] and g["shift_quanta"] == r["P"]
+    assert g["delta"] == r["delta"]
+    assert g["n_nodes"] == len(r["nodes"]["X"]) and g["n_arcs"] == int(r["net"]["row_ptr"][-1])
+    assert g["opt_quanta"] == r["opt"], (g["opt_quanta"], r["opt"])
+    assert g["verified"] == 1
+    assert g["w1"] == math.ldexp(r["opt"], -r["k"])
+    return g, r
+
+
+@pytest.mark.parametrize("eps", [0.1, 0.5, 2.0])
+def test_w1_approx_uniform2k(pd, ctx, eps):
+    A, B, dt = PAIRS["uniform2k"]()
+    g, r = _check_w1(pd, ctx, A, B, dt, eps)
+    # (1 +- eps) band against the exact FP64 W1 (Corollary, approximation bound)
+    w = oracle.w1_exact(A.astype(np.float64), B.astype(np.float64))
+    q = 2.0 ** -20
+    slack = g["slack_quanta"] * q + (r["FA"] + r["FB"]) * q
+    assert (1 - eps) * w - slack <= g["w1"] <= (1 + eps) * w + slack
+
+
+@pytest.mark.parametrize("eps", [0.1, 0.05])
+def test_w1_approx_lowerstar_u8(pd, ctx, eps):
+    A, B = synth.lowerstar_u8(20000, 1000), synth.lowerstar_u8(20000, 1001)
+    _check_w1(pd, ctx, A, B, "u8", eps)
+
+
+def test_w1_approx_edge_cases(pd, ctx):
+    A = synth.uniform_exp(500, 41)
+    B = synth.uniform_exp(450, 42)
+    E = np.zeros((0, 2), np.float32)
+    _check_w1(pd, ctx, A, E, "f32", 0.1)
+    g, r = _check_w1(pd, ctx, A, E, "f32", 0.1, condense=False)  # one side empty: all mass to the diagonal
+    assert g["opt_quanta"] == g["rwmd_quanta"]
+    g, _ = _check_w1(pd, ctx, A, A, "f32", 0.1)
+    assert g["opt_quanta"] == 0
+    g1, _ = _check_w1(pd, ctx, A, B, "f32", 0.1, seed=7)
+    g2, _ = _check_w1(pd, ctx, B, A, "f32", 0.1, seed=7)
+    assert g1["opt_quanta"] == g2["opt_quanta"]
+    _check_w1(pd, ctx, A, B, "f32", 0.1, s_override=1)
+    _check_w1(pd, ctx, A, B, "f32", 0.1, s_override=3, perturb=False)
+    _check_w1(pd, ctx, A, B, "f32", 0.1, condense=False)
+    _check_w1(pd, ctx, A, B, "f32", 0.1, k=12)
+    g = pd.pd_w1_approx(ctx, _cuda(E), _cuda(E), 0.1)
+    assert g["opt_quanta"] == 0 and g["n_nodes"] == 0
+
+
+def test_solver_round_cap_returns_timeout(pd, ctx):
+    A, B, dt = PAIRS["uniform2k"]()
+    with pytest.raises(pd.PDError) as e:
+        pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.1, pd.opts(max_rounds=3))
+    assert e.value.status == pd.PD_ETIMEOUT
+    # and the context keeps working
+    assert pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.5)["opt_quanta"] > 0
+
+
+def test_w1_approx_full_size_lowerstar_100k(pd, ctx):
+    """The benchmark workload (100k + 100k uint8 points, eps = 0.05), exact
+    parity of every integer result with the oracle."""
+    A, B = synth.lowerstar_u8(100000, 1000), synth.lowerstar_u8(100000, 1001)
+    _check_w1(pd, ctx, A, B, "u8", 0.05)

@@ -549,3 +549,20 @@ def test_pipeline_empty_and_one_sided(orc):
     r0 = orc.w1_approx(A, E, "f32", eps=0.1, condense=False)
     assert r0["opt"] == closed
     assert orc.w1_approx(E, E, "f32", eps=0.1)["opt"] == 0
+
+
+@pytest.mark.parametrize("seed,eps", [(400, 0.1), (402, 0.5), (404, 2.0)])
+def test_contracting_the_zero_cost_diagonal_arc_keeps_the_optimum(orc, seed, eps):
+    """The GPU solver merges ā and b̄ (the zero-cost arc b̄ -> ā contracted);
+    the optimum of the paper's network must be unchanged."""
+    A, B = synth.uniform_exp(300, seed), synth.uniform_exp(260, seed + 1)
+    r = orc.w1_approx(A, B, "f32", eps=eps)
+    net = r["net"]
+    N = net["n_nodes"]
+    rp, head, cost, sup = net["row_ptr"], net["head"], net["cost"], net["supply"]
+    tails = np.repeat(np.arange(N + 2), np.diff(rp)).astype(np.int32)
+    keep = ~((tails == N + 1) & (head == N))        # drop b̄ -> ā
+    t = np.where(tails[keep] == N + 1, N, tails[keep]).astype(np.int32)  # b̄ becomes the merged node
+    msup = np.concatenate([sup[:N], [sup[N] + sup[N + 1]]])
+    st, opt, flow, pot = orc.mcf_arcs(N + 1, t, head[keep], cost[keep], msup)
+    assert st == 0 and opt == r["opt"]
