@@ -79,7 +79,10 @@ typedef struct {
     int64_t max_rounds;  /* solver watchdog: push/relabel rounds over all phases (0 = default) */
     int64_t time_limit_ms;  /* solver watchdog: device wall-clock limit of one solve (0 = 60000) */
     int64_t update_every;   /* relabels between global price updates (0 = number of nodes, -1 = never) */
-    int32_t seq_threshold;  /* at most this many active nodes: one block finishes them (-1 = default 64) */
+    int32_t seq_threshold;  /* cost scaling: at most this many active nodes, one block finishes them (-1 = 64) */
+    int32_t solver;         /* 0 = network simplex (default), 1 = cost scaling with push/relabel */
+    int64_t ns_block;       /* network simplex pricing block in arcs (0 = max(2048, sqrt(arcs))) */
+    int32_t ns_transport;   /* W1 only: 1 = try the transportation form with its certificate first (default) */
     int32_t reserved;
 } pd_opts;
 
@@ -134,6 +137,10 @@ typedef struct {
     int64_t repair_passes;  /* solver: price-repair passes */
     int64_t price_updates;  /* solver: global price updates */
     int64_t update_passes;  /* solver: relaxation passes of the global price updates */
+    int64_t pivots;         /* network simplex: pivots (all attempts) */
+    int64_t degenerate;     /* network simplex: pivots that moved no flow */
+    int32_t solve_method;   /* 0 cost scaling, 1 simplex on the sparse network, 2 transportation form + certificate */
+    int32_t cert_failures;  /* pairs of the transportation optimum missing from the sparse network */
     float stage_ms[8];      /* quantize+0-condense, RWMD, delta-condense, tree, WSPD, CSR, solve, total */
 } pd_result;
 

@@ -149,6 +149,9 @@ extern "C" void pd_opts_default(pd_opts* o) {
     o->time_limit_ms = 0;
     o->update_every = 0;
     o->seq_threshold = -1;
+    o->solver = 0;
+    o->ns_block = 0;
+    o->ns_transport = 1;
 }
 
 extern "C" pd_status pd_create(pd_ctx** out, int device, size_t arena_bytes) {
@@ -291,7 +294,10 @@ extern "C" pd_status pd_mcf_solve(pd_ctx* c, const pd_network* net, const pd_opt
     pd_opts o = resolve_opts(opts);
     PD_TRY(validate_network(c, *net, (cudaStream_t)stream));
     SolveStats ss;
-    PD_TRY(stage_solve(c, *net, o, &ss, (cudaStream_t)stream));
+    if (o.solver == 1)
+        PD_TRY(stage_solve(c, *net, o, &ss, (cudaStream_t)stream));
+    else
+        PD_TRY(ns_solve_network(c, *net, o, &ss, (cudaStream_t)stream));
     *opt_out = ss.opt;
     if (stats) {
         memset(stats, 0, sizeof(*stats));
@@ -304,6 +310,10 @@ extern "C" pd_status pd_mcf_solve(pd_ctx* c, const pd_network* net, const pd_opt
         stats->repair_passes = ss.repairs;
         stats->price_updates = ss.updates;
         stats->update_passes = ss.update_passes;
+        stats->pivots = ss.pivots;
+        stats->degenerate = ss.degenerate;
+        stats->solve_method = ss.method;
+        stats->cert_failures = (int32_t)ss.cert_failures;
         stats->verified = ss.verified;
         stats->n_nodes = net->n_nodes;
         stats->n_arcs = net->n_arcs;
@@ -358,7 +368,10 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
     pd_network mnet;
     PD_TRY(merge_diagonal(c, net, nodes.n_nodes, &mnet, st));
     SolveStats ss;
-    PD_TRY(stage_solve(c, mnet, o, &ss, st));
+    if (o.solver == 1)
+        PD_TRY(stage_solve(c, mnet, o, &ss, st));
+    else
+        PD_TRY(ns_solve_w1(c, nodes, net, mnet, o, &ss, st));
     PD_TRY_CUDA(c, cudaEventRecord(e6, st));
     PD_TRY_CUDA(c, cudaEventSynchronize(e6));
     float ms[4];
@@ -394,6 +407,10 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
     r.repair_passes = ss.repairs;
     r.price_updates = ss.updates;
     r.update_passes = ss.update_passes;
+    r.pivots = ss.pivots;
+    r.degenerate = ss.degenerate;
+    r.solve_method = ss.method;
+    r.cert_failures = (int32_t)ss.cert_failures;
     r.stage_ms[0] = ms[0];
     r.stage_ms[1] = ms[1];
     r.stage_ms[2] = ms[2];

@@ -25,6 +25,8 @@ enum Buf : int {
     B_S_E, B_S_P, B_S_D, B_S_CUR, B_S_RELAB, B_S_CTL, B_S_Q,
     B_RS_COUNTS, B_RS_PART, B_SCAN_PART,
     B_M_ROWPTR, B_M_SUPPLY,
+    B_NS_PI, B_NS_PARENT, B_NS_PRED, B_NS_DEPTH, B_NS_FLOW, B_NS_UP, B_NS_ORD, B_NS_POS, B_NS_SIZE, B_NS_TMP,
+    B_NS_PATH, B_NS_SEG, B_NS_INST, B_NS_COST, B_TR_S, B_TR_T, B_TR_SUP,
     B_SMALL,                        // small device scalars
     B_COUNT
 };
@@ -84,7 +86,13 @@ struct Hats {
 
 struct SolveStats {
     int64_t opt = 0, slack = 0, rounds = 0, pushes = 0, relabels = 0, repairs = 0, updates = 0, update_passes = 0;
-    int32_t phases = 0, verified = 0;
+    int64_t pivots = 0, degenerate = 0, cert_failures = 0;
+    int32_t phases = 0, verified = 0, method = 0;  // method: 0 cost scaling, 1 simplex on the network, 2 transport form
+};
+
+struct NSOut {
+    int64_t opt = 0, pivots = 0, degenerate = 0;
+    int32_t status = 0;
 };
 
 pd_status stage_condense0(Ctx* c, const DevDiag& A, const DevDiag& B, int k, Hats* out, cudaStream_t st);
@@ -98,6 +106,13 @@ pd_status stage_solve(Ctx* c, const pd_network& net, const pd_opts& o, SolveStat
 
 pd_status validate_nodes(Ctx* c, const pd_nodes& nodes, cudaStream_t st);
 pd_status validate_network(Ctx* c, const pd_network& net, cudaStream_t st);
+
+pd_status ns_solve_network(Ctx* c, const pd_network& net, const pd_opts& o, SolveStats* out, cudaStream_t st);
+pd_status ns_solve_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const pd_network& merged,
+                      const pd_opts& o, SolveStats* out, cudaStream_t st);
+__global__ void k_arc_tails(const int64_t* __restrict__ rp, int64_t n, int64_t m, int32_t* __restrict__ tail);
+__global__ void k_max_cost(const int64_t* __restrict__ cost, int64_t m, unsigned long long* __restrict__ out);
+__global__ void k_max_cost32(const int32_t* __restrict__ cost, int64_t m, unsigned long long* __restrict__ out);
 
 __global__ void k_row_ptr(const uint64_t* key, int64_t m, int hb, int64_t nrows, int64_t* row_ptr);
 

@@ -1,0 +1,698 @@
+// Primal network simplex for the uncapacitated min-cost flow, one CTA per
+// instance (the min-cost flow of the network-simplex section: block search
+// pivoting, run to optimality).
+//
+// GPU layout.  Pricing is the parallel part: the whole CTA evaluates a block
+// of arcs (reduced cost c - pi(tail) + pi(head)) and reduces to the most
+// negative one.  The pivot walk (apex, leaving arc, flow change) is sequential
+// on one thread.  The spanning tree is kept as an explicit preorder array
+// (ord, pos, size), so that re-hanging the cut subtree is a handful of
+// contiguous segment moves done by all threads, with per-segment depth shifts
+// and one potential shift -- no pointer chasing over the subtree.
+//
+// Big-M start: node i has an artificial arc to (supply >= 0) or from (< 0) an
+// extra root; zero-flow tree arcs point to the root (strongly feasible tree),
+// and the leaving arc is the last blocking arc met when the cycle is walked
+// from the apex in the direction of the entering arc, which rules out cycling.
+#include "internal.h"
+#include "prims.cuh"
+
+namespace pd {
+
+constexpr int NS_THREADS = 1024;
+
+struct NSInst {
+    int32_t n;         // real nodes (root = n)
+    int64_t m;         // real arcs
+    const int32_t* tail;
+    const int32_t* head;
+    const int32_t* cost;
+    const int64_t* supply;
+    int64_t* pi;       // n + 1
+    int32_t* parent;   // n + 1
+    int64_t* pred;     // n + 1 (arc id; artificial arc of node i is m + i)
+    int32_t* depth;    // n + 1
+    int64_t* flow;     // n + 1: flow on the pred arc
+    uint8_t* up;       // n + 1: pred arc points from the node to its parent
+    int32_t* ord;      // n + 1 preorder
+    int32_t* pos;      // n + 1
+    int32_t* size;     // n + 1
+    int32_t* tmp;      // n + 1 scratch
+    int32_t* path;     // n + 1 scratch (re-hang path)
+    int32_t* seg;      // 4 * (2n + 3) scratch: segment start, length, output offset, depth shift
+    int64_t block;     // pricing block (arcs)
+    int64_t max_pivots;
+    uint64_t time_limit_ns;
+    // results
+    int64_t opt;
+    int64_t pivots;
+    int64_t degenerate;
+    int32_t status;    // 0 ok, 1 infeasible, 2 pivot cap / time, 3 unbounded, 4 path too long
+    int32_t pad;
+};
+
+PD_D uint64_t ns_now() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+PD_D void arc_ends(const NSInst& I, int64_t a, int32_t* t, int32_t* h) {
+    if (a < I.m) {
+        *t = I.tail[a];
+        *h = I.head[a];
+    } else {
+        int32_t i = (int32_t)(a - I.m);
+        if (I.supply[i] >= 0) {
+            *t = i;
+            *h = I.n;
+        } else {
+            *t = I.n;
+            *h = i;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_t big) {
+    NSInst& I = insts[blockIdx.x];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int32_t n = I.n, root = n, N1 = n + 1;
+    const int64_t M = I.m + n;  // arcs including the artificial ones
+
+    __shared__ int64_t s_val[32];
+    __shared__ int64_t s_idx[32];
+    __shared__ int64_t s_best, s_bidx, s_next, s_dpi;
+    __shared__ int32_t s_go, s_status;
+    // re-hang plan
+    __shared__ int32_t s_k, s_L0, s_S, s_pr, s_nseg;
+    const int32_t SEGN = 2 * n + 3;
+    int32_t* seg_start = I.seg;
+    int32_t* seg_len = I.seg + SEGN;
+    int32_t* seg_out = I.seg + 2 * SEGN;
+    int32_t* seg_dd = I.seg + 3 * SEGN;
+
+    // ---- initial tree: the root star --------------------------------------
+    for (int32_t i = tid; i < n; i += NS_THREADS) {
+        int64_t s = I.supply[i];
+        I.parent[i] = root;
+        I.pred[i] = I.m + i;
+        I.up[i] = s >= 0;
+        I.flow[i] = s >= 0 ? s : -s;
+        I.pi[i] = s >= 0 ? big : -big;  // reduced cost of the artificial arc is 0
+        I.depth[i] = 1;
+        I.ord[1 + i] = i;
+        I.pos[i] = 1 + i;
+        I.size[i] = 1;
+    }
+    if (tid == 0) {
+        I.parent[root] = -1;
+        I.pred[root] = -1;
+        I.up[root] = 0;
+        I.flow[root] = 0;
+        I.pi[root] = 0;
+        I.depth[root] = 0;
+        I.ord[0] = root;
+        I.pos[root] = 0;
+        I.size[root] = N1;
+        s_next = 0;
+        s_status = 0;
+    }
+    __syncthreads();
+    const uint64_t t0 = ns_now();
+    int64_t pivots = 0, degen = 0;
+    const int64_t B = I.block < 1 ? 1 : I.block;
+
+    for (;;) {
+        // ---- pricing: blocks of B arcs from s_next, first block holding a
+        // negative reduced cost wins (most negative in it, lowest index on ties)
+        int64_t scanned = 0, a0 = s_next;
+        int64_t best = 0, bidx = -1;
+        while (scanned < M) {
+            int64_t len = B < M - scanned ? B : M - scanned;
+            int64_t lb = 0, li = -1;
+            for (int64_t o = tid; o < len; o += NS_THREADS) {
+                int64_t a = a0 + o;
+                if (a >= M) a -= M;
+                int32_t t, h;
+                int64_t c;
+                if (a < I.m) {
+                    t = I.tail[a];
+                    h = I.head[a];
+                    c = I.cost[a];
+                } else {
+                    arc_ends(I, a, &t, &h);
+                    c = big;
+                }
+                int64_t rc = c - I.pi[t] + I.pi[h];
+                if (rc < lb || (rc == lb && rc < 0 && a < li)) {
+                    lb = rc;
+                    li = a;
+                }
+            }
+            // CTA argmin (value, then index)
+            for (int off = 16; off > 0; off >>= 1) {
+                int64_t ov = __shfl_xor_sync(0xffffffffu, lb, off);
+                int64_t oi = __shfl_xor_sync(0xffffffffu, li, off);
+                if (ov < lb || (ov == lb && oi >= 0 && (li < 0 || oi < li))) {
+                    lb = ov;
+                    li = oi;
+                }
+            }
+            if (lane == 0) {
+                s_val[wid] = lb;
+                s_idx[wid] = li;
+            }
+            __syncthreads();
+            if (wid == 0) {
+                lb = s_val[lane];
+                li = s_idx[lane];
+                for (int off = 16; off > 0; off >>= 1) {
+                    int64_t ov = __shfl_xor_sync(0xffffffffu, lb, off);
+                    int64_t oi = __shfl_xor_sync(0xffffffffu, li, off);
+                    if (ov < lb || (ov == lb && oi >= 0 && (li < 0 || oi < li))) {
+                        lb = ov;
+                        li = oi;
+                    }
+                }
+                if (lane == 0) {
+                    s_best = lb;
+                    s_bidx = li;
+                }
+            }
+            __syncthreads();
+            best = s_best;
+            bidx = s_bidx;
+            scanned += len;
+            a0 += len;
+            if (a0 >= M) a0 -= M;
+            __syncthreads();
+            if (best < 0) break;
+        }
+        if (best >= 0 || bidx < 0) break;  // optimal
+        if (tid == 0) s_go = (pivots < I.max_pivots && ns_now() - t0 <= I.time_limit_ns) ? 1 : 0;
+        __syncthreads();
+        if (!s_go) {
+            if (tid == 0) s_status = 2;
+            __syncthreads();
+            break;
+        }
+        pivots++;
+
+        // ---- sequential pivot walk (thread 0) ---------------------------------
+        if (tid == 0) {
+            s_next = a0;
+            int64_t e = bidx;
+            int32_t i, j;
+            arc_ends(I, e, &i, &j);
+            int64_t ce = e < I.m ? (int64_t)I.cost[e] : big;
+            int32_t u = i, v = j;
+            while (u != v) {
+                int32_t du = I.depth[u], dv = I.depth[v];
+                if (du > dv)
+                    u = I.parent[u];
+                else if (dv > du)
+                    v = I.parent[v];
+                else {
+                    u = I.parent[u];
+                    v = I.parent[v];
+                }
+            }
+            const int32_t join = u;
+            int64_t delta = INT64_MAX;
+            int32_t leave = -1, side = 0;
+            for (int32_t x = i; x != join; x = I.parent[x])
+                if (I.up[x] && I.flow[x] < delta) {
+                    delta = I.flow[x];
+                    leave = x;
+                    side = 1;
+                }
+            for (int32_t x = j; x != join; x = I.parent[x])
+                if (!I.up[x] && I.flow[x] <= delta) {
+                    delta = I.flow[x];
+                    leave = x;
+                    side = 2;
+                }
+            s_go = 0;
+            if (leave < 0) {
+                s_status = 3;
+            } else {
+                if (delta > 0) {
+                    for (int32_t x = i; x != join; x = I.parent[x]) I.flow[x] += I.up[x] ? -delta : delta;
+                    for (int32_t x = j; x != join; x = I.parent[x]) I.flow[x] += I.up[x] ? delta : -delta;
+                } else {
+                    degen++;
+                }
+                const int32_t q = side == 1 ? i : j, r = side == 1 ? j : i;
+                int64_t rc = ce - I.pi[i] + I.pi[j];
+                s_dpi = side == 1 ? rc : -rc;
+                // path q = v0, v1, ..., vk = leave
+                int32_t k = 0;
+                I.path[0] = q;
+                while (I.path[k] != leave) {
+                    I.path[k + 1] = I.parent[I.path[k]];
+                    k++;
+                }
+                {
+                    const int32_t S = I.size[leave];
+                    // ancestors: the cut subtree leaves the chain above leave and joins the chain of r
+                    for (int32_t x = I.parent[leave]; x != join; x = I.parent[x]) I.size[x] -= S;
+                    for (int32_t x = r; x != join; x = I.parent[x]) I.size[x] += S;
+                    // new preorder of the cut subtree, re-rooted at q, as segments of the old order
+                    const int32_t dr = I.depth[r];
+                    int32_t ns = 0, out = 0;
+                    seg_start[ns] = I.pos[q];
+                    seg_len[ns] = I.size[q];
+                    seg_out[ns] = out;
+                    seg_dd[ns] = dr + 1 - I.depth[q];
+                    out += seg_len[ns];
+                    ns++;
+                    for (int32_t t = 1; t <= k; t++) {
+                        int32_t vt = I.path[t], vp = I.path[t - 1];
+                        int32_t dd = dr + 1 + t - I.depth[vt];
+                        int32_t a_len = I.pos[vp] - I.pos[vt];
+                        int32_t b_st = I.pos[vp] + I.size[vp];
+                        int32_t b_len = I.pos[vt] + I.size[vt] - b_st;
+                        seg_start[ns] = I.pos[vt];
+                        seg_len[ns] = a_len;
+                        seg_out[ns] = out;
+                        seg_dd[ns] = dd;
+                        out += a_len;
+                        ns++;
+                        seg_start[ns] = b_st;
+                        seg_len[ns] = b_len;
+                        seg_out[ns] = out;
+                        seg_dd[ns] = dd;
+                        out += b_len;
+                        ns++;
+                    }
+                    // new subtree sizes along the path (suffix sums of A_t + B_t)
+                    int32_t acc = 0;
+                    for (int32_t t = k; t >= 1; t--) {
+                        acc += seg_len[2 * t - 1] + seg_len[2 * t];
+                        I.tmp[t] = acc;  // stash; applied below after old sizes are no longer read
+                    }
+                    // parent / pred / direction / flow along the reversed path
+                    int64_t prev_pred = e;
+                    uint8_t prev_up = (uint8_t)(i == q ? 1 : 0);  // e runs i -> j: up for q iff q == i
+                    int64_t prev_flow = delta;
+                    int32_t prev_par = r;
+                    for (int32_t t = 0; t <= k; t++) {
+                        int32_t vt = I.path[t];
+                        int64_t op = I.pred[vt];
+                        uint8_t ou = I.up[vt];
+                        int64_t of = I.flow[vt];
+                        I.pred[vt] = prev_pred;
+                        I.up[vt] = prev_up;
+                        I.flow[vt] = prev_flow;
+                        I.parent[vt] = prev_par;
+                        prev_pred = op;
+                        prev_up = (uint8_t)!ou;
+                        prev_flow = of;
+                        prev_par = vt;
+                    }
+                    I.size[q] = S;
+                    for (int32_t t = 1; t <= k; t++) I.size[I.path[t]] = I.tmp[t];
+                    s_k = k;
+                    s_nseg = ns;
+                    s_L0 = I.pos[leave];
+                    s_S = S;
+                    s_pr = I.pos[r];
+                    s_go = 1;
+                }
+            }
+        }
+        __syncthreads();
+        if (!s_go) break;
+        // ---- parallel re-hang: move the cut segment after r, re-rooted ------
+        {
+            const int32_t L0 = s_L0, S = s_S, pr = s_pr, nseg = s_nseg;
+            const int64_t dpi = s_dpi;
+            // new order over the affected index range [lo, hi)
+            int32_t lo, hi, ins;  // ins: first index of the new segment in the new order
+            if (pr < L0) {
+                lo = pr + 1;
+                hi = L0 + S;
+                ins = pr + 1;
+            } else {
+                lo = L0;
+                hi = pr + 1;
+                ins = pr + 1 - S;
+            }
+            for (int32_t x = lo + tid; x < hi; x += NS_THREADS) {
+                int32_t node;
+                if (x >= ins && x < ins + S) {
+                    int32_t o = x - ins;
+                    int32_t sl = 0, sh = nseg - 1;  // last segment with seg_out <= o
+                    while (sl < sh) {
+                        int32_t mid = (sl + sh + 1) >> 1;
+                        if (seg_out[mid] <= o)
+                            sl = mid;
+                        else
+                            sh = mid - 1;
+                    }
+                    int32_t sidx = sl;
+                    node = I.ord[seg_start[sidx] + (o - seg_out[sidx])];
+                    I.depth[node] += seg_dd[sidx];
+                    I.pi[node] += dpi;
+                } else if (pr < L0) {
+                    // [pr+1, L0) shifted right by S
+                    node = I.ord[x - S];
+                } else {
+                    // [L0+S, pr] shifted left by S
+                    node = I.ord[x + S];
+                }
+                I.tmp[x] = node;
+            }
+            __syncthreads();
+            for (int32_t x = lo + tid; x < hi; x += NS_THREADS) {
+                int32_t node = I.tmp[x];
+                I.ord[x] = node;
+                I.pos[node] = x;
+            }
+            __syncthreads();
+        }
+    }
+    // ---- result ------------------------------------------------------------
+    __syncthreads();
+    if (tid == 0) {
+        int st = s_status;
+        I.pivots = pivots;
+        I.degenerate = degen;
+        I.status = st;
+    }
+    // objective over tree arcs, and feasibility (no flow left on artificial arcs)
+    __shared__ unsigned long long s_obj, s_art;
+    if (tid == 0) {
+        s_obj = 0;
+        s_art = 0;
+    }
+    __syncthreads();
+    unsigned long long obj = 0, art = 0;
+    for (int32_t v = tid; v < n; v += NS_THREADS) {
+        int64_t a = I.pred[v], f = I.flow[v];
+        if (a >= I.m) {
+            if (f != 0) art++;
+        } else if (f > 0) {
+            obj += (unsigned long long)((int64_t)I.cost[a] * f);
+        }
+    }
+    atomicAdd(&s_obj, obj);
+    atomicAdd(&s_art, art);
+    __syncthreads();
+    if (tid == 0) {
+        I.opt = (int64_t)s_obj;
+        if (I.status == 0 && s_art) I.status = 1;
+    }
+}
+
+}  // namespace pd
+
+namespace pd {
+
+__global__ void k_i64_to_i32_cost(const int64_t* __restrict__ c, int64_t m, int32_t* __restrict__ o,
+                                  unsigned long long* __restrict__ bad) {
+    int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= m) return;
+    int64_t v = c[a];
+    if (v < 0 || v >= (int64_t(1) << 31)) atomicAdd(bad, 1ull);
+    o[a] = (int32_t)v;
+}
+
+// Network simplex on an arc list (one CTA).  cmax = largest arc cost.
+pd_status ns_solve_arcs(Ctx* c, int32_t n, int64_t m, const int32_t* tail, const int32_t* head, const int32_t* cost,
+                        const int64_t* supply, int64_t cmax, const pd_opts& o, NSOut* out, cudaStream_t st) {
+    *out = NSOut{};
+    if (n <= 0) return PD_OK;
+    int64_t N1 = (int64_t)n + 1;
+    NSInst h{};
+    h.n = n;
+    h.m = m;
+    h.tail = tail;
+    h.head = head;
+    h.cost = cost;
+    h.supply = supply;
+    h.pi = bufT<int64_t>(c, B_NS_PI, N1);
+    h.parent = bufT<int32_t>(c, B_NS_PARENT, N1);
+    h.pred = bufT<int64_t>(c, B_NS_PRED, N1);
+    h.depth = bufT<int32_t>(c, B_NS_DEPTH, N1);
+    h.flow = bufT<int64_t>(c, B_NS_FLOW, N1);
+    h.up = bufT<uint8_t>(c, B_NS_UP, N1);
+    h.ord = bufT<int32_t>(c, B_NS_ORD, N1);
+    h.pos = bufT<int32_t>(c, B_NS_POS, N1);
+    h.size = bufT<int32_t>(c, B_NS_SIZE, N1);
+    h.tmp = bufT<int32_t>(c, B_NS_TMP, N1);
+    h.path = bufT<int32_t>(c, B_NS_PATH, N1);
+    h.seg = bufT<int32_t>(c, B_NS_SEG, 4 * (2 * N1 + 3));
+    NSInst* d = bufT<NSInst>(c, B_NS_INST, 1);
+    if (!h.pi || !h.parent || !h.pred || !h.depth || !h.flow || !h.up || !h.ord || !h.pos || !h.size || !h.tmp ||
+        !h.path || !h.seg || !d)
+        return PD_ENOMEM;
+    int64_t M = m + n;
+    int64_t blk = o.ns_block > 0 ? o.ns_block : (int64_t)sqrt((double)M);
+    if (blk < 2048) blk = 2048;
+    h.block = blk;
+    h.max_pivots = o.max_rounds > 0 ? o.max_rounds : (int64_t(1) << 40);
+    h.time_limit_ns = (o.time_limit_ms > 0 ? (uint64_t)o.time_limit_ms : 60000ull) * 1000000ull;
+    // big-M: more than any path cost; |potentials| stay below ~3 big
+    if (cmax > (INT64_MAX / 8) / N1) return fail(c, PD_EOVERFLOW, "network simplex big-M would overflow");
+    int64_t big = N1 * (cmax + 1) + 1;
+    PD_TRY_CUDA(c, cudaMemcpyAsync(d, &h, sizeof(NSInst), cudaMemcpyHostToDevice, st));
+    k_netsimplex<<<1, NS_THREADS, 0, st>>>(d, big);
+    PD_TRY_CUDA(c, cudaGetLastError());
+    NSInst r;
+    PD_TRY_CUDA(c, cudaMemcpyAsync(&r, d, sizeof(NSInst), cudaMemcpyDeviceToHost, st));
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    out->opt = r.opt;
+    out->pivots = r.pivots;
+    out->degenerate = r.degenerate;
+    out->status = r.status;
+    if (r.status == 2) return fail(c, PD_ETIMEOUT, "network simplex pivot cap or time limit reached");
+    if (r.status == 1) return fail(c, PD_EINFEASIBLE, "network has no feasible flow");
+    if (r.status == 3) return fail(c, PD_EINFEASIBLE, "network simplex found an unbounded cycle");
+    if (r.status != 0) return fail(c, PD_ECUDA, "network simplex failed");
+    return PD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// transportation form of the condensed problem, and its certificate on WS
+// ---------------------------------------------------------------------------
+
+__global__ void k_side_flags(const int64_t* __restrict__ cntA, const int64_t* __restrict__ cntB, int64_t N,
+                             int64_t* __restrict__ fs, int64_t* __restrict__ ft) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= N) return;
+    int64_t s = cntA[u] - cntB[u];
+    fs[u] = s > 0;
+    ft[u] = s < 0;
+}
+
+__global__ void k_side_lists(const int64_t* __restrict__ cntA, const int64_t* __restrict__ cntB, int64_t N,
+                             const int64_t* __restrict__ os, const int64_t* __restrict__ ot, int32_t* __restrict__ S,
+                             int32_t* __restrict__ T, int64_t* __restrict__ sup, int64_t nS) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= N) return;
+    int64_t s = cntA[u] - cntB[u];
+    if (s > 0) {
+        S[os[u]] = (int32_t)u;
+        sup[os[u]] = s;
+    } else if (s < 0) {
+        T[ot[u]] = (int32_t)u;
+        sup[nS + ot[u]] = s;
+    }
+}
+
+// Arc i*nT + j: source i -> sink j at min(l2, diag(i) + diag(j)) (the route
+// through the diagonal node has unbounded capacity); then the arcs of the
+// diagonal node if its supply |B| - |A| is not 0.
+__global__ void k_transport_arcs(const int32_t* __restrict__ S, const int32_t* __restrict__ T, int64_t nS,
+                                 int64_t nT, int dside, const int32_t* __restrict__ X, const int32_t* __restrict__ Y,
+                                 int32_t* __restrict__ tail, int32_t* __restrict__ head, int32_t* __restrict__ cost,
+                                 unsigned long long* __restrict__ bad) {
+    int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t mst = nS * nT;
+    int64_t D = nS + nT;
+    int64_t c;
+    if (a < mst) {
+        int64_t i = a / nT, j = a - i * nT;
+        int32_t u = S[i], v = T[j];
+        int64_t d = cost_l2(X[u], Y[u], X[v], Y[v]);
+        int64_t g = cost_diag(X[u], Y[u]) + cost_diag(X[v], Y[v]);
+        c = d < g ? d : g;
+        tail[a] = (int32_t)i;
+        head[a] = (int32_t)(nS + j);
+    } else if (dside < 0 && a < mst + nS) {
+        int64_t i = a - mst;
+        int32_t u = S[i];
+        c = cost_diag(X[u], Y[u]);
+        tail[a] = (int32_t)i;
+        head[a] = (int32_t)D;
+    } else if (dside > 0 && a < mst + nT) {
+        int64_t j = a - mst;
+        int32_t v = T[j];
+        c = cost_diag(X[v], Y[v]);
+        tail[a] = (int32_t)D;
+        head[a] = (int32_t)(nS + j);
+    } else {
+        return;
+    }
+    if (c >= (int64_t(1) << 31)) atomicAdd(bad, 1ull);
+    cost[a] = (int32_t)c;
+}
+
+// Certificate: every source->sink pair that carries flow on its direct route
+// must be an arc of the sparse network (then the transport optimum, a lower
+// bound on the sparse optimum, is attained on the sparse network).  Also
+// counts the arcs of the sparse network the flow uses (rounding slack).
+__global__ void k_certify_transport(const NSInst* __restrict__ I, const int32_t* __restrict__ S,
+                                    const int32_t* __restrict__ T, int64_t nS, int64_t nT,
+                                    const int32_t* __restrict__ X, const int32_t* __restrict__ Y,
+                                    const int64_t* __restrict__ rp, const int32_t* __restrict__ hd,
+                                    unsigned long long* __restrict__ out) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= I->n) return;
+    int64_t a = I->pred[v], f = I->flow[v];
+    if (a >= I->m || f <= 0) return;
+    int64_t mst = nS * nT;
+    if (a >= mst) {  // arc of the diagonal node: one arc of the sparse network
+        atomicAdd(&out[1], (unsigned long long)f);
+        return;
+    }
+    int64_t i = a / nT, j = a - i * nT;
+    int32_t u = S[i], w = T[j];
+    int64_t d = cost_l2(X[u], Y[u], X[w], Y[w]);
+    int64_t g = cost_diag(X[u], Y[u]) + cost_diag(X[w], Y[w]);
+    if (g <= d) {  // through the diagonal node: u -> diag -> w, both arcs exist
+        atomicAdd(&out[1], (unsigned long long)(2 * f));
+        return;
+    }
+    int64_t lo = rp[u], hi = rp[u + 1] - 1;
+    bool found = false;
+    while (lo <= hi) {
+        int64_t mid = (lo + hi) >> 1;
+        int32_t h = hd[mid];
+        if (h == w) {
+            found = true;
+            break;
+        }
+        if (h < w)
+            lo = mid + 1;
+        else
+            hi = mid - 1;
+    }
+    if (!found) atomicAdd(&out[0], 1ull);
+    atomicAdd(&out[1], (unsigned long long)f);
+}
+
+// Total flow over the arcs of a solved arc-list network (rounding slack).
+__global__ void k_tree_flow(const NSInst* __restrict__ I, unsigned long long* __restrict__ out) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= I->n) return;
+    if (I->pred[v] < I->m && I->flow[v] > 0) atomicAdd(out, (unsigned long long)I->flow[v]);
+}
+
+pd_status ns_solve_network(Ctx* c, const pd_network& net, const pd_opts& o, SolveStats* out, cudaStream_t st) {
+    int64_t n = net.n_nodes, m = net.n_arcs;
+    if (n >= (int64_t(1) << 31) - 2) return fail(c, PD_ECAPACITY, "too many nodes");
+    int32_t* tail = bufT<int32_t>(c, B_S_TAIL, m);
+    int32_t* c32 = bufT<int32_t>(c, B_NS_COST, m);
+    unsigned long long* sm = bufT<unsigned long long>(c, B_SMALL, 64);
+    if (!tail || !c32 || !sm) return PD_ENOMEM;
+    PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, 8 * sizeof(unsigned long long), st));
+    if (m > 0) {
+        k_arc_tails<<<grid_for(m, 256), 256, 0, st>>>(net.row_ptr, n, m, tail);
+        k_i64_to_i32_cost<<<grid_for(m, 256), 256, 0, st>>>(net.cost, m, c32, sm);
+        k_max_cost<<<grid_for(m, 256), 256, 0, st>>>(net.cost, m, sm + 1);
+    }
+    PD_TRY_CUDA(c, cudaGetLastError());
+    PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    if (c->h_small[0]) return fail(c, PD_EOVERFLOW, "arc cost outside [0, 2^31)");
+    int64_t cmax = c->h_small[1];
+    NSOut r;
+    PD_TRY(ns_solve_arcs(c, (int32_t)n, m, tail, net.head, c32, net.supply, cmax, o, &r, st));
+    PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, sizeof(unsigned long long), st));
+    k_tree_flow<<<grid_for(n, 256), 256, 0, st>>>(bufT<NSInst>(c, B_NS_INST, 1), sm);
+    PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    out->opt = r.opt;
+    out->slack = c->h_small[0];
+    out->pivots = r.pivots;
+    out->degenerate = r.degenerate;
+    out->verified = 1;  // the pricing loop ends only when no arc has a negative reduced cost
+    out->method = 1;
+    return PD_OK;
+}
+
+// The W1 network: try the transportation form with the certificate first
+// when it is not much larger than the sparse network, else (or if the
+// certificate fails) run the simplex on the sparse network itself.
+pd_status ns_solve_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const pd_network& merged,
+                      const pd_opts& o, SolveStats* out, cudaStream_t st) {
+    *out = SolveStats{};
+    int64_t N = nodes.n_nodes;
+    if (N == 0) return ns_solve_network(c, merged, o, out, st);
+    int64_t* fs = bufT<int64_t>(c, B_WSFLAG, N);
+    int64_t* ft = bufT<int64_t>(c, B_WSOFF, N);
+    unsigned long long* sm = bufT<unsigned long long>(c, B_SMALL, 64);
+    if (!fs || !ft || !sm) return PD_ENOMEM;
+    k_side_flags<<<grid_for(N, 256), 256, 0, st>>>(nodes.cntA, nodes.cntB, N, fs, ft);
+    PD_TRY(scan_i64(c, fs, fs, N, (int64_t*)sm + 2, st));
+    PD_TRY(scan_i64(c, ft, ft, N, (int64_t*)sm + 3, st));
+    PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    int64_t nS = c->h_small[2], nT = c->h_small[3];
+    // masses: diagonal supply |B| - |A| from the merged network's last node
+    int64_t dsup = 0;
+    PD_TRY_CUDA(c, cudaMemcpyAsync(&dsup, merged.supply + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    int64_t mst = nS * nT;
+    int64_t mt = mst + (dsup < 0 ? nS : (dsup > 0 ? nT : 0));
+    bool try_transport = o.ns_transport != 0 && mt <= 2 * ws.n_arcs + 4096 && mt < (int64_t(1) << 31);
+    if (try_transport) {
+        int64_t nt = nS + nT + 1;
+        int32_t* S = bufT<int32_t>(c, B_TR_S, nS);
+        int32_t* T = bufT<int32_t>(c, B_TR_T, nT);
+        int64_t* sup = bufT<int64_t>(c, B_TR_SUP, nt);
+        int32_t* tail = bufT<int32_t>(c, B_S_TAIL, mt);
+        int32_t* head = bufT<int32_t>(c, B_S_HEAD, mt);
+        int32_t* cost = bufT<int32_t>(c, B_NS_COST, mt);
+        if (!S || !T || !sup || !tail || !head || !cost) return PD_ENOMEM;
+        k_side_lists<<<grid_for(N, 256), 256, 0, st>>>(nodes.cntA, nodes.cntB, N, fs, ft, S, T, sup, nS);
+        PD_TRY_CUDA(c, cudaMemcpyAsync(sup + nS + nT, &dsup, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, 8 * sizeof(unsigned long long), st));
+        if (mt > 0)
+            k_transport_arcs<<<grid_for(mt, 256), 256, 0, st>>>(S, T, nS, nT, dsup < 0 ? -1 : (dsup > 0 ? 1 : 0),
+                                                                  nodes.X, nodes.Y, tail, head, cost, sm);
+        PD_TRY_CUDA(c, cudaGetLastError());
+        k_max_cost32<<<grid_for(mt, 256), 256, 0, st>>>(cost, mt, sm + 1);
+        PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+        if (c->h_small[0] == 0) {
+            NSOut r;
+            PD_TRY(ns_solve_arcs(c, (int32_t)nt, mt, tail, head, cost, sup, c->h_small[1], o, &r, st));
+            PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, 4 * sizeof(unsigned long long), st));
+            k_certify_transport<<<grid_for(nt, 256), 256, 0, st>>>(bufT<NSInst>(c, B_NS_INST, 1), S, T, nS, nT,
+                                                                    nodes.X, nodes.Y, ws.row_ptr, ws.head, sm);
+            PD_TRY_CUDA(c, cudaGetLastError());
+            PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+            out->pivots = r.pivots;
+            out->degenerate = r.degenerate;
+            if (c->h_small[0] == 0) {
+                out->opt = r.opt;
+                out->slack = c->h_small[1];
+                out->verified = 1;
+                out->method = 2;
+                return PD_OK;
+            }
+            out->cert_failures = c->h_small[0];
+        }
+    }
+    int64_t piv = out->pivots, fails = out->cert_failures;
+    PD_TRY(ns_solve_network(c, merged, o, out, st));
+    out->pivots += piv;
+    out->cert_failures = fails;
+    return PD_OK;
+}
+
+}  // namespace pd

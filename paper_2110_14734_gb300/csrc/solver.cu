@@ -754,6 +754,16 @@ __global__ void k_max_cost(const int64_t* __restrict__ cost, int64_t m, unsigned
     if ((threadIdx.x & 31) == 0 && c) atomicMax(out, c);
 }
 
+__global__ void k_max_cost32(const int32_t* __restrict__ cost, int64_t m, unsigned long long* __restrict__ out) {
+    int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long c = a < m ? (unsigned long long)(uint32_t)cost[a] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long u = __shfl_xor_sync(0xffffffffu, c, o);
+        c = u > c ? u : c;
+    }
+    if ((threadIdx.x & 31) == 0 && c) atomicMax(out, c);
+}
+
 // OPT = sum of c * x over slots carrying flow in their arc's direction;
 // slack = total flow (each rounded-up unit cost exceeds the real one by < 1).
 __global__ void k_objective(const uint32_t* __restrict__ cw, const int64_t* __restrict__ x, int64_t ms,

@@ -191,9 +191,12 @@ def test_mcf_random_networks_match_network_simplex(pd, ctx, seed):
     net = _random_network(rng, int(rng.integers(5, 300)), int(rng.integers(10, 3000)))
     st, opt, flow, pot = oracle.mcf_arcs(len(net["supply"]), net["tails"], net["head"], net["cost"], net["supply"])
     assert st == 0
-    for alpha in (2, 8, 16):
-        got, stats = pd.pd_mcf_solve(ctx, {k: _cuda(v) for k, v in net.items() if k != "tails"},
-                                     pd.opts(alpha=alpha, verify=1))
+    dnet = {k: _cuda(v) for k, v in net.items() if k != "tails"}
+    for blk in (0, 1, 64):  # network simplex, different pricing blocks
+        got, stats = pd.pd_mcf_solve(ctx, dnet, pd.opts(ns_block=blk))
+        assert got == opt and stats["verified"] == 1 and stats["solve_method"] == 1
+    for alpha in (2, 8, 16):  # cost scaling
+        got, stats = pd.pd_mcf_solve(ctx, dnet, pd.opts(solver=1, alpha=alpha, verify=1))
         assert got == opt and stats["verified"] == 1
 
 
@@ -204,6 +207,9 @@ def test_mcf_on_w1_networks(pd, ctx, name):
     net = {k: _cuda(r["net"][k]) for k in ("row_ptr", "head", "cost", "supply")}
     got, stats = pd.pd_mcf_solve(ctx, net, pd.opts(verify=1))
     assert got == r["opt"] and stats["verified"] == 1
+    if name != "mixture5k":
+        got, stats = pd.pd_mcf_solve(ctx, net, pd.opts(solver=1, verify=1))
+        assert got == r["opt"] and stats["verified"] == 1
 
 
 def _check_w1(pd, ctx, A, B, dt, eps, **kw):
@@ -214,6 +220,11 @@ def _check_w1(pd, ctx, A, B, dt, eps, **kw):
                 coord_shift=kw.get("k", -1) if kw.get("k") is not None else -1)
     g = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), eps, o)
     assert (g["rwmd_A"], g["rwmd_B"]) == (r["LA"], r["LB"])
+    # the simplex straight on the sparse network must agree as well
+    g2 = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), eps, pd.opts(
+        s_override=o.s_override, perturb=o.perturb, seed=o.seed, condense=o.condense, coord_shift=o.coord_shift,
+        ns_transport=0))
+    assert g2["opt_quanta"] == r["opt"] and g2["solve_method"] == 1
     assert g["s"] == r["s"] and g["cell_quanta"] == r["G"] and g["shift_quanta"] == r["P"]
     assert g["delta"] == r["delta"]
     assert g["n_nodes"] == len(r["nodes"]["X"]) and g["n_arcs"] == int(r["net"]["row_ptr"][-1])
