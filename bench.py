@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Benchmark: approximate W1 between two persistence diagrams of 100,000 uint8
+lower-star points each (eps = 0.05, WSPD parameter s = 327), in pairs/s.
+
+One step = one pd_w1_approx call on one pair: quantise, 0-condense, RWMD,
+delta-condense, radix tree, WSPD, diagonal arcs, CSR, exact min-cost flow.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle (the
+plain C restatement of the method) on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "W1 pairs/s at 100k pts, eps=0.05"
+UNIT = "pairs/s"
+WORKLOAD = "lower-star uint8 persistence diagrams, 100000 + 100000 points, eps=0.05 (s=327)"
+SAMPLE_N = 10000  # points per diagram of the CPU-oracle sample
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=100000)
+    ap.add_argument("--eps", type=float, default=0.05)
+    ap.add_argument("--pool", type=int, default=6, help="distinct seeded pairs cycled over the steps")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_cores_used():
+    return 1  # the oracle is single-threaded C
+
+
+def host_info():
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                info["model"] = line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return info
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, device):
+        self.device = device
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        cmd = ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + ",".join(self.FIELDS),
+               "--format=csv,noheader,nounits"]
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(cmd, capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 3 + i and s[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs
+# ---------------------------------------------------------------------------
+
+def oracle_pair_seconds(seed):
+    import oracle
+    from paper_2110_14734_gb300 import synth
+    A, B = synth.lowerstar_u8(SAMPLE_N, seed), synth.lowerstar_u8(SAMPLE_N, seed + 1)
+    t = time.perf_counter()
+    oracle.w1_approx(A, B, "u8", eps=0.05)
+    return time.perf_counter() - t
+
+
+def cpu_baseline():
+    sec = oracle_pair_seconds(1000)
+    return {"value": 1.0 / sec, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+            "sample": "CPU oracle (plain C, single thread: quantise .. network simplex on the sparse network) on "
+                      "one %d + %d point pair of the same generator, eps=0.05; %.1f s" % (SAMPLE_N, SAMPLE_N, sec),
+            "host": host_info()}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    for i in range(args.warmup):
+        oracle_pair_seconds(5000 + 2 * i)
+    times = [oracle_pair_seconds(7000 + 2 * i) for i in range(args.steps)]
+    tot = sum(times)
+    value = args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded lower-star uint8 diagrams)",
+            "config": {"workload": WORKLOAD, "sample_points_per_diagram": SAMPLE_N, "eps": 0.05},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+                             "sample": "each step: CPU oracle on one %d + %d point pair (distinct seeds)" %
+                                       (SAMPLE_N, SAMPLE_N), "host": host_info()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def load_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from a committed ncu summary, if the
+    kernel's source is unchanged since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))[kernel]
+        src = open(os.path.join(ROOT, d["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
+            return None
+        return d["dram_bytes_per_launch_full"]
+    except Exception:
+        return None
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def run_ours(args):
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2110_14734_gb300 import build
+    build.build()
+    from paper_2110_14734_gb300 import pdw1, synth
+
+    dev = torch.device("cuda", local)
+    ctx = pdw1.pd_create(local)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    opts = pdw1.opts()
+
+    # seeded pairs, resident in HBM before the timed region
+    pool = []
+    for i in range(max(1, min(args.pool, args.warmup + args.steps))):
+        sa, sb = synth.pair_seeds(i + 1000 * rank)
+        A = synth.lowerstar_u8(args.n, sa)
+        B = synth.lowerstar_u8(args.n, sb)
+        pool.append((A, B, torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)))
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def diag(t):
+        d, _ = pdw1.diagram(t)
+        return d
+
+    res = pdw1.pd_result()
+
+    def step(i, host=False):
+        A, B, dA, dB = pool[i % len(pool)]
+        if host:
+            da, db = host_diags[i % len(pool)]
+        else:
+            da, db = diag(dA), diag(dB)
+        st = pdw1.pd_w1_approx_raw(ctx, da, db, args.eps, opts, res, sptr)
+        if st != 0:
+            raise pdw1.PDError(st, pdw1._lib.pd_last_error(ctx.ptr).decode())
+        return res.to_dict()
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region ------------------------------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    results = []
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the event pair)
+            ev[i][0].record(stream)
+            results.append(step(args.warmup + i))
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if ws > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    pairs = args.steps * ws
+    value = pairs / (tot_ms / 1000.0)
+
+    # ---- end to end through the C ABI with pinned host buffers -------------
+    host_diags = []
+    keep = []
+    for A, B, _, _ in pool:
+        hA = torch.from_numpy(A).pin_memory()
+        hB = torch.from_numpy(B).pin_memory()
+        keep += [hA, hB]
+        host_diags.append((diag(hA), diag(hB)))
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    step(0, host=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        step(args.warmup + i, host=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = 2 * args.n * 2
+    d2h = C.sizeof(pdw1.pd_result)
+
+    # ---- roofline of the dominant kernel (network simplex) ----------------
+    ns_ms = [r["ns_kernel_ms"] for r in results]
+    priced = [r["arcs_priced"] for r in results]
+    launches = sum(r["kernel_launches"] for r in results)
+    avg_ns_ms = statistics.mean(ns_ms)
+    algo_bytes = 4.0 * statistics.mean(priced)  # one int32 cost streamed per priced arc
+    achieved = algo_bytes / (avg_ns_ms / 1000.0) / 1e9
+    pk, pk_src = peaks()
+    roof = {"kernel": "k_netsimplex", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": load_traffic("k_netsimplex"), "peak_source": pk_src,
+            "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_ms": avg_ns_ms,
+            "share_of_step": avg_ns_ms / statistics.mean(step_ms)}
+
+    r0 = results[0]
+    stage_names = ["condense0", "rwmd", "delta_condense", "tree", "wspd", "csr", "solve", "total"]
+    stages = {k: statistics.mean(r["stage_ms"][i] for r in results) for i, k in enumerate(stage_names)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak" if ws > 1 else "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded lower-star uint8 diagrams of Gaussian-smoothed noise images)",
+            "config": {"workload": WORKLOAD, "n_points": args.n, "eps": args.eps, "s": r0["s"],
+                       "pairs_in_pool": len(pool), "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "nodes": r0["n_nodes"], "arcs": r0["n_arcs"]},
+            "e2e": {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "stage_ms": stages,
+            "solver": {"method": r0["solve_method"], "pivots": statistics.mean(r["pivots"] for r in results),
+                       "arcs_priced": statistics.mean(priced)},
+            "wall_s": t_wall}
+    if rank == 0:
+        line["clocks"] = clk.summary()
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

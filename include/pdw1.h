@@ -83,7 +83,7 @@ typedef struct {
     int32_t solver;         /* 0 = network simplex (default), 1 = cost scaling with push/relabel */
     int64_t ns_block;       /* network simplex pricing block in arcs (0 = max(2048, sqrt(arcs))) */
     int32_t ns_transport;   /* W1 only: 1 = try the transportation form with its certificate first (default) */
-    int32_t reserved;
+    int32_t ns_smem;        /* network simplex: 1 = hot node arrays in shared memory when they fit (default) */
 } pd_opts;
 
 void pd_opts_default(pd_opts* opts);
@@ -139,8 +139,12 @@ typedef struct {
     int64_t update_passes;  /* solver: relaxation passes of the global price updates */
     int64_t pivots;         /* network simplex: pivots (all attempts) */
     int64_t degenerate;     /* network simplex: pivots that moved no flow */
+    int64_t arcs_priced;    /* network simplex: arcs whose reduced cost was evaluated */
     int32_t solve_method;   /* 0 cost scaling, 1 simplex on the sparse network, 2 transportation form + certificate */
     int32_t cert_failures;  /* pairs of the transportation optimum missing from the sparse network */
+    int64_t kernel_launches; /* kernels this call launched */
+    float ns_kernel_ms;     /* device time of the network simplex kernel(s) of this call */
+    int32_t reserved;
     float stage_ms[8];      /* quantize+0-condense, RWMD, delta-condense, tree, WSPD, CSR, solve, total */
 } pd_result;
 

@@ -15,6 +15,11 @@ struct pd_ctx : public pd::Ctx {};
 
 namespace pd {
 
+long long& launch_count_ref() {
+    static thread_local long long n = 0;
+    return n;
+}
+
 __global__ void k_fill_i64(int64_t* p, int64_t n, int64_t v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
@@ -152,6 +157,7 @@ extern "C" void pd_opts_default(pd_opts* o) {
     o->solver = 0;
     o->ns_block = 0;
     o->ns_transport = 1;
+    o->ns_smem = 1;
 }
 
 extern "C" pd_status pd_create(pd_ctx** out, int device, size_t arena_bytes) {
@@ -293,6 +299,8 @@ extern "C" pd_status pd_mcf_solve(pd_ctx* c, const pd_network* net, const pd_opt
     if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
     pd_opts o = resolve_opts(opts);
     PD_TRY(validate_network(c, *net, (cudaStream_t)stream));
+    c->last_ns_ms = 0.f;
+    const long long launches0 = launch_count_ref();
     SolveStats ss;
     if (o.solver == 1)
         PD_TRY(stage_solve(c, *net, o, &ss, (cudaStream_t)stream));
@@ -312,11 +320,14 @@ extern "C" pd_status pd_mcf_solve(pd_ctx* c, const pd_network* net, const pd_opt
         stats->update_passes = ss.update_passes;
         stats->pivots = ss.pivots;
         stats->degenerate = ss.degenerate;
+        stats->arcs_priced = ss.scanned;
         stats->solve_method = ss.method;
         stats->cert_failures = (int32_t)ss.cert_failures;
         stats->verified = ss.verified;
         stats->n_nodes = net->n_nodes;
         stats->n_arcs = net->n_arcs;
+        stats->kernel_launches = launch_count_ref() - launches0;
+        stats->ns_kernel_ms = c->last_ns_ms;
     }
     return PD_OK;
 }
@@ -327,10 +338,12 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
     c->err.clear();
     pd_opts o = resolve_opts(opts);
     if (!(eps > 0.0) && o.s_override <= 0) return fail(c, PD_EINVAL, "eps must be > 0 (or set s_override)");
+    c->last_ns_ms = 0.f;
     if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
     pd_result r;
     memset(&r, 0, sizeof(r));
+    const long long launches0 = launch_count_ref();
     cudaEvent_t ev[5];
     for (int q = 0; q < 5; q++) PD_TRY_CUDA(c, cudaEventCreate(&ev[q]));
     PD_TRY_CUDA(c, cudaEventRecord(ev[0], st));
@@ -409,6 +422,7 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
     r.update_passes = ss.update_passes;
     r.pivots = ss.pivots;
     r.degenerate = ss.degenerate;
+    r.arcs_priced = ss.scanned;
     r.solve_method = ss.method;
     r.cert_failures = (int32_t)ss.cert_failures;
     r.stage_ms[0] = ms[0];
@@ -419,6 +433,8 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
     r.stage_ms[5] = mc;
     r.stage_ms[6] = ms[3];
     r.stage_ms[7] = tot;
+    r.kernel_launches = launch_count_ref() - launches0;
+    r.ns_kernel_ms = c->last_ns_ms;
     *out = r;
     return PD_OK;
 }

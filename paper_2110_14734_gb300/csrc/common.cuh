@@ -8,6 +8,10 @@
 
 namespace pd {
 
+// Kernel launches issued by this library in this process (host-side count).
+long long& launch_count_ref();
+inline void count_launch() { launch_count_ref()++; }
+
 // Error bits raised by kernels into a device status word (host reads it back).
 enum : uint32_t {
     ERR_INPUT = 1u,       // non-finite or out-of-range coordinate

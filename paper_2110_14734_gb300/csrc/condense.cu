@@ -142,7 +142,7 @@ pd_status stage_condense0(Ctx* c, const DevDiag& A, const DevDiag& B, int k, Hat
     int64_t n = A.n + B.n;
     int64_t* sm = bufT<int64_t>(c, B_SMALL, 64);
     if (!sm) return PD_ENOMEM;
-    k_init_small<<<1, 64, 0, st>>>(sm);
+    k_init_small<<<1, 64, 0, st>>>(sm); pd::count_launch();
     out->nA = out->nB = out->FA = out->FB = 0;
     out->X = bufT<int32_t>(c, B_HAT_X, n);
     out->Y = bufT<int32_t>(c, B_HAT_Y, n);
@@ -157,7 +157,7 @@ pd_status stage_condense0(Ctx* c, const DevDiag& A, const DevDiag& B, int k, Hat
     int64_t* flag = bufT<int64_t>(c, B_IDX, n);
     int64_t* start = bufT<int64_t>(c, B_QVAL, n);
     if (!X || !Y || !keep || !key || !key2 || !flag || !start) return PD_ENOMEM;
-    k_quantize<<<grid_for(n, 256), 256, 0, st>>>(A.bd, A.n, A.dtype, B.bd, B.n, B.dtype, k, X, Y, keep, sm);
+    k_quantize<<<grid_for(n, 256), 256, 0, st>>>(A.bd, A.n, A.dtype, B.bd, B.n, B.dtype, k, X, Y, keep, sm); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, sizeof(int64_t) * S_COUNT, cudaMemcpyDeviceToHost, st));
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
@@ -170,19 +170,19 @@ pd_status stage_condense0(Ctx* c, const DevDiag& A, const DevDiag& B, int k, Hat
     int bx = bits_for((uint64_t)(h[S_MXX] - h[S_MNX])), by = bits_for((uint64_t)(h[S_MXY] - h[S_MNY]));
     int kb = bx + by + 2;
     uint64_t sent = (kb >= 64) ? ~0ull : ((1ull << kb) - 1);
-    k_point_keys<<<grid_for(n, 256), 256, 0, st>>>(X, Y, keep, A.n, n, sm, bx, by, key);
+    k_point_keys<<<grid_for(n, 256), 256, 0, st>>>(X, Y, keep, A.n, n, sm, bx, by, key); pd::count_launch();
     PD_TRY(sort_u64(c, key, key2, nullptr, nullptr, n, kb, st));
-    k_run_flags<<<grid_for(n, 256), 256, 0, st>>>(key, n, sent, flag);
+    k_run_flags<<<grid_for(n, 256), 256, 0, st>>>(key, n, sent, flag); pd::count_launch();
     PD_TRY(scan_i64(c, flag, flag, n, sm + S_M, st));
     k_hat_compact<<<grid_for(n, 256), 256, 0, st>>>(key, n, sent, flag, sm, bx, by, out->X, out->Y, start,
-                                                      sm + S_NA);
+                                                      sm + S_NA); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, sizeof(int64_t) * S_COUNT, cudaMemcpyDeviceToHost, st));
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     int64_t M = h[S_M];
     out->nA = h[S_NA];
     out->nB = M - out->nA;
-    k_hat_counts<<<grid_for(M, 256), 256, 0, st>>>(start, M, nvalid, out->cnt);
+    k_hat_counts<<<grid_for(M, 256), 256, 0, st>>>(start, M, nvalid, out->cnt); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     return PD_OK;
 }
@@ -267,7 +267,7 @@ pd_status stage_rwmd(Ctx* c, const Hats& h, int64_t L[3], cudaStream_t st) {
     if (!sm || !mind2) return PD_ENOMEM;
     PD_TRY_CUDA(c, cudaMemsetAsync(sm + S_L0, 0, 2 * sizeof(int64_t), st));
     if (n > 0) {
-        k_fill_u64<<<grid_for(n, 256), 256, 0, st>>>(mind2, n, ~0ull);
+        k_fill_u64<<<grid_for(n, 256), 256, 0, st>>>(mind2, n, ~0ull); pd::count_launch();
         int64_t npmax = h.nA > h.nB ? h.nA : h.nB;
         int64_t gx = (npmax + RW_THREADS - 1) / RW_THREADS;
         int64_t want = 4LL * (c->sm_count > 0 ? c->sm_count : 152);
@@ -278,8 +278,8 @@ pd_status stage_rwmd(Ctx* c, const Hats& h, int64_t L[3], cudaStream_t st) {
         gy = (nqmax + chunk - 1) / chunk;
         if (gy < 1) gy = 1;
         if (gx > 0 && h.nA > 0 && h.nB > 0)
-            k_rwmd_min<<<dim3((unsigned)gx, (unsigned)gy, 2), RW_THREADS, 0, st>>>(h.X, h.Y, h.nA, h.nB, chunk, mind2);
-        k_rwmd_sum<<<grid_for(n, 256), 256, 0, st>>>(h.X, h.Y, h.cnt, h.nA, n, mind2, sm + S_L0);
+            k_rwmd_min<<<dim3((unsigned)gx, (unsigned)gy, 2), RW_THREADS, 0, st>>>(h.X, h.Y, h.nA, h.nB, chunk, mind2); pd::count_launch();
+        k_rwmd_sum<<<grid_for(n, 256), 256, 0, st>>>(h.X, h.Y, h.cnt, h.nA, n, mind2, sm + S_L0); pd::count_launch();
         PD_TRY_CUDA(c, cudaGetLastError());
     }
     PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, sizeof(int64_t) * S_COUNT, cudaMemcpyDeviceToHost, st));
@@ -429,21 +429,21 @@ pd_status stage_condense_delta(Ctx* c, const Hats& h, int64_t G, int64_t P, uint
     int64_t* CA = bufT<int64_t>(c, B_CA, n);
     int64_t* CB = bufT<int64_t>(c, B_CB, n);
     if (!CX || !CY || !key || !key2 || !val || !val2 || !idx || !NX || !NY || !CA || !CB) return PD_ENOMEM;
-    k_init_small<<<1, 64, 0, st>>>(sm);
-    k_cells<<<grid_for(n, 256), 256, 0, st>>>(h.X, h.Y, n, G, CX, CY, sm);
+    k_init_small<<<1, 64, 0, st>>>(sm); pd::count_launch();
+    k_cells<<<grid_for(n, 256), 256, 0, st>>>(h.X, h.Y, n, G, CX, CY, sm); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, sizeof(int64_t) * S_COUNT, cudaMemcpyDeviceToHost, st));
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     int64_t* hs = c->h_small;
     int bcx = bits_for((uint64_t)(hs[S_CMXX] - hs[S_CMNX])), bcy = bits_for((uint64_t)(hs[S_CMXY] - hs[S_CMNY]));
-    k_cell_keys<<<grid_for(n, 256), 256, 0, st>>>(CX, CY, n, sm, bcy, key, val);
+    k_cell_keys<<<grid_for(n, 256), 256, 0, st>>>(CX, CY, n, sm, bcy, key, val); pd::count_launch();
     PD_TRY(sort_u64(c, key, key2, val, val2, n, bcx + bcy, st));
-    k_run_flags<<<grid_for(n, 256), 256, 0, st>>>(key, n, ~0ull, idx);
+    k_run_flags<<<grid_for(n, 256), 256, 0, st>>>(key, n, ~0ull, idx); pd::count_launch();
     PD_TRY(scan_i64(c, idx, idx, n, sm + S_N, st));
-    k_cell_place<<<grid_for(n, 256), 256, 0, st>>>(key, n, idx, sm, bcy, G, P, seed, NX, NY, sm);
+    k_cell_place<<<grid_for(n, 256), 256, 0, st>>>(key, n, idx, sm, bcy, G, P, seed, NX, NY, sm); pd::count_launch();
     PD_TRY_CUDA(c, cudaMemsetAsync(CA, 0, sizeof(int64_t) * n, st));
     PD_TRY_CUDA(c, cudaMemsetAsync(CB, 0, sizeof(int64_t) * n, st));
-    k_cell_accum<<<grid_for(n, 256), 256, 0, st>>>(key, val, n, idx, h.cnt, h.nA, CA, CB);
+    k_cell_accum<<<grid_for(n, 256), 256, 0, st>>>(key, val, n, idx, h.cnt, h.nA, CA, CB); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, sizeof(int64_t) * S_COUNT, cudaMemcpyDeviceToHost, st));
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
@@ -452,10 +452,10 @@ pd_status stage_condense_delta(Ctx* c, const Hats& h, int64_t G, int64_t P, uint
     int bm = bits_for((uint64_t)(hs[S_NMXX] - hs[S_NMNX]));
     int bm2 = bits_for((uint64_t)(hs[S_NMXY] - hs[S_NMNY]));
     if (bm2 > bm) bm = bm2;
-    k_morton_keys<<<grid_for(N, 256), 256, 0, st>>>(NX, NY, N, sm, key, val);
+    k_morton_keys<<<grid_for(N, 256), 256, 0, st>>>(NX, NY, N, sm, key, val); pd::count_launch();
     PD_TRY(sort_u64(c, key, key2, val, val2, N, 2 * bm, st));
     k_node_gather<<<grid_for(N, 256), 256, 0, st>>>(key, val, N, NX, NY, CA, CB, out->X, out->Y, out->cntA,
-                                                      out->cntB, out->morton);
+                                                      out->cntB, out->morton); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     out->n_nodes = N;
     return PD_OK;

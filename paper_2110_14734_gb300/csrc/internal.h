@@ -26,7 +26,7 @@ enum Buf : int {
     B_RS_COUNTS, B_RS_PART, B_SCAN_PART,
     B_M_ROWPTR, B_M_SUPPLY,
     B_NS_PI, B_NS_PARENT, B_NS_PRED, B_NS_DEPTH, B_NS_FLOW, B_NS_UP, B_NS_ORD, B_NS_POS, B_NS_SIZE, B_NS_TMP,
-    B_NS_PATH, B_NS_SEG, B_NS_INST, B_NS_COST, B_TR_S, B_TR_T, B_TR_SUP,
+    B_NS_PATH, B_NS_SEG, B_NS_INST, B_NS_COST, B_TR_S, B_TR_T, B_TR_SUP, B_TR_XCOST,
     B_SMALL,                        // small device scalars
     B_COUNT
 };
@@ -42,6 +42,7 @@ struct Ctx {
     pd_nodes nodes{};
     pd_network net{};
     int sm_count = 0;
+    float last_ns_ms = 0.f;  // device time of the last network simplex kernel
 };
 
 // Returns a device buffer of at least `bytes` bytes (contents undefined), or
@@ -86,12 +87,12 @@ struct Hats {
 
 struct SolveStats {
     int64_t opt = 0, slack = 0, rounds = 0, pushes = 0, relabels = 0, repairs = 0, updates = 0, update_passes = 0;
-    int64_t pivots = 0, degenerate = 0, cert_failures = 0;
+    int64_t pivots = 0, degenerate = 0, cert_failures = 0, scanned = 0;
     int32_t phases = 0, verified = 0, method = 0;  // method: 0 cost scaling, 1 simplex on the network, 2 transport form
 };
 
 struct NSOut {
-    int64_t opt = 0, pivots = 0, degenerate = 0;
+    int64_t opt = 0, pivots = 0, degenerate = 0, scanned = 0;
     int32_t status = 0;
 };
 

@@ -24,6 +24,12 @@ constexpr int NS_THREADS = 1024;
 struct NSInst {
     int32_t n;         // real nodes (root = n)
     int64_t m;         // real arcs
+    // arcs a < mst are implicit: tail a / nT, head nS + a % nT, cost cmat[a];
+    // arcs mst <= a < m are explicit: tail/head/cost[a - mst]
+    int64_t mst;
+    int64_t nT;
+    int64_t nS;
+    const int32_t* cmat;
     const int32_t* tail;
     const int32_t* head;
     const int32_t* cost;
@@ -41,6 +47,9 @@ struct NSInst {
     int32_t* path;     // n + 1 scratch (re-hang path)
     int32_t* seg;      // 4 * (2n + 3) scratch: segment start, length, output offset, depth shift
     int64_t block;     // pricing block (arcs)
+    int32_t smem_nodes; // 1: hot node arrays live in shared memory
+    int32_t pad0;
+    int64_t scanned;   // result: arcs priced
     int64_t max_pivots;
     uint64_t time_limit_ns;
     // results
@@ -58,9 +67,13 @@ PD_D uint64_t ns_now() {
 }
 
 PD_D void arc_ends(const NSInst& I, int64_t a, int32_t* t, int32_t* h) {
-    if (a < I.m) {
-        *t = I.tail[a];
-        *h = I.head[a];
+    if (a < I.mst) {
+        int64_t i = a / I.nT;
+        *t = (int32_t)i;
+        *h = (int32_t)(I.nS + (a - i * I.nT));
+    } else if (a < I.m) {
+        *t = I.tail[a - I.mst];
+        *h = I.head[a - I.mst];
     } else {
         int32_t i = (int32_t)(a - I.m);
         if (I.supply[i] >= 0) {
@@ -73,11 +86,41 @@ PD_D void arc_ends(const NSInst& I, int64_t a, int32_t* t, int32_t* h) {
     }
 }
 
+PD_D int64_t arc_cost(const NSInst& I, int64_t a, int64_t big) {
+    if (a < I.mst) return I.cmat[a];
+    if (a < I.m) return I.cost[a - I.mst];
+    return big;
+}
+
+PD_D void take_min(int64_t rc, int64_t a, int64_t& lb, int64_t& li) {
+    if (rc < lb || (rc == lb && rc < 0 && a < li)) {
+        lb = rc;
+        li = a;
+    }
+}
+
+// Bytes of dynamic shared memory for the hot node arrays of n + 1 nodes.
+inline size_t ns_smem_bytes(int64_t N1) { return (size_t)N1 * (8 + 8 + 4 + 4 + 1) + 64; }
+
 __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_t big) {
-    NSInst& I = insts[blockIdx.x];
+    NSInst& G = insts[blockIdx.x];
+    NSInst I = G;  // local copy: the hot arrays may be redirected to shared memory
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int32_t n = I.n, root = n, N1 = n + 1;
     const int64_t M = I.m + n;  // arcs including the artificial ones
+    extern __shared__ __align__(16) unsigned char dyn[];
+    if (I.smem_nodes) {
+        unsigned char* p = dyn;
+        I.pi = (int64_t*)p;
+        p += sizeof(int64_t) * N1;
+        I.flow = (int64_t*)p;
+        p += sizeof(int64_t) * N1;
+        I.parent = (int32_t*)p;
+        p += sizeof(int32_t) * N1;
+        I.depth = (int32_t*)p;
+        p += sizeof(int32_t) * N1;
+        I.up = (uint8_t*)p;
+    }
 
     __shared__ int64_t s_val[32];
     __shared__ int64_t s_idx[32];
@@ -119,7 +162,7 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
     }
     __syncthreads();
     const uint64_t t0 = ns_now();
-    int64_t pivots = 0, degen = 0;
+    int64_t pivots = 0, degen = 0, nscan = 0;
     const int64_t B = I.block < 1 ? 1 : I.block;
 
     for (;;) {
@@ -128,25 +171,44 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
         int64_t scanned = 0, a0 = s_next;
         int64_t best = 0, bidx = -1;
         while (scanned < M) {
-            int64_t len = B < M - scanned ? B : M - scanned;
+            const int64_t aend = a0 + B < M ? a0 + B : M;
+            const int64_t len = aend - a0;
             int64_t lb = 0, li = -1;
-            for (int64_t o = tid; o < len; o += NS_THREADS) {
-                int64_t a = a0 + o;
-                if (a >= M) a -= M;
-                int32_t t, h;
-                int64_t c;
-                if (a < I.m) {
-                    t = I.tail[a];
-                    h = I.head[a];
-                    c = I.cost[a];
+            // chunks of 8 consecutive arcs per thread, 16-byte vector loads
+            for (int64_t c0 = a0 + 8 * (int64_t)tid; c0 < aend; c0 += 8 * NS_THREADS) {
+                if (c0 + 8 <= aend && c0 + 8 <= I.mst) {
+                    int4 w0 = __ldcs((const int4*)(I.cmat + c0));
+                    int4 w1 = __ldcs((const int4*)(I.cmat + c0 + 4));
+                    int32_t cv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+                    int64_t i = c0 / I.nT, j = c0 - i * I.nT;
+                    int64_t pt = I.pi[i];
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        int64_t rc = (int64_t)cv[q] - pt + I.pi[I.nS + j];
+                        take_min(rc, c0 + q, lb, li);
+                        if (++j == I.nT) {
+                            j = 0;
+                            ++i;
+                            if (q < 7) pt = I.pi[i];
+                        }
+                    }
+                } else if (c0 >= I.mst && c0 + 8 <= aend && c0 + 8 <= I.m && ((c0 - I.mst) & 7) == 0) {
+                    const int64_t x = c0 - I.mst;
+                    int4 t0 = __ldcs((const int4*)(I.tail + x)), t1 = __ldcs((const int4*)(I.tail + x + 4));
+                    int4 h0 = __ldcs((const int4*)(I.head + x)), h1 = __ldcs((const int4*)(I.head + x + 4));
+                    int4 k0 = __ldcs((const int4*)(I.cost + x)), k1 = __ldcs((const int4*)(I.cost + x + 4));
+                    int32_t tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+                    int32_t hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+                    int32_t cv[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+#pragma unroll
+                    for (int q = 0; q < 8; q++) take_min((int64_t)cv[q] - I.pi[tv[q]] + I.pi[hv[q]], c0 + q, lb, li);
                 } else {
-                    arc_ends(I, a, &t, &h);
-                    c = big;
-                }
-                int64_t rc = c - I.pi[t] + I.pi[h];
-                if (rc < lb || (rc == lb && rc < 0 && a < li)) {
-                    lb = rc;
-                    li = a;
+                    int64_t ce = c0 + 8 < aend ? c0 + 8 : aend;
+                    for (int64_t a = c0; a < ce; a++) {
+                        int32_t t, h;
+                        arc_ends(I, a, &t, &h);
+                        take_min(arc_cost(I, a, big) - I.pi[t] + I.pi[h], a, lb, li);
+                    }
                 }
             }
             // CTA argmin (value, then index)
@@ -183,8 +245,8 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
             best = s_best;
             bidx = s_bidx;
             scanned += len;
-            a0 += len;
-            if (a0 >= M) a0 -= M;
+            nscan += len;
+            a0 = aend >= M ? 0 : aend;
             __syncthreads();
             if (best < 0) break;
         }
@@ -204,7 +266,7 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
             int64_t e = bidx;
             int32_t i, j;
             arc_ends(I, e, &i, &j);
-            int64_t ce = e < I.m ? (int64_t)I.cost[e] : big;
+            int64_t ce = arc_cost(I, e, big);
             int32_t u = i, v = j;
             while (u != v) {
                 int32_t du = I.depth[u], dv = I.depth[v];
@@ -374,11 +436,20 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
     }
     // ---- result ------------------------------------------------------------
     __syncthreads();
+    if (I.smem_nodes) {
+        for (int32_t v = tid; v < N1; v += NS_THREADS) {
+            G.pi[v] = I.pi[v];
+            G.flow[v] = I.flow[v];
+            G.parent[v] = I.parent[v];
+            G.depth[v] = I.depth[v];
+            G.up[v] = I.up[v];
+        }
+    }
     if (tid == 0) {
-        int st = s_status;
-        I.pivots = pivots;
-        I.degenerate = degen;
-        I.status = st;
+        G.pivots = pivots;
+        G.degenerate = degen;
+        G.scanned = nscan;
+        G.status = s_status;
     }
     // objective over tree arcs, and feasibility (no flow left on artificial arcs)
     __shared__ unsigned long long s_obj, s_art;
@@ -393,15 +464,15 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
         if (a >= I.m) {
             if (f != 0) art++;
         } else if (f > 0) {
-            obj += (unsigned long long)((int64_t)I.cost[a] * f);
+            obj += (unsigned long long)(arc_cost(I, a, big) * f);
         }
     }
     atomicAdd(&s_obj, obj);
     atomicAdd(&s_art, art);
     __syncthreads();
     if (tid == 0) {
-        I.opt = (int64_t)s_obj;
-        if (I.status == 0 && s_art) I.status = 1;
+        G.opt = (int64_t)s_obj;
+        if (s_status == 0 && s_art) G.status = 1;
     }
 }
 
@@ -419,14 +490,19 @@ __global__ void k_i64_to_i32_cost(const int64_t* __restrict__ c, int64_t m, int3
 }
 
 // Network simplex on an arc list (one CTA).  cmax = largest arc cost.
-pd_status ns_solve_arcs(Ctx* c, int32_t n, int64_t m, const int32_t* tail, const int32_t* head, const int32_t* cost,
-                        const int64_t* supply, int64_t cmax, const pd_opts& o, NSOut* out, cudaStream_t st) {
+pd_status ns_solve_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS, int64_t nT, const int32_t* cmat,
+                        const int32_t* tail, const int32_t* head, const int32_t* cost, const int64_t* supply,
+                        int64_t cmax, const pd_opts& o, NSOut* out, cudaStream_t st) {
     *out = NSOut{};
     if (n <= 0) return PD_OK;
     int64_t N1 = (int64_t)n + 1;
     NSInst h{};
     h.n = n;
     h.m = m;
+    h.mst = mst;
+    h.nS = nS;
+    h.nT = nT > 0 ? nT : 1;
+    h.cmat = cmat;
     h.tail = tail;
     h.head = head;
     h.cost = cost;
@@ -450,21 +526,39 @@ pd_status ns_solve_arcs(Ctx* c, int32_t n, int64_t m, const int32_t* tail, const
     int64_t M = m + n;
     int64_t blk = o.ns_block > 0 ? o.ns_block : (int64_t)sqrt((double)M);
     if (blk < 2048) blk = 2048;
+    blk = (blk + 7) & ~(int64_t)7;  // blocks start at multiples of 8 (vector loads)
     h.block = blk;
     h.max_pivots = o.max_rounds > 0 ? o.max_rounds : (int64_t(1) << 40);
     h.time_limit_ns = (o.time_limit_ms > 0 ? (uint64_t)o.time_limit_ms : 60000ull) * 1000000ull;
     // big-M: more than any path cost; |potentials| stay below ~3 big
     if (cmax > (INT64_MAX / 8) / N1) return fail(c, PD_EOVERFLOW, "network simplex big-M would overflow");
     int64_t big = N1 * (cmax + 1) + 1;
+    size_t smem = ns_smem_bytes(N1);
+    int max_optin = 0;
+    PD_TRY_CUDA(c, cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    h.smem_nodes = (o.ns_smem != 0 && smem + 4096 <= (size_t)max_optin) ? 1 : 0;
+    if (!h.smem_nodes) smem = 0;
+    PD_TRY_CUDA(c, cudaFuncSetAttribute(k_netsimplex, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     PD_TRY_CUDA(c, cudaMemcpyAsync(d, &h, sizeof(NSInst), cudaMemcpyHostToDevice, st));
-    k_netsimplex<<<1, NS_THREADS, 0, st>>>(d, big);
+    cudaEvent_t e0, e1;
+    PD_TRY_CUDA(c, cudaEventCreate(&e0));
+    PD_TRY_CUDA(c, cudaEventCreate(&e1));
+    PD_TRY_CUDA(c, cudaEventRecord(e0, st));
+    k_netsimplex<<<1, NS_THREADS, smem, st>>>(d, big); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
+    PD_TRY_CUDA(c, cudaEventRecord(e1, st));
     NSInst r;
     PD_TRY_CUDA(c, cudaMemcpyAsync(&r, d, sizeof(NSInst), cudaMemcpyDeviceToHost, st));
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    float nms = 0.f;
+    cudaEventElapsedTime(&nms, e0, e1);
+    c->last_ns_ms += nms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     out->opt = r.opt;
     out->pivots = r.pivots;
     out->degenerate = r.degenerate;
+    out->scanned = r.scanned;
     out->status = r.status;
     if (r.status == 2) return fail(c, PD_ETIMEOUT, "network simplex pivot cap or time limit reached");
     if (r.status == 1) return fail(c, PD_EINFEASIBLE, "network has no feasible flow");
@@ -506,8 +600,8 @@ __global__ void k_side_lists(const int64_t* __restrict__ cntA, const int64_t* __
 // diagonal node if its supply |B| - |A| is not 0.
 __global__ void k_transport_arcs(const int32_t* __restrict__ S, const int32_t* __restrict__ T, int64_t nS,
                                  int64_t nT, int dside, const int32_t* __restrict__ X, const int32_t* __restrict__ Y,
-                                 int32_t* __restrict__ tail, int32_t* __restrict__ head, int32_t* __restrict__ cost,
-                                 unsigned long long* __restrict__ bad) {
+                                 int32_t* __restrict__ cmat, int32_t* __restrict__ tail, int32_t* __restrict__ head,
+                                 int32_t* __restrict__ cost, unsigned long long* __restrict__ bad) {
     int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t mst = nS * nT;
     int64_t D = nS + nT;
@@ -518,25 +612,26 @@ __global__ void k_transport_arcs(const int32_t* __restrict__ S, const int32_t* _
         int64_t d = cost_l2(X[u], Y[u], X[v], Y[v]);
         int64_t g = cost_diag(X[u], Y[u]) + cost_diag(X[v], Y[v]);
         c = d < g ? d : g;
-        tail[a] = (int32_t)i;
-        head[a] = (int32_t)(nS + j);
+        if (c >= (int64_t(1) << 31)) atomicAdd(bad, 1ull);
+        cmat[a] = (int32_t)c;
+        return;
     } else if (dside < 0 && a < mst + nS) {
         int64_t i = a - mst;
         int32_t u = S[i];
         c = cost_diag(X[u], Y[u]);
-        tail[a] = (int32_t)i;
-        head[a] = (int32_t)D;
+        tail[a - mst] = (int32_t)i;
+        head[a - mst] = (int32_t)D;
     } else if (dside > 0 && a < mst + nT) {
         int64_t j = a - mst;
         int32_t v = T[j];
         c = cost_diag(X[v], Y[v]);
-        tail[a] = (int32_t)D;
-        head[a] = (int32_t)(nS + j);
+        tail[a - mst] = (int32_t)D;
+        head[a - mst] = (int32_t)(nS + j);
     } else {
         return;
     }
     if (c >= (int64_t(1) << 31)) atomicAdd(bad, 1ull);
-    cost[a] = (int32_t)c;
+    cost[a - mst] = (int32_t)c;
 }
 
 // Certificate: every source->sink pair that carries flow on its direct route
@@ -599,9 +694,9 @@ pd_status ns_solve_network(Ctx* c, const pd_network& net, const pd_opts& o, Solv
     if (!tail || !c32 || !sm) return PD_ENOMEM;
     PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, 8 * sizeof(unsigned long long), st));
     if (m > 0) {
-        k_arc_tails<<<grid_for(m, 256), 256, 0, st>>>(net.row_ptr, n, m, tail);
-        k_i64_to_i32_cost<<<grid_for(m, 256), 256, 0, st>>>(net.cost, m, c32, sm);
-        k_max_cost<<<grid_for(m, 256), 256, 0, st>>>(net.cost, m, sm + 1);
+        k_arc_tails<<<grid_for(m, 256), 256, 0, st>>>(net.row_ptr, n, m, tail); pd::count_launch();
+        k_i64_to_i32_cost<<<grid_for(m, 256), 256, 0, st>>>(net.cost, m, c32, sm); pd::count_launch();
+        k_max_cost<<<grid_for(m, 256), 256, 0, st>>>(net.cost, m, sm + 1); pd::count_launch();
     }
     PD_TRY_CUDA(c, cudaGetLastError());
     PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -609,15 +704,16 @@ pd_status ns_solve_network(Ctx* c, const pd_network& net, const pd_opts& o, Solv
     if (c->h_small[0]) return fail(c, PD_EOVERFLOW, "arc cost outside [0, 2^31)");
     int64_t cmax = c->h_small[1];
     NSOut r;
-    PD_TRY(ns_solve_arcs(c, (int32_t)n, m, tail, net.head, c32, net.supply, cmax, o, &r, st));
+    PD_TRY(ns_solve_arcs(c, (int32_t)n, m, 0, 0, 1, nullptr, tail, net.head, c32, net.supply, cmax, o, &r, st));
     PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, sizeof(unsigned long long), st));
-    k_tree_flow<<<grid_for(n, 256), 256, 0, st>>>(bufT<NSInst>(c, B_NS_INST, 1), sm);
+    k_tree_flow<<<grid_for(n, 256), 256, 0, st>>>(bufT<NSInst>(c, B_NS_INST, 1), sm); pd::count_launch();
     PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     out->opt = r.opt;
     out->slack = c->h_small[0];
     out->pivots = r.pivots;
     out->degenerate = r.degenerate;
+    out->scanned = r.scanned;
     out->verified = 1;  // the pricing loop ends only when no arc has a negative reduced cost
     out->method = 1;
     return PD_OK;
@@ -635,7 +731,7 @@ pd_status ns_solve_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const
     int64_t* ft = bufT<int64_t>(c, B_WSOFF, N);
     unsigned long long* sm = bufT<unsigned long long>(c, B_SMALL, 64);
     if (!fs || !ft || !sm) return PD_ENOMEM;
-    k_side_flags<<<grid_for(N, 256), 256, 0, st>>>(nodes.cntA, nodes.cntB, N, fs, ft);
+    k_side_flags<<<grid_for(N, 256), 256, 0, st>>>(nodes.cntA, nodes.cntB, N, fs, ft); pd::count_launch();
     PD_TRY(scan_i64(c, fs, fs, N, (int64_t*)sm + 2, st));
     PD_TRY(scan_i64(c, ft, ft, N, (int64_t*)sm + 3, st));
     PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -653,31 +749,36 @@ pd_status ns_solve_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const
         int32_t* S = bufT<int32_t>(c, B_TR_S, nS);
         int32_t* T = bufT<int32_t>(c, B_TR_T, nT);
         int64_t* sup = bufT<int64_t>(c, B_TR_SUP, nt);
-        int32_t* tail = bufT<int32_t>(c, B_S_TAIL, mt);
-        int32_t* head = bufT<int32_t>(c, B_S_HEAD, mt);
-        int32_t* cost = bufT<int32_t>(c, B_NS_COST, mt);
-        if (!S || !T || !sup || !tail || !head || !cost) return PD_ENOMEM;
-        k_side_lists<<<grid_for(N, 256), 256, 0, st>>>(nodes.cntA, nodes.cntB, N, fs, ft, S, T, sup, nS);
+        int64_t mx = mt - mst;
+        int32_t* cmat = bufT<int32_t>(c, B_NS_COST, mst);
+        int32_t* tail = bufT<int32_t>(c, B_S_TAIL, mx);
+        int32_t* head = bufT<int32_t>(c, B_S_HEAD, mx);
+        int32_t* cost = bufT<int32_t>(c, B_TR_XCOST, mx);
+        if (!S || !T || !sup || !tail || !head || !cost || !cmat) return PD_ENOMEM;
+        k_side_lists<<<grid_for(N, 256), 256, 0, st>>>(nodes.cntA, nodes.cntB, N, fs, ft, S, T, sup, nS); pd::count_launch();
         PD_TRY_CUDA(c, cudaMemcpyAsync(sup + nS + nT, &dsup, sizeof(int64_t), cudaMemcpyHostToDevice, st));
         PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, 8 * sizeof(unsigned long long), st));
         if (mt > 0)
             k_transport_arcs<<<grid_for(mt, 256), 256, 0, st>>>(S, T, nS, nT, dsup < 0 ? -1 : (dsup > 0 ? 1 : 0),
-                                                                  nodes.X, nodes.Y, tail, head, cost, sm);
+                                                                  nodes.X, nodes.Y, cmat, tail, head, cost, sm); pd::count_launch();
         PD_TRY_CUDA(c, cudaGetLastError());
-        k_max_cost32<<<grid_for(mt, 256), 256, 0, st>>>(cost, mt, sm + 1);
+        if (mst > 0) k_max_cost32<<<grid_for(mst, 256), 256, 0, st>>>(cmat, mst, sm + 1); pd::count_launch();
+        if (mx > 0) k_max_cost32<<<grid_for(mx, 256), 256, 0, st>>>(cost, mx, sm + 1); pd::count_launch();
         PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         PD_TRY_CUDA(c, cudaStreamSynchronize(st));
         if (c->h_small[0] == 0) {
             NSOut r;
-            PD_TRY(ns_solve_arcs(c, (int32_t)nt, mt, tail, head, cost, sup, c->h_small[1], o, &r, st));
+            PD_TRY(ns_solve_arcs(c, (int32_t)nt, mt, mst, nS, nT, cmat, tail, head, cost, sup, c->h_small[1], o, &r,
+                                 st));
             PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, 4 * sizeof(unsigned long long), st));
             k_certify_transport<<<grid_for(nt, 256), 256, 0, st>>>(bufT<NSInst>(c, B_NS_INST, 1), S, T, nS, nT,
-                                                                    nodes.X, nodes.Y, ws.row_ptr, ws.head, sm);
+                                                                    nodes.X, nodes.Y, ws.row_ptr, ws.head, sm); pd::count_launch();
             PD_TRY_CUDA(c, cudaGetLastError());
             PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
             PD_TRY_CUDA(c, cudaStreamSynchronize(st));
             out->pivots = r.pivots;
             out->degenerate = r.degenerate;
+            out->scanned = r.scanned;
             if (c->h_small[0] == 0) {
                 out->opt = r.opt;
                 out->slack = c->h_small[1];
@@ -688,9 +789,10 @@ pd_status ns_solve_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const
             out->cert_failures = c->h_small[0];
         }
     }
-    int64_t piv = out->pivots, fails = out->cert_failures;
+    int64_t piv = out->pivots, fails = out->cert_failures, scn = out->scanned;
     PD_TRY(ns_solve_network(c, merged, o, out, st));
     out->pivots += piv;
+    out->scanned += scn;
     out->cert_failures = fails;
     return PD_OK;
 }

@@ -132,9 +132,9 @@ cudaError_t exclusive_scan(const T* in, T* out, int64_t n, T* part, T* total_dev
         return cudaSuccess;
     }
     int64_t nb = scan_tiles(n);
-    k_tile_sum<T><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, part);
-    k_scan_partials<T><<<1, 1024, 0, st>>>(part, nb, total_dev);
-    k_tile_scan<T><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, part);
+    k_tile_sum<T><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, part); pd::count_launch();
+    k_scan_partials<T><<<1, 1024, 0, st>>>(part, nb, total_dev); pd::count_launch();
+    k_tile_scan<T><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, part); pd::count_launch();
     return cudaGetLastError();
 }
 
@@ -232,10 +232,10 @@ cudaError_t radix_sort(K* keys, uint32_t* vals, int64_t n, int bits, RadixScratc
     int passes = (bits + 7) / 8;
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
-        k_radix_hist<K><<<(unsigned)nb, RS_THREADS, 0, st>>>(ka, n, shift, nb, s.counts);
+        k_radix_hist<K><<<(unsigned)nb, RS_THREADS, 0, st>>>(ka, n, shift, nb, s.counts); pd::count_launch();
         cudaError_t e = exclusive_scan<int64_t>(s.counts, s.counts, 256 * nb, s.part, nullptr, st);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<K><<<(unsigned)nb, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, nb, s.counts);
+        k_radix_scatter<K><<<(unsigned)nb, RS_THREADS, 0, st>>>(ka, va, kb, vb, n, shift, nb, s.counts); pd::count_launch();
         K* t = ka;
         ka = kb;
         kb = t;

@@ -842,7 +842,7 @@ pd_status validate_network(Ctx* c, const pd_network& net, cudaStream_t st) {
     unsigned long long* sm = bufT<unsigned long long>(c, B_SMALL, 64);
     if (!sm) return PD_ENOMEM;
     PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, sizeof(unsigned long long), st));
-    k_check_network<<<grid_for(n, 256), 256, 0, st>>>(net.row_ptr, net.head, n, m, sm);
+    k_check_network<<<grid_for(n, 256), 256, 0, st>>>(net.row_ptr, net.head, n, m, sm); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
@@ -871,10 +871,10 @@ pd_status stage_solve(Ctx* c, const pd_network& net, const pd_opts& o, SolveStat
     int64_t* xpos = bufT<int64_t>(c, B_S_XPOS, m);
     if (!sm || !tail || !pair || !xkey || !xkey2 || !xval || !xval2 || !xptr || !xpos) return PD_ENOMEM;
     PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, 64 * sizeof(unsigned long long), st));
-    k_arc_tails<<<grid_for(m, 256), 256, 0, st>>>(net.row_ptr, n, m, tail);
+    k_arc_tails<<<grid_for(m, 256), 256, 0, st>>>(net.row_ptr, n, m, tail); pd::count_launch();
     k_pairing<<<grid_for(m, 256), 256, 0, st>>>(net.row_ptr, net.head, net.cost, tail, m, hb, sent, pair, xkey, xval,
-                                                 (int*)&sm[0], &sm[2]);
-    k_max_cost<<<grid_for(m, 256), 256, 0, st>>>(net.cost, m, &sm[1]);
+                                                 (int*)&sm[0], &sm[2]); pd::count_launch();
+    k_max_cost<<<grid_for(m, 256), 256, 0, st>>>(net.cost, m, &sm[1]); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     PD_TRY(sort_u64(c, xkey, xkey2, xval, xval2, m, 2 * hb, st));
     PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -886,7 +886,7 @@ pd_status stage_solve(Ctx* c, const pd_network& net, const pd_opts& o, SolveStat
         int64_t ms = m + E;
         // rows of the extras
         if (E > 0) {
-            k_row_ptr<<<grid_for(E, 256), 256, 0, st>>>(xkey, E, hb, n, xptr);
+            k_row_ptr<<<grid_for(E, 256), 256, 0, st>>>(xkey, E, hb, n, xptr); pd::count_launch();
         } else {
             PD_TRY_CUDA(c, cudaMemsetAsync(xptr, 0, sizeof(int64_t) * (n + 1), st));
         }
@@ -902,15 +902,15 @@ pd_status stage_solve(Ctx* c, const pd_network& net, const pd_opts& o, SolveStat
         int8_t* srl = bufT<int8_t>(c, B_S_RELAB, n);
         SolverCtl* ctl = bufT<SolverCtl>(c, B_S_CTL, 1);
         if (!srp || !shd || !scw || !stw || !sx || !se || !sp || !scur || !srl || !ctl || !sd) return PD_ENOMEM;
-        k_sym_rowptr<<<grid_for(n + 1, 256), 256, 0, st>>>(net.row_ptr, xptr, n, srp);
+        k_sym_rowptr<<<grid_for(n + 1, 256), 256, 0, st>>>(net.row_ptr, xptr, n, srp); pd::count_launch();
         if (E > 0)
             k_fill_extra<<<grid_for(E, 256), 256, 0, st>>>(xkey, xval, E, hb, net.row_ptr, xptr, srp, net.cost, shd,
-                                                           scw, stw, xpos);
+                                                           scw, stw, xpos); pd::count_launch();
         k_fill_dir<<<grid_for(m, 256), 256, 0, st>>>(net.row_ptr, net.head, net.cost, tail, pair, xpos, m, srp, shd,
-                                                      scw, stw);
+                                                      scw, stw); pd::count_launch();
         PD_TRY_CUDA(c, cudaMemsetAsync(sx, 0, sizeof(int64_t) * ms, st));
         PD_TRY_CUDA(c, cudaMemsetAsync(sp, 0, sizeof(int64_t) * n, st));
-        k_copy_i64<<<grid_for(n, 256), 256, 0, st>>>(net.supply, se, n);
+        k_copy_i64<<<grid_for(n, 256), 256, 0, st>>>(net.supply, se, n); pd::count_launch();
         PD_TRY_CUDA(c, cudaMemsetAsync(ctl, 0, sizeof(SolverCtl), st));
         PD_TRY_CUDA(c, cudaGetLastError());
 
@@ -954,9 +954,10 @@ pd_status stage_solve(Ctx* c, const pd_network& net, const pd_opts& o, SolveStat
         int blocks = c->sm_count * (int)per_sm;
         void* kargs[] = {&args};
         PD_TRY_CUDA(c, cudaLaunchCooperativeKernel((const void*)k_solve, dim3(blocks), dim3(SV_THREADS), kargs, 0, st));
+        pd::count_launch();
         PD_TRY_CUDA(c, cudaMemsetAsync(sm + 4, 0, 8 * sizeof(unsigned long long), st));
-        k_objective<<<grid_for(ms, 256), 256, 0, st>>>(scw, sx, ms, sm + 4);
-        if (o.verify) k_certify<<<grid_for(n * 32, 256), 256, 0, st>>>(srp, shd, scw, sx, se, sp, n, K, sm + 8);
+        k_objective<<<grid_for(ms, 256), 256, 0, st>>>(scw, sx, ms, sm + 4); pd::count_launch();
+        if (o.verify) k_certify<<<grid_for(n * 32, 256), 256, 0, st>>>(srp, shd, scw, sx, se, sp, n, K, sm + 8); pd::count_launch();
         PD_TRY_CUDA(c, cudaGetLastError());
         SolverCtl hc;
         PD_TRY_CUDA(c, cudaMemcpyAsync(&hc, ctl, sizeof(SolverCtl), cudaMemcpyDeviceToHost, st));

@@ -285,7 +285,7 @@ pd_status validate_nodes(Ctx* c, const pd_nodes& nodes, cudaStream_t st) {
     unsigned long long* sm = bufT<unsigned long long>(c, B_SMALL, 64);
     if (!sm) return PD_ENOMEM;
     PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, sizeof(unsigned long long), st));
-    k_check_nodes<<<grid_for(N, 256), 256, 0, st>>>(nodes.morton, nodes.X, nodes.Y, nodes.cntA, nodes.cntB, N, sm);
+    k_check_nodes<<<grid_for(N, 256), 256, 0, st>>>(nodes.morton, nodes.X, nodes.Y, nodes.cntA, nodes.cntB, N, sm); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
@@ -311,7 +311,7 @@ pd_status merge_diagonal(Ctx* c, const pd_network& net, int64_t N, pd_network* o
     int64_t* mrp = bufT<int64_t>(c, B_M_ROWPTR, N + 2);
     int64_t* msup = bufT<int64_t>(c, B_M_SUPPLY, N + 1);
     if (!mrp || !msup) return PD_ENOMEM;
-    k_merge_diag<<<grid_for(N + 2, 256), 256, 0, st>>>(net.row_ptr, net.supply, N, net.n_arcs, mrp, msup);
+    k_merge_diag<<<grid_for(N + 2, 256), 256, 0, st>>>(net.row_ptr, net.supply, N, net.n_arcs, mrp, msup); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     out->n_nodes = N + 1;
     out->n_arcs = net.n_arcs - 1;
@@ -341,9 +341,9 @@ pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* ou
     unsigned long long* cnts = bufT<unsigned long long>(c, B_SMALL, 64);
     if (!left || !right || !bb || !rep || !par_int || !par_leaf || !visit || !cnts) return PD_ENOMEM;
     if (N >= 2) {
-        k_karras<<<grid_for(N - 1, 256), 256, 0, st>>>(nodes.morton, N, left, right, par_int, par_leaf);
+        k_karras<<<grid_for(N - 1, 256), 256, 0, st>>>(nodes.morton, N, left, right, par_int, par_leaf); pd::count_launch();
         PD_TRY_CUDA(c, cudaMemsetAsync(visit, 0, sizeof(int32_t) * M, st));
-        k_bbox<<<grid_for(N, 256), 256, 0, st>>>(N, nodes.X, nodes.Y, left, right, par_int, par_leaf, bb, rep, visit);
+        k_bbox<<<grid_for(N, 256), 256, 0, st>>>(N, nodes.X, nodes.Y, left, right, par_int, par_leaf, bb, rep, visit); pd::count_launch();
         PD_TRY_CUDA(c, cudaGetLastError());
     }
     PD_TRY_CUDA(c, cudaEventRecord(ev[1], st));
@@ -356,7 +356,7 @@ pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* ou
     int64_t fcap = nf > 0 ? nf : 1;
     int2* F = bufT<int2>(c, B_F0, fcap);
     if (!F) return PD_ENOMEM;
-    if (nf > 0) k_frontier_init<<<grid_for(nf, 256), 256, 0, st>>>(N, left, right, F);
+    if (nf > 0) k_frontier_init<<<grid_for(nf, 256), 256, 0, st>>>(N, left, right, F); pd::count_launch();
     int64_t narcs = 0;
     int64_t acap = 0;
     uint64_t* arcs = nullptr;
@@ -366,7 +366,7 @@ pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* ou
         int64_t* flag = bufT<int64_t>(c, B_WSFLAG, nf);
         int64_t* off = bufT<int64_t>(c, B_WSOFF, nf);
         if (!flag || !off) return PD_ENOMEM;
-        k_ws_classify<<<grid_for(nf, 256), 256, 0, st>>>(F, nf, nodes.X, nodes.Y, bb, rep, left, right, s, flag, off);
+        k_ws_classify<<<grid_for(nf, 256), 256, 0, st>>>(F, nf, nodes.X, nodes.Y, bb, rep, left, right, s, flag, off); pd::count_launch();
         PD_TRY(scan_i64(c, off, off, nf, (int64_t*)cnts + 8, st));
         PD_TRY_CUDA(c, cudaMemcpyAsync(h, (int64_t*)cnts + 8, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         PD_TRY_CUDA(c, cudaStreamSynchronize(st));
@@ -389,7 +389,7 @@ pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* ou
         if (!Fn) return PD_ENOMEM;
         // F may have moved if its buffer grew: it did not (only Fn's buffer is resized here)
         k_ws_expand<<<grid_for(nf, 256), 256, 0, st>>>(F, nf, flag, off, nodes.X, nodes.Y, bb, rep, left, right, hb,
-                                                        arcs + narcs, Fn);
+                                                        arcs + narcs, Fn); pd::count_launch();
         PD_TRY_CUDA(c, cudaGetLastError());
         narcs += 2 * nws;
         nf = nn;
@@ -404,8 +404,8 @@ pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* ou
     }
     // diagonal arcs + masses
     PD_TRY_CUDA(c, cudaMemsetAsync(cnts, 0, 8 * sizeof(unsigned long long), st));
-    k_diag_arcs<<<grid_for(N + 1, 256), 256, 0, st>>>(N, nodes.cntA, nodes.cntB, hb, sent, arcs + narcs, cnts);
-    k_mass<<<grid_for(N, 256), 256, 0, st>>>(N, nodes.cntA, nodes.cntB, cnts);
+    k_diag_arcs<<<grid_for(N + 1, 256), 256, 0, st>>>(N, nodes.cntA, nodes.cntB, hb, sent, arcs + narcs, cnts); pd::count_launch();
+    k_mass<<<grid_for(N, 256), 256, 0, st>>>(N, nodes.cntA, nodes.cntB, cnts); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     PD_TRY_CUDA(c, cudaMemcpyAsync(h, cnts, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     int64_t ntot = narcs + 2 * N + 1;
@@ -423,9 +423,9 @@ pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* ou
     out->cost = bufT<int64_t>(c, B_COST, m);
     out->supply = bufT<int64_t>(c, B_SUPPLY, nrows);
     if (!out->row_ptr || !out->head || !out->cost || !out->supply) return PD_ENOMEM;
-    k_row_ptr<<<grid_for(m, 256), 256, 0, st>>>(arcs, m, hb, nrows, out->row_ptr);
-    k_head_cost<<<grid_for(m, 256), 256, 0, st>>>(arcs, m, hb, N, nodes.X, nodes.Y, out->head, out->cost);
-    k_supply<<<grid_for(N + 2, 256), 256, 0, st>>>(N, nodes.cntA, nodes.cntB, FA, FB, out->supply);
+    k_row_ptr<<<grid_for(m, 256), 256, 0, st>>>(arcs, m, hb, nrows, out->row_ptr); pd::count_launch();
+    k_head_cost<<<grid_for(m, 256), 256, 0, st>>>(arcs, m, hb, N, nodes.X, nodes.Y, out->head, out->cost); pd::count_launch();
+    k_supply<<<grid_for(N + 2, 256), 256, 0, st>>>(N, nodes.cntA, nodes.cntB, FA, FB, out->supply); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     PD_TRY_CUDA(c, cudaEventRecord(ev[3], st));
     PD_TRY_CUDA(c, cudaEventSynchronize(ev[3]));

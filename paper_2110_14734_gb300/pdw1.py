@@ -35,7 +35,7 @@ class pd_opts(C.Structure):
                 ("perturb", C.c_int32), ("seed", C.c_uint64), ("alpha", C.c_int32), ("verify", C.c_int32),
                 ("max_rounds", C.c_int64), ("time_limit_ms", C.c_int64), ("update_every", C.c_int64),
                 ("seq_threshold", C.c_int32), ("solver", C.c_int32), ("ns_block", C.c_int64),
-                ("ns_transport", C.c_int32), ("reserved", C.c_int32)]
+                ("ns_transport", C.c_int32), ("ns_smem", C.c_int32)]
 
 
 class pd_nodes(C.Structure):
@@ -56,8 +56,10 @@ class pd_result(C.Structure):
                 ("n_nodes", C.c_int64), ("n_arcs", C.c_int64), ("phases", C.c_int32), ("verified", C.c_int32),
                 ("rounds", C.c_int64), ("pushes", C.c_int64), ("relabels", C.c_int64),
                 ("repair_passes", C.c_int64), ("price_updates", C.c_int64), ("update_passes", C.c_int64),
-                ("pivots", C.c_int64), ("degenerate", C.c_int64), ("solve_method", C.c_int32),
-                ("cert_failures", C.c_int32), ("stage_ms", C.c_float * 8)]
+                ("pivots", C.c_int64), ("degenerate", C.c_int64), ("arcs_priced", C.c_int64),
+                ("solve_method", C.c_int32),
+                ("cert_failures", C.c_int32), ("kernel_launches", C.c_int64), ("ns_kernel_ms", C.c_float),
+                ("reserved", C.c_int32), ("stage_ms", C.c_float * 8)]
 
     def to_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "stage_ms"}
