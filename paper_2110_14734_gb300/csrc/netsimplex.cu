@@ -38,13 +38,13 @@ struct NSInst {
     int32_t* parent;   // n + 1
     int64_t* pred;     // n + 1 (arc id; artificial arc of node i is m + i)
     int32_t* depth;    // n + 1
-    int64_t* flow;     // n + 1: flow on the pred arc
+    int32_t* flow;     // n + 1: flow on the pred arc (total supply < 2^31)
     uint8_t* up;       // n + 1: pred arc points from the node to its parent
     int32_t* ord;      // n + 1 preorder
     int32_t* pos;      // n + 1
     int32_t* size;     // n + 1
     int32_t* tmp;      // n + 1 scratch
-    int32_t* path;     // n + 1 scratch (re-hang path)
+    int32_t* path;     // 2 (n + 1) scratch: the two half-cycles past the shared-memory part
     int32_t* seg;      // 4 * (2n + 3) scratch: segment start, length, output offset, depth shift
     int64_t block;     // pricing block (arcs)
     int32_t smem_nodes; // 1: hot node arrays live in shared memory
@@ -100,7 +100,9 @@ PD_D void take_min(int64_t rc, int64_t a, int64_t& lb, int64_t& li) {
 }
 
 // Bytes of dynamic shared memory for the hot node arrays of n + 1 nodes.
-inline size_t ns_smem_bytes(int64_t N1) { return (size_t)N1 * (8 + 8 + 4 + 4 + 1) + 64; }
+inline size_t ns_smem_bytes(int64_t N1) { return (size_t)N1 * (8 + 4 + 4 + 4 + 4 + 4 + 1) + 64; }
+
+constexpr int NS_LMAX = 512;  // half-cycle entries kept in shared memory
 
 __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_t big) {
     NSInst& G = insts[blockIdx.x];
@@ -113,14 +115,23 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
         unsigned char* p = dyn;
         I.pi = (int64_t*)p;
         p += sizeof(int64_t) * N1;
-        I.flow = (int64_t*)p;
-        p += sizeof(int64_t) * N1;
+        I.flow = (int32_t*)p;
+        p += sizeof(int32_t) * N1;
         I.parent = (int32_t*)p;
         p += sizeof(int32_t) * N1;
         I.depth = (int32_t*)p;
         p += sizeof(int32_t) * N1;
+        I.size = (int32_t*)p;
+        p += sizeof(int32_t) * N1;
+        I.pos = (int32_t*)p;
+        p += sizeof(int32_t) * N1;
         I.up = (uint8_t*)p;
     }
+    __shared__ int32_t pa[NS_LMAX], pb[NS_LMAX];
+    int32_t* gpa = I.path;
+    int32_t* gpb = I.path + N1;
+    __shared__ int32_t s_la, s_lb, s_join, s_i, s_j;
+    __shared__ int64_t s_ce;
 
     __shared__ int64_t s_val[32];
     __shared__ int64_t s_idx[32];
@@ -140,7 +151,7 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
         I.parent[i] = root;
         I.pred[i] = I.m + i;
         I.up[i] = s >= 0;
-        I.flow[i] = s >= 0 ? s : -s;
+        I.flow[i] = (int32_t)(s >= 0 ? s : -s);
         I.pi[i] = s >= 0 ? big : -big;  // reduced cost of the artificial arc is 0
         I.depth[i] = 1;
         I.ord[1 + i] = i;
@@ -260,65 +271,131 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
         }
         pivots++;
 
-        // ---- sequential pivot walk (thread 0) ---------------------------------
-        if (tid == 0) {
-            s_next = a0;
-            int64_t e = bidx;
-            int32_t i, j;
-            arc_ends(I, e, &i, &j);
-            int64_t ce = arc_cost(I, e, big);
-            int32_t u = i, v = j;
-            while (u != v) {
-                int32_t du = I.depth[u], dv = I.depth[v];
-                if (du > dv)
-                    u = I.parent[u];
-                else if (dv > du)
-                    v = I.parent[v];
-                else {
-                    u = I.parent[u];
-                    v = I.parent[v];
+        // ---- pivot: apex walk (one thread), then the two recorded half-cycles
+        // are processed by warp 0 (leaving arc, flows, ancestor sizes) ---------
+        if (wid == 0) {
+            if (lane == 0) {
+                s_next = a0;
+                int64_t e = bidx;
+                int32_t i, j;
+                arc_ends(I, e, &i, &j);
+                s_ce = arc_cost(I, e, big);
+                int32_t u = i, v = j, la = 0, lb = 0;
+                while (u != v) {
+                    int32_t du = I.depth[u], dv = I.depth[v];
+                    if (du >= dv) {
+                        if (la < NS_LMAX) pa[la] = u; else gpa[la] = u;
+                        la++;
+                        u = I.parent[u];
+                    }
+                    if (dv >= du) {
+                        if (lb < NS_LMAX) pb[lb] = v; else gpb[lb] = v;
+                        lb++;
+                        v = I.parent[v];
+                    }
+                }
+                s_la = la;
+                s_lb = lb;
+                s_join = u;
+                s_i = i;
+                s_j = j;
+            }
+            __syncwarp();
+            const int32_t la = s_la, lb = s_lb, i = s_i, j = s_j;
+#define PA(t) ((t) < NS_LMAX ? pa[t] : gpa[t])
+#define PB(t) ((t) < NS_LMAX ? pb[t] : gpb[t])
+            // leaving arc: last blocking arc walking from the apex along the
+            // cycle -- on the i-side the one closest to i (smallest index), on
+            // the j-side the one closest to the apex (largest index), j-side
+            // preferred on ties.
+            int64_t fi = INT64_MAX, ti = INT32_MAX, fj = INT64_MAX, tj = -1;
+            for (int32_t t = lane; t < la; t += 32) {
+                int32_t x = PA(t);
+                if (I.up[x]) {
+                    int64_t f = I.flow[x];
+                    if (f < fi || (f == fi && t < ti)) {
+                        fi = f;
+                        ti = t;
+                    }
                 }
             }
-            const int32_t join = u;
-            int64_t delta = INT64_MAX;
-            int32_t leave = -1, side = 0;
-            for (int32_t x = i; x != join; x = I.parent[x])
-                if (I.up[x] && I.flow[x] < delta) {
-                    delta = I.flow[x];
-                    leave = x;
-                    side = 1;
+            for (int32_t t = lane; t < lb; t += 32) {
+                int32_t x = PB(t);
+                if (!I.up[x]) {
+                    int64_t f = I.flow[x];
+                    if (f < fj || (f == fj && t > tj)) {
+                        fj = f;
+                        tj = t;
+                    }
                 }
-            for (int32_t x = j; x != join; x = I.parent[x])
-                if (!I.up[x] && I.flow[x] <= delta) {
-                    delta = I.flow[x];
-                    leave = x;
-                    side = 2;
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                int64_t of = __shfl_xor_sync(0xffffffffu, fi, off);
+                int64_t ot = __shfl_xor_sync(0xffffffffu, ti, off);
+                if (of < fi || (of == fi && ot < ti)) {
+                    fi = of;
+                    ti = ot;
                 }
-            s_go = 0;
-            if (leave < 0) {
-                s_status = 3;
+                of = __shfl_xor_sync(0xffffffffu, fj, off);
+                ot = __shfl_xor_sync(0xffffffffu, tj, off);
+                if (of < fj || (of == fj && ot > tj)) {
+                    fj = of;
+                    tj = ot;
+                }
+            }
+            int side;
+            int64_t delta;
+            int32_t tl;
+            if (tj >= 0 && fj <= fi) {
+                side = 2;
+                delta = fj;
+                tl = (int32_t)tj;
+            } else if (ti != INT32_MAX) {
+                side = 1;
+                delta = fi;
+                tl = (int32_t)ti;
+            } else {
+                side = 0;
+                delta = 0;
+                tl = 0;
+            }
+            if (side == 0) {
+                if (lane == 0) {
+                    s_status = 3;
+                    s_go = 0;
+                }
             } else {
                 if (delta > 0) {
-                    for (int32_t x = i; x != join; x = I.parent[x]) I.flow[x] += I.up[x] ? -delta : delta;
-                    for (int32_t x = j; x != join; x = I.parent[x]) I.flow[x] += I.up[x] ? delta : -delta;
+                    const int32_t d32 = (int32_t)delta;
+                    for (int32_t t = lane; t < la; t += 32) {
+                        int32_t x = PA(t);
+                        I.flow[x] += I.up[x] ? -d32 : d32;
+                    }
+                    for (int32_t t = lane; t < lb; t += 32) {
+                        int32_t x = PB(t);
+                        I.flow[x] += I.up[x] ? d32 : -d32;
+                    }
+                }
+                const int32_t leave = side == 1 ? PA(tl) : PB(tl);
+                const int32_t S = I.size[leave];
+                __syncwarp();
+                // the cut subtree leaves the chain above `leave` and joins r's chain
+                if (side == 1) {
+                    for (int32_t t = tl + 1 + lane; t < la; t += 32) I.size[PA(t)] -= S;
+                    for (int32_t t = lane; t < lb; t += 32) I.size[PB(t)] += S;
                 } else {
-                    degen++;
+                    for (int32_t t = tl + 1 + lane; t < lb; t += 32) I.size[PB(t)] -= S;
+                    for (int32_t t = lane; t < la; t += 32) I.size[PA(t)] += S;
                 }
-                const int32_t q = side == 1 ? i : j, r = side == 1 ? j : i;
-                int64_t rc = ce - I.pi[i] + I.pi[j];
-                s_dpi = side == 1 ? rc : -rc;
-                // path q = v0, v1, ..., vk = leave
-                int32_t k = 0;
-                I.path[0] = q;
-                while (I.path[k] != leave) {
-                    I.path[k + 1] = I.parent[I.path[k]];
-                    k++;
-                }
-                {
-                    const int32_t S = I.size[leave];
-                    // ancestors: the cut subtree leaves the chain above leave and joins the chain of r
-                    for (int32_t x = I.parent[leave]; x != join; x = I.parent[x]) I.size[x] -= S;
-                    for (int32_t x = r; x != join; x = I.parent[x]) I.size[x] += S;
+                __syncwarp();
+                if (lane == 0) {
+                    if (delta == 0) degen++;
+                    const int64_t e = bidx;
+                    const int32_t q = side == 1 ? i : j, r = side == 1 ? j : i;
+                    int64_t rc = s_ce - I.pi[i] + I.pi[j];
+                    s_dpi = side == 1 ? rc : -rc;
+                    const int32_t k = tl;  // path q = v0 .. vk = leave
+#define PV(t) (side == 1 ? PA(t) : PB(t))
                     // new preorder of the cut subtree, re-rooted at q, as segments of the old order
                     const int32_t dr = I.depth[r];
                     int32_t ns = 0, out = 0;
@@ -329,7 +406,7 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
                     out += seg_len[ns];
                     ns++;
                     for (int32_t t = 1; t <= k; t++) {
-                        int32_t vt = I.path[t], vp = I.path[t - 1];
+                        int32_t vt = PV(t), vp = PV(t - 1);
                         int32_t dd = dr + 1 + t - I.depth[vt];
                         int32_t a_len = I.pos[vp] - I.pos[vt];
                         int32_t b_st = I.pos[vp] + I.size[vp];
@@ -351,18 +428,20 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
                     int32_t acc = 0;
                     for (int32_t t = k; t >= 1; t--) {
                         acc += seg_len[2 * t - 1] + seg_len[2 * t];
-                        I.tmp[t] = acc;  // stash; applied below after old sizes are no longer read
+                        I.tmp[t] = acc;
                     }
+                    s_L0 = I.pos[leave];
+                    s_pr = I.pos[r];
                     // parent / pred / direction / flow along the reversed path
                     int64_t prev_pred = e;
-                    uint8_t prev_up = (uint8_t)(i == q ? 1 : 0);  // e runs i -> j: up for q iff q == i
-                    int64_t prev_flow = delta;
+                    uint8_t prev_up = (uint8_t)(i == q ? 1 : 0);  // e runs i -> j
+                    int32_t prev_flow = (int32_t)delta;
                     int32_t prev_par = r;
                     for (int32_t t = 0; t <= k; t++) {
-                        int32_t vt = I.path[t];
+                        int32_t vt = PV(t);
                         int64_t op = I.pred[vt];
                         uint8_t ou = I.up[vt];
-                        int64_t of = I.flow[vt];
+                        int32_t of = I.flow[vt];
                         I.pred[vt] = prev_pred;
                         I.up[vt] = prev_up;
                         I.flow[vt] = prev_flow;
@@ -373,15 +452,16 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
                         prev_par = vt;
                     }
                     I.size[q] = S;
-                    for (int32_t t = 1; t <= k; t++) I.size[I.path[t]] = I.tmp[t];
+                    for (int32_t t = 1; t <= k; t++) I.size[PV(t)] = I.tmp[t];
+#undef PV
                     s_k = k;
                     s_nseg = ns;
-                    s_L0 = I.pos[leave];
                     s_S = S;
-                    s_pr = I.pos[r];
                     s_go = 1;
                 }
             }
+#undef PA
+#undef PB
         }
         __syncthreads();
         if (!s_go) break;
@@ -442,6 +522,8 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
             G.flow[v] = I.flow[v];
             G.parent[v] = I.parent[v];
             G.depth[v] = I.depth[v];
+            G.size[v] = I.size[v];
+            G.pos[v] = I.pos[v];
             G.up[v] = I.up[v];
         }
     }
@@ -489,6 +571,18 @@ __global__ void k_i64_to_i32_cost(const int64_t* __restrict__ c, int64_t m, int3
     o[a] = (int32_t)v;
 }
 
+__global__ void k_abs_sum(const int64_t* __restrict__ s, int64_t n, unsigned long long* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (i < n) {
+        int64_t x = s[i];
+        v = (unsigned long long)(x < 0 ? -x : x);
+        if (v >= (1ull << 40)) v = 1ull << 40;
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
+
 // Network simplex on an arc list (one CTA).  cmax = largest arc cost.
 pd_status ns_solve_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS, int64_t nT, const int32_t* cmat,
                         const int32_t* tail, const int32_t* head, const int32_t* cost, const int64_t* supply,
@@ -511,13 +605,13 @@ pd_status ns_solve_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS, i
     h.parent = bufT<int32_t>(c, B_NS_PARENT, N1);
     h.pred = bufT<int64_t>(c, B_NS_PRED, N1);
     h.depth = bufT<int32_t>(c, B_NS_DEPTH, N1);
-    h.flow = bufT<int64_t>(c, B_NS_FLOW, N1);
+    h.flow = bufT<int32_t>(c, B_NS_FLOW, N1);
     h.up = bufT<uint8_t>(c, B_NS_UP, N1);
     h.ord = bufT<int32_t>(c, B_NS_ORD, N1);
     h.pos = bufT<int32_t>(c, B_NS_POS, N1);
     h.size = bufT<int32_t>(c, B_NS_SIZE, N1);
     h.tmp = bufT<int32_t>(c, B_NS_TMP, N1);
-    h.path = bufT<int32_t>(c, B_NS_PATH, N1);
+    h.path = bufT<int32_t>(c, B_NS_PATH, 2 * N1);
     h.seg = bufT<int32_t>(c, B_NS_SEG, 4 * (2 * N1 + 3));
     NSInst* d = bufT<NSInst>(c, B_NS_INST, 1);
     if (!h.pi || !h.parent || !h.pred || !h.depth || !h.flow || !h.up || !h.ord || !h.pos || !h.size || !h.tmp ||
@@ -530,13 +624,24 @@ pd_status ns_solve_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS, i
     h.block = blk;
     h.max_pivots = o.max_rounds > 0 ? o.max_rounds : (int64_t(1) << 40);
     h.time_limit_ns = (o.time_limit_ms > 0 ? (uint64_t)o.time_limit_ms : 60000ull) * 1000000ull;
+    // flows are int32: the total supply must stay below 2^31
+    {
+        unsigned long long* sm = bufT<unsigned long long>(c, B_SMALL, 64);
+        if (!sm) return PD_ENOMEM;
+        PD_TRY_CUDA(c, cudaMemsetAsync(sm + 16, 0, sizeof(unsigned long long), st));
+        k_abs_sum<<<grid_for(n, 256), 256, 0, st>>>(supply, n, sm + 16); pd::count_launch();
+        PD_TRY_CUDA(c, cudaGetLastError());
+        PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small + 16, sm + 16, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+        if ((unsigned long long)c->h_small[16] >= (1ull << 31)) return fail(c, PD_ECAPACITY, "total supply >= 2^31");
+    }
     // big-M: more than any path cost; |potentials| stay below ~3 big
     if (cmax > (INT64_MAX / 8) / N1) return fail(c, PD_EOVERFLOW, "network simplex big-M would overflow");
     int64_t big = N1 * (cmax + 1) + 1;
     size_t smem = ns_smem_bytes(N1);
     int max_optin = 0;
     PD_TRY_CUDA(c, cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    h.smem_nodes = (o.ns_smem != 0 && smem + 4096 <= (size_t)max_optin) ? 1 : 0;
+    h.smem_nodes = (o.ns_smem != 0 && smem + 6144 <= (size_t)max_optin) ? 1 : 0;
     if (!h.smem_nodes) smem = 0;
     PD_TRY_CUDA(c, cudaFuncSetAttribute(k_netsimplex, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     PD_TRY_CUDA(c, cudaMemcpyAsync(d, &h, sizeof(NSInst), cudaMemcpyHostToDevice, st));
