@@ -206,6 +206,35 @@ pd_status pd_mcf_solve(pd_ctx* ctx, const pd_network* net, const pd_opts* opts, 
 pd_status pd_w1_approx(pd_ctx* ctx, pd_diagram A, pd_diagram B, double eps, const pd_opts* opts,
                        pd_result* out, void* stream);
 
+/*
+ * Allocation-free min-cost flow (no counterpart in the paper).
+ *
+ * Some callers cannot allocate device memory when they solve: code running
+ * under an allocator that forbids growth after start-up (a serving process
+ * with a fixed memory budget, a framework that owns every device byte through
+ * its own pool), or code that must not trigger the implicit synchronisation
+ * and latency of cudaMalloc / cudaFree in the middle of its work.  For them
+ * this entry point solves the same problem as pd_mcf_solve, with the same
+ * network simplex kernel, but takes no context and allocates nothing: its
+ * scratch is one fixed array of 12 MiB in the library's device memory, which
+ * every GPU that loads the library holds until the process exits.
+ *
+ * `net`: device memory in pd_network layout, as for pd_mcf_solve, with at
+ * most PD_NOALLOC_MAX_NODES - 1 nodes and PD_NOALLOC_MAX_ARCS arcs; larger
+ * networks return PD_ECAPACITY (so do total supplies >= 2^31).  *opt_out
+ * (host) receives the optimum; the call synchronises `stream`.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and it keeps the last call's
+ * contents: calls whose GPU work overlaps (other streams, other host threads
+ * on the same device) race with each other and must be serialised by the
+ * caller.  Errors are reported by the return code only.
+ */
+#define PD_NOALLOC_MAX_NODES 32768
+#define PD_NOALLOC_MAX_ARCS (1 << 20)
+pd_status pd_mcf_solve_noalloc(const pd_network* net, int64_t* opt_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

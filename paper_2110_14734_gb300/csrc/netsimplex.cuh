@@ -1,0 +1,57 @@
+// Instance record of the single-CTA network simplex kernel (netsimplex.cu).
+#pragma once
+#include <stddef.h>
+#include <stdint.h>
+
+namespace pd {
+
+constexpr int NS_THREADS = 1024;
+
+struct NSInst {
+    int32_t n;         // real nodes (root = n)
+    int64_t m;         // real arcs
+    // arcs a < mst are implicit: tail a / nT, head nS + a % nT, cost cmat[a];
+    // arcs mst <= a < m are explicit: tail/head/cost[a - mst]
+    int64_t mst;
+    int64_t nT;
+    int64_t nS;
+    const int32_t* cmat;
+    const int32_t* tail;
+    const int32_t* head;
+    const int32_t* cost;
+    const int64_t* supply;
+    int64_t* pi;       // n + 1
+    int32_t* parent;   // n + 1
+    int64_t* pred;     // n + 1 (arc id; artificial arc of node i is m + i)
+    int32_t* depth;    // n + 1
+    int32_t* flow;     // n + 1: flow on the pred arc (total supply < 2^31)
+    uint8_t* up;       // n + 1: pred arc points from the node to its parent
+    int32_t* ord;      // n + 1 preorder
+    int32_t* pos;      // n + 1
+    int32_t* size;     // n + 1
+    int32_t* tmp;      // n + 1 scratch
+    int32_t* path;     // 2 (n + 1) scratch: the two half-cycles past the shared-memory part
+    int32_t* seg;      // 4 * (2n + 3) scratch: segment start, length, output offset, depth shift
+    int64_t block;     // pricing block (arcs)
+    int32_t smem_nodes; // 1: hot node arrays live in shared memory
+    int32_t pad0;
+    int64_t scanned;   // result: arcs priced
+    int64_t max_pivots;
+    uint64_t time_limit_ns;
+    // results
+    int64_t opt;
+    int64_t pivots;
+    int64_t degenerate;
+    int32_t status;    // 0 ok, 1 infeasible, 2 pivot cap / time, 3 unbounded, 4 path too long
+    int32_t pad;
+};
+
+__global__ void k_netsimplex(NSInst* insts, int64_t big);
+size_t ns_smem_bytes(int64_t N1);
+__global__ void k_i64_to_i32_cost(const int64_t* __restrict__ c, int64_t m, int32_t* __restrict__ o,
+                                  unsigned long long* __restrict__ bad);
+__global__ void k_abs_sum(const int64_t* __restrict__ s, int64_t n, unsigned long long* __restrict__ out);
+__global__ void k_check_network(const int64_t* __restrict__ rp, const int32_t* __restrict__ hd, int64_t n, int64_t m,
+                                unsigned long long* __restrict__ bad);
+
+}  // namespace pd

@@ -90,6 +90,9 @@ _lib.pd_w1_approx.restype = C.c_int
 _lib.pd_w1_approx.argtypes = [C.c_void_p, pd_diagram, pd_diagram, C.c_double, C.POINTER(pd_opts),
                               C.POINTER(pd_result), C.c_void_p]
 
+_lib.pd_mcf_solve_noalloc.restype = C.c_int
+_lib.pd_mcf_solve_noalloc.argtypes = [C.POINTER(pd_network), C.POINTER(C.c_int64), C.c_void_p]
+
 _cudart = None
 
 
@@ -257,3 +260,18 @@ def pd_w1_approx(ctx: Context, A, B, eps: float, o: pd_opts | None = None, strea
 def pd_w1_approx_raw(ctx: Context, da: pd_diagram, db: pd_diagram, eps: float, o, res: pd_result, stream: int):
     """Allocation-free call for timing loops: prebuilt structs, result in res."""
     return _lib.pd_w1_approx(ctx.ptr, da, db, eps, C.byref(o) if o else None, C.byref(res), C.c_void_p(stream))
+
+
+def pd_mcf_solve_noalloc(net: dict, stream=None) -> int:
+    """The allocation-free solve (no context, fixed scratch in the library).
+    net: dict of cuda tensors row_ptr, head, cost, supply.  Returns OPT."""
+    keep = [net["row_ptr"].contiguous(), net["head"].contiguous(), net["cost"].contiguous(),
+            net["supply"].contiguous()]
+    n = int(keep[0].numel()) - 1
+    m = int(keep[1].numel())
+    nw = pd_network(n, m, *[C.c_void_p(t.data_ptr()) for t in keep])
+    opt = C.c_int64()
+    st = _lib.pd_mcf_solve_noalloc(C.byref(nw), C.byref(opt), C.c_void_p(_stream(stream)))
+    if st != PD_OK:
+        raise PDError(st, "pd_mcf_solve_noalloc failed")
+    return int(opt.value)
