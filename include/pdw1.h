@@ -81,7 +81,7 @@ typedef struct {
     int64_t update_every;   /* relabels between global price updates (0 = number of nodes, -1 = never) */
     int32_t seq_threshold;  /* cost scaling: at most this many active nodes, one block finishes them (-1 = 64) */
     int32_t solver;         /* 0 = network simplex (default), 1 = cost scaling with push/relabel */
-    int64_t ns_block;       /* network simplex pricing block in arcs (0 = max(2048, sqrt(arcs))) */
+    int64_t ns_block;       /* network simplex pricing block in arcs (0 = max(8192, sqrt(arcs))) */
     int32_t ns_transport;   /* W1 only: 1 = try the transportation form with its certificate first (default) */
     int32_t ns_smem;        /* network simplex: 1 = hot node arrays in shared memory when they fit (default) */
 } pd_opts;

@@ -4,16 +4,22 @@
 //
 // GPU layout.  Pricing is the parallel part: the whole CTA evaluates a block
 // of arcs (reduced cost c - pi(tail) + pi(head)) and reduces to the most
-// negative one.  The pivot walk (apex, leaving arc, flow change) is sequential
-// on one thread.  The spanning tree is kept as an explicit preorder array
-// (ord, pos, size), so that re-hanging the cut subtree is a handful of
-// contiguous segment moves done by all threads, with per-segment depth shifts
-// and one potential shift -- no pointer chasing over the subtree.
+// negative one.  The pivot is done by one warp: lanes 0 and 1 walk the two
+// half-cycles up to the apex (found with the preorder ancestor test
+// pos(a) <= pos(b) < pos(a) + size(a), so no depths are kept), then the warp
+// finds the leaving arc, changes the flow and re-roots the cut path.  The
+// spanning tree is kept as an explicit preorder array (ord, pos, size), so
+// re-hanging the cut subtree is a handful of contiguous segment moves done by
+// all threads plus one potential shift -- no pointer chasing over the subtree.
+// Up to 9216 nodes the node arrays live in shared memory with 16-bit indices
+// (24 bytes per node); larger trees keep 32-bit arrays in global memory.
 //
 // Big-M start: node i has an artificial arc to (supply >= 0) or from (< 0) an
 // extra root; zero-flow tree arcs point to the root (strongly feasible tree),
 // and the leaving arc is the last blocking arc met when the cycle is walked
 // from the apex in the direction of the entering arc, which rules out cycling.
+#include <algorithm>
+
 #include "internal.h"
 #include "netsimplex.cuh"
 #include "prims.cuh"
@@ -27,10 +33,10 @@ PD_D uint64_t ns_now() {
 }
 
 PD_D void arc_ends(const NSInst& I, int64_t a, int32_t* t, int32_t* h) {
-    if (a < I.mst) {
-        int64_t i = a / I.nT;
-        *t = (int32_t)i;
-        *h = (int32_t)(I.nS + (a - i * I.nT));
+    if (a < I.mst) {  // m + n < 2^31, so 32-bit division is exact
+        int32_t i = (int32_t)a / (int32_t)I.nT;
+        *t = i;
+        *h = (int32_t)I.nS + ((int32_t)a - i * (int32_t)I.nT);
     } else if (a < I.m) {
         *t = I.tail[a - I.mst];
         *h = I.head[a - I.mst];
@@ -59,75 +65,71 @@ PD_D void take_min(int64_t rc, int64_t a, int64_t& lb, int64_t& li) {
     }
 }
 
-// Bytes of dynamic shared memory for the hot node arrays of n + 1 nodes.
-size_t ns_smem_bytes(int64_t N1) { return (size_t)N1 * (8 + 4 + 4 + 4 + 4 + 4 + 1) + 64; }
+// Node arrays of the spanning tree.  IX = uint16_t: compact layout in shared
+// memory (parent, subtree size, preorder position and the preorder itself as
+// 16-bit indices); IX = int32_t: global memory.  Flow and direction of the
+// pred arc share one word: bit 31 = the arc points from the node to its parent.
+template <typename IX>
+struct Tree {
+    int64_t* pi;
+    int32_t* pred;
+    uint32_t* fu;
+    IX* par;
+    IX* sz;
+    IX* ps;
+    IX* od;
+    PD_D int32_t parent(int32_t v) const {
+        IX p = par[v];
+        return p == (IX)~(IX)0 ? -1 : (int32_t)p;
+    }
+    PD_D void set_parent(int32_t v, int32_t p) { par[v] = p < 0 ? (IX)~(IX)0 : (IX)p; }
+    PD_D int32_t flow(int32_t v) const { return (int32_t)(fu[v] & 0x7fffffffu); }
+    PD_D bool up(int32_t v) const { return (fu[v] >> 31) != 0; }
+    PD_D void set_fu(int32_t v, int32_t f, bool u) { fu[v] = (uint32_t)f | (u ? 0x80000000u : 0u); }
+    PD_D void add_flow(int32_t v, int32_t d) { fu[v] = (uint32_t)((int32_t)fu[v] + d); }  // flow stays in [0, 2^31)
+};
 
-constexpr int NS_LMAX = 512;  // half-cycle entries kept in shared memory
+constexpr int NS_LMAX = 512;     // half-cycle entries kept in shared memory
+constexpr int NS_SEGSM = 65;     // re-hang segments kept in shared memory (paths shorter than 32)
+constexpr int NS_REGS = 9;       // shared-memory layout: at most 9 * 1024 nodes (re-hang buffered in registers)
 
-__global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_t big) {
-    NSInst& G = insts[blockIdx.x];
-    NSInst I = G;  // local copy: the hot arrays may be redirected to shared memory
+template <typename IX>
+__device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T, int64_t big) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int32_t n = I.n, root = n, N1 = n + 1;
     const int64_t M = I.m + n;  // arcs including the artificial ones
-    extern __shared__ __align__(16) unsigned char dyn[];
-    if (I.smem_nodes) {
-        unsigned char* p = dyn;
-        I.pi = (int64_t*)p;
-        p += sizeof(int64_t) * N1;
-        I.flow = (int32_t*)p;
-        p += sizeof(int32_t) * N1;
-        I.parent = (int32_t*)p;
-        p += sizeof(int32_t) * N1;
-        I.depth = (int32_t*)p;
-        p += sizeof(int32_t) * N1;
-        I.size = (int32_t*)p;
-        p += sizeof(int32_t) * N1;
-        I.pos = (int32_t*)p;
-        p += sizeof(int32_t) * N1;
-        I.up = (uint8_t*)p;
-    }
     __shared__ int32_t pa[NS_LMAX], pb[NS_LMAX];
     int32_t* gpa = I.path;
     int32_t* gpb = I.path + N1;
-    __shared__ int32_t s_la, s_lb, s_join, s_i, s_j;
+    __shared__ int32_t s_la, s_lb;
     __shared__ int64_t s_ce;
-
     __shared__ int64_t s_val[32];
     __shared__ int64_t s_idx[32];
-    __shared__ int64_t s_best, s_bidx, s_next, s_dpi;
+    __shared__ int64_t s_next, s_dpi, s_e;
     __shared__ int32_t s_go, s_status;
-    // re-hang plan
-    __shared__ int32_t s_k, s_L0, s_S, s_pr, s_nseg;
+    __shared__ int32_t s_L0, s_S, s_pr, s_nseg, s_segsm;
+    __shared__ int32_t sseg[3][NS_SEGSM];
     const int32_t SEGN = 2 * n + 3;
-    int32_t* seg_start = I.seg;
-    int32_t* seg_len = I.seg + SEGN;
-    int32_t* seg_out = I.seg + 2 * SEGN;
-    int32_t* seg_dd = I.seg + 3 * SEGN;
 
     // ---- initial tree: the root star --------------------------------------
     for (int32_t i = tid; i < n; i += NS_THREADS) {
         int64_t s = I.supply[i];
-        I.parent[i] = root;
-        I.pred[i] = I.m + i;
-        I.up[i] = s >= 0;
-        I.flow[i] = (int32_t)(s >= 0 ? s : -s);
-        I.pi[i] = s >= 0 ? big : -big;  // reduced cost of the artificial arc is 0
-        I.depth[i] = 1;
-        I.ord[1 + i] = i;
-        I.pos[i] = 1 + i;
-        I.size[i] = 1;
+        T.set_parent(i, root);
+        T.pred[i] = (int32_t)(I.m + i);
+        T.set_fu(i, (int32_t)(s >= 0 ? s : -s), s >= 0);
+        T.pi[i] = s >= 0 ? big : -big;  // reduced cost of the artificial arc is 0
+        T.od[1 + i] = (IX)i;
+        T.ps[i] = (IX)(1 + i);
+        T.sz[i] = (IX)1;
     }
     if (tid == 0) {
-        I.parent[root] = -1;
-        I.pred[root] = -1;
-        I.up[root] = 0;
-        I.flow[root] = 0;
-        I.pi[root] = 0;
-        I.depth[root] = 0;
-        I.ord[0] = root;
-        I.pos[root] = 0;
-        I.size[root] = N1;
+        T.set_parent(root, -1);
+        T.pred[root] = -1;
+        T.set_fu(root, 0, false);
+        T.pi[root] = 0;
+        T.od[0] = (IX)root;
+        T.ps[root] = 0;
+        T.sz[root] = (IX)N1;
         s_next = 0;
         s_status = 0;
     }
@@ -137,52 +139,51 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
     const int64_t B = I.block < 1 ? 1 : I.block;
 
     for (;;) {
-        // ---- pricing: blocks of B arcs from s_next, first block holding a
-        // negative reduced cost wins (most negative in it, lowest index on ties)
+        // ---- pricing: blocks of B arcs from s_next; the most negative reduced
+        // cost of the first block that has one enters -------------------------
         int64_t scanned = 0, a0 = s_next;
-        int64_t best = 0, bidx = -1;
+        bool found = false;
         while (scanned < M) {
             const int64_t aend = a0 + B < M ? a0 + B : M;
             const int64_t len = aend - a0;
             int64_t lb = 0, li = -1;
-            // chunks of 8 consecutive arcs per thread, 16-byte vector loads
             for (int64_t c0 = a0 + 8 * (int64_t)tid; c0 < aend; c0 += 8 * NS_THREADS) {
                 if (c0 + 8 <= aend && c0 + 8 <= I.mst) {
                     int4 w0 = __ldcs((const int4*)(I.cmat + c0));
                     int4 w1 = __ldcs((const int4*)(I.cmat + c0 + 4));
                     int32_t cv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-                    int64_t i = c0 / I.nT, j = c0 - i * I.nT;
-                    int64_t pt = I.pi[i];
+                    int32_t i = (int32_t)c0 / (int32_t)I.nT, j = (int32_t)c0 - i * (int32_t)I.nT;
+                    int64_t pt = T.pi[i];
 #pragma unroll
                     for (int q = 0; q < 8; q++) {
-                        int64_t rc = (int64_t)cv[q] - pt + I.pi[I.nS + j];
+                        int64_t rc = (int64_t)cv[q] - pt + T.pi[I.nS + j];
                         take_min(rc, c0 + q, lb, li);
-                        if (++j == I.nT) {
+                        if (++j == (int32_t)I.nT) {
                             j = 0;
                             ++i;
-                            if (q < 7) pt = I.pi[i];
+                            if (q < 7) pt = T.pi[i];
                         }
                     }
-                } else if (c0 >= I.mst && c0 + 8 <= aend && c0 + 8 <= I.m && ((c0 - I.mst) & 7) == 0) {
+                } else if (I.vec_explicit && c0 >= I.mst && c0 + 8 <= aend && c0 + 8 <= I.m &&
+                           ((c0 - I.mst) & 7) == 0) {
                     const int64_t x = c0 - I.mst;
-                    int4 t0 = __ldcs((const int4*)(I.tail + x)), t1 = __ldcs((const int4*)(I.tail + x + 4));
+                    int4 t0v = __ldcs((const int4*)(I.tail + x)), t1v = __ldcs((const int4*)(I.tail + x + 4));
                     int4 h0 = __ldcs((const int4*)(I.head + x)), h1 = __ldcs((const int4*)(I.head + x + 4));
                     int4 k0 = __ldcs((const int4*)(I.cost + x)), k1 = __ldcs((const int4*)(I.cost + x + 4));
-                    int32_t tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+                    int32_t tv[8] = {t0v.x, t0v.y, t0v.z, t0v.w, t1v.x, t1v.y, t1v.z, t1v.w};
                     int32_t hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
                     int32_t cv[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
 #pragma unroll
-                    for (int q = 0; q < 8; q++) take_min((int64_t)cv[q] - I.pi[tv[q]] + I.pi[hv[q]], c0 + q, lb, li);
+                    for (int q = 0; q < 8; q++) take_min((int64_t)cv[q] - T.pi[tv[q]] + T.pi[hv[q]], c0 + q, lb, li);
                 } else {
                     int64_t ce = c0 + 8 < aend ? c0 + 8 : aend;
                     for (int64_t a = c0; a < ce; a++) {
                         int32_t t, h;
                         arc_ends(I, a, &t, &h);
-                        take_min(arc_cost(I, a, big) - I.pi[t] + I.pi[h], a, lb, li);
+                        take_min(arc_cost(I, a, big) - T.pi[t] + T.pi[h], a, lb, li);
                     }
                 }
             }
-            // CTA argmin (value, then index)
             for (int off = 16; off > 0; off >>= 1) {
                 int64_t ov = __shfl_xor_sync(0xffffffffu, lb, off);
                 int64_t oi = __shfl_xor_sync(0xffffffffu, li, off);
@@ -196,32 +197,32 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
                 s_idx[wid] = li;
             }
             __syncthreads();
-            if (wid == 0) {
-                lb = s_val[lane];
-                li = s_idx[lane];
-                for (int off = 16; off > 0; off >>= 1) {
-                    int64_t ov = __shfl_xor_sync(0xffffffffu, lb, off);
-                    int64_t oi = __shfl_xor_sync(0xffffffffu, li, off);
-                    if (ov < lb || (ov == lb && oi >= 0 && (li < 0 || oi < li))) {
-                        lb = ov;
-                        li = oi;
-                    }
-                }
-                if (lane == 0) {
-                    s_best = lb;
-                    s_bidx = li;
-                }
-            }
-            __syncthreads();
-            best = s_best;
-            bidx = s_bidx;
             scanned += len;
             nscan += len;
             a0 = aend >= M ? 0 : aend;
+            if (wid == 0) {
+                int64_t bv = s_val[lane], bi = s_idx[lane];
+                for (int off = 16; off > 0; off >>= 1) {
+                    int64_t ov = __shfl_xor_sync(0xffffffffu, bv, off);
+                    int64_t oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                    if (ov < bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) {
+                        bv = ov;
+                        bi = oi;
+                    }
+                }
+                if (lane == 0) {
+                    s_e = bv < 0 ? bi : -1;
+                    if (bv < 0) s_next = a0;
+                }
+            }
             __syncthreads();
-            if (best < 0) break;
+            if (s_e >= 0) {
+                found = true;
+                break;
+            }
         }
-        if (best >= 0 || bidx < 0) break;  // optimal
+        if (!found) break;  // no arc with a negative reduced cost: optimal
+        const int64_t ent = s_e;
         if (tid == 0) s_go = (pivots < I.max_pivots && ns_now() - t0 <= I.time_limit_ns) ? 1 : 0;
         __syncthreads();
         if (!s_go) {
@@ -231,48 +232,58 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
         }
         pivots++;
 
-        // ---- pivot: apex walk (one thread), then the two recorded half-cycles
-        // are processed by warp 0 (leaving arc, flows, ancestor sizes) ---------
+        // ---- pivot ----------------------------------------------------------
         if (wid == 0) {
+            // the two half-cycles, walked concurrently by lanes 0 and 1: from i
+            // up to the first ancestor of j, and from j up to the first ancestor
+            // of i -- both stop at the apex
+            int32_t i, j;
+            arc_ends(I, ent, &i, &j);
             if (lane == 0) {
-                s_next = a0;
-                int64_t e = bidx;
-                int32_t i, j;
-                arc_ends(I, e, &i, &j);
-                s_ce = arc_cost(I, e, big);
-                int32_t u = i, v = j, la = 0, lb = 0;
-                while (u != v) {
-                    int32_t du = I.depth[u], dv = I.depth[v];
-                    if (du >= dv) {
-                        if (la < NS_LMAX) pa[la] = u; else gpa[la] = u;
-                        la++;
-                        u = I.parent[u];
+                s_ce = arc_cost(I, ent, big);
+                const int32_t pj = T.ps[j];
+                int32_t u = i, la = 0;
+                for (;;) {
+                    if (u < 0 || la >= n) {  // no ancestor found within n steps: corrupt tree
+                        la = -1;
+                        break;
                     }
-                    if (dv >= du) {
-                        if (lb < NS_LMAX) pb[lb] = v; else gpb[lb] = v;
-                        lb++;
-                        v = I.parent[v];
-                    }
+                    int32_t pu = T.ps[u];
+                    if (pu <= pj && pj < pu + (int32_t)T.sz[u]) break;
+                    if (la < NS_LMAX) pa[la] = u; else gpa[la] = u;
+                    la++;
+                    u = T.parent(u);
                 }
                 s_la = la;
+            } else if (lane == 1) {
+                const int32_t pi_ = T.ps[i];
+                int32_t v = j, lb = 0;
+                for (;;) {
+                    if (v < 0 || lb >= n) {  // no ancestor found within n steps: corrupt tree
+                        lb = -1;
+                        break;
+                    }
+                    int32_t pv = T.ps[v];
+                    if (pv <= pi_ && pi_ < pv + (int32_t)T.sz[v]) break;
+                    if (lb < NS_LMAX) pb[lb] = v; else gpb[lb] = v;
+                    lb++;
+                    v = T.parent(v);
+                }
                 s_lb = lb;
-                s_join = u;
-                s_i = i;
-                s_j = j;
             }
             __syncwarp();
-            const int32_t la = s_la, lb = s_lb, i = s_i, j = s_j;
+            const int32_t la = s_la, lb = s_lb;
 #define PA(t) ((t) < NS_LMAX ? pa[t] : gpa[t])
 #define PB(t) ((t) < NS_LMAX ? pb[t] : gpb[t])
             // leaving arc: last blocking arc walking from the apex along the
             // cycle -- on the i-side the one closest to i (smallest index), on
             // the j-side the one closest to the apex (largest index), j-side
             // preferred on ties.
-            int64_t fi = INT64_MAX, ti = INT32_MAX, fj = INT64_MAX, tj = -1;
+            int32_t fi = INT32_MAX, ti = INT32_MAX, fj = INT32_MAX, tj = -1;
             for (int32_t t = lane; t < la; t += 32) {
                 int32_t x = PA(t);
-                if (I.up[x]) {
-                    int64_t f = I.flow[x];
+                if (T.up(x)) {
+                    int32_t f = T.flow(x);
                     if (f < fi || (f == fi && t < ti)) {
                         fi = f;
                         ti = t;
@@ -281,8 +292,8 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
             }
             for (int32_t t = lane; t < lb; t += 32) {
                 int32_t x = PB(t);
-                if (!I.up[x]) {
-                    int64_t f = I.flow[x];
+                if (!T.up(x)) {
+                    int32_t f = T.flow(x);
                     if (f < fj || (f == fj && t > tj)) {
                         fj = f;
                         tj = t;
@@ -290,8 +301,8 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
                 }
             }
             for (int off = 16; off > 0; off >>= 1) {
-                int64_t of = __shfl_xor_sync(0xffffffffu, fi, off);
-                int64_t ot = __shfl_xor_sync(0xffffffffu, ti, off);
+                int32_t of = __shfl_xor_sync(0xffffffffu, fi, off);
+                int32_t ot = __shfl_xor_sync(0xffffffffu, ti, off);
                 if (of < fi || (of == fi && ot < ti)) {
                     fi = of;
                     ti = ot;
@@ -304,121 +315,171 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
                 }
             }
             int side;
-            int64_t delta;
-            int32_t tl;
-            if (tj >= 0 && fj <= fi) {
+            int32_t delta, tl;
+            if (la < 0 || lb < 0) {
+                side = -1;
+                delta = 0;
+                tl = 0;
+            } else if (tj >= 0 && fj <= fi) {
                 side = 2;
                 delta = fj;
-                tl = (int32_t)tj;
+                tl = tj;
             } else if (ti != INT32_MAX) {
                 side = 1;
                 delta = fi;
-                tl = (int32_t)ti;
+                tl = ti;
             } else {
                 side = 0;
                 delta = 0;
                 tl = 0;
             }
-            if (side == 0) {
+            if (side <= 0) {
                 if (lane == 0) {
-                    s_status = 3;
+                    s_status = side == 0 ? 3 : 4;
                     s_go = 0;
                 }
             } else {
                 if (delta > 0) {
-                    const int32_t d32 = (int32_t)delta;
                     for (int32_t t = lane; t < la; t += 32) {
                         int32_t x = PA(t);
-                        I.flow[x] += I.up[x] ? -d32 : d32;
+                        T.add_flow(x, T.up(x) ? -delta : delta);
                     }
                     for (int32_t t = lane; t < lb; t += 32) {
                         int32_t x = PB(t);
-                        I.flow[x] += I.up[x] ? d32 : -d32;
+                        T.add_flow(x, T.up(x) ? delta : -delta);
                     }
+                } else if (lane == 0) {
+                    degen++;
                 }
                 const int32_t leave = side == 1 ? PA(tl) : PB(tl);
-                const int32_t S = I.size[leave];
+                const int32_t S = T.sz[leave];
+                const int32_t q = side == 1 ? i : j, r = side == 1 ? j : i;
                 __syncwarp();
                 // the cut subtree leaves the chain above `leave` and joins r's chain
                 if (side == 1) {
-                    for (int32_t t = tl + 1 + lane; t < la; t += 32) I.size[PA(t)] -= S;
-                    for (int32_t t = lane; t < lb; t += 32) I.size[PB(t)] += S;
+                    for (int32_t t = tl + 1 + lane; t < la; t += 32) T.sz[PA(t)] = (IX)((int32_t)T.sz[PA(t)] - S);
+                    for (int32_t t = lane; t < lb; t += 32) T.sz[PB(t)] = (IX)((int32_t)T.sz[PB(t)] + S);
                 } else {
-                    for (int32_t t = tl + 1 + lane; t < lb; t += 32) I.size[PB(t)] -= S;
-                    for (int32_t t = lane; t < la; t += 32) I.size[PA(t)] += S;
+                    for (int32_t t = tl + 1 + lane; t < lb; t += 32) T.sz[PB(t)] = (IX)((int32_t)T.sz[PB(t)] - S);
+                    for (int32_t t = lane; t < la; t += 32) T.sz[PA(t)] = (IX)((int32_t)T.sz[PA(t)] + S);
                 }
                 __syncwarp();
-                if (lane == 0) {
-                    if (delta == 0) degen++;
-                    const int64_t e = bidx;
-                    const int32_t q = side == 1 ? i : j, r = side == 1 ? j : i;
-                    int64_t rc = s_ce - I.pi[i] + I.pi[j];
-                    s_dpi = side == 1 ? rc : -rc;
-                    const int32_t k = tl;  // path q = v0 .. vk = leave
+                const int32_t k = tl;  // path q = v0 .. vk = leave
 #define PV(t) (side == 1 ? PA(t) : PB(t))
-                    // new preorder of the cut subtree, re-rooted at q, as segments of the old order
-                    const int32_t dr = I.depth[r];
+                if (lane == 0) {
+                    int64_t rc = s_ce - T.pi[i] + T.pi[j];
+                    s_dpi = side == 1 ? rc : -rc;
+                    s_L0 = T.ps[leave];
+                    s_pr = T.ps[r];
+                    s_S = S;
+                    s_nseg = 2 * k + 1;
+                    s_segsm = k < 32 ? 1 : 0;
+                }
+                if (k < 32) {
+                    // one lane per path node: segments of the re-rooted order,
+                    // new subtree sizes, and the reversed parent/pred/flow chain
+                    const bool on = lane <= k;
+                    int32_t vt = on ? PV(lane) : 0;
+                    int32_t vp = (on && lane > 0) ? PV(lane - 1) : 0;
+                    int32_t a_st = 0, a_len = 0, b_st = 0, b_len = 0, L = 0;
+                    int32_t opred = 0, oflow = 0, oup = 0;
+                    if (on) {
+                        if (lane == 0) {
+                            a_st = T.ps[q];
+                            a_len = T.sz[q];
+                            L = a_len;
+                        } else {
+                            int32_t pvt = T.ps[vt], pvp = T.ps[vp];
+                            a_st = pvt;
+                            a_len = pvp - pvt;
+                            b_st = pvp + (int32_t)T.sz[vp];
+                            b_len = pvt + (int32_t)T.sz[vt] - b_st;
+                            L = a_len + b_len;
+                        }
+                        opred = T.pred[vt];
+                        oflow = T.flow(vt);
+                        oup = T.up(vt) ? 1 : 0;
+                    }
+                    int32_t incl = L;
+                    for (int off = 1; off < 32; off <<= 1) {
+                        int32_t o = __shfl_up_sync(0xffffffffu, incl, off);
+                        if (lane >= off) incl += o;
+                    }
+                    const int32_t excl = incl - L;  // output offset of A_t
+                    const int32_t ppred = __shfl_up_sync(0xffffffffu, opred, 1);
+                    const int32_t pflow = __shfl_up_sync(0xffffffffu, oflow, 1);
+                    const int32_t pup = __shfl_up_sync(0xffffffffu, oup, 1);
+                    __syncwarp();
+                    if (on) {
+                        if (lane == 0) {
+                            sseg[0][0] = a_st;
+                            sseg[1][0] = a_len;
+                            sseg[2][0] = 0;
+                            T.pred[vt] = (int32_t)ent;
+                            T.set_fu(vt, delta, i == q);  // the entering arc runs i -> j
+                            T.set_parent(vt, r);
+                            T.sz[vt] = (IX)S;
+                        } else {
+                            sseg[0][2 * lane - 1] = a_st;
+                            sseg[1][2 * lane - 1] = a_len;
+                            sseg[2][2 * lane - 1] = excl;
+                            sseg[0][2 * lane] = b_st;
+                            sseg[1][2 * lane] = b_len;
+                            sseg[2][2 * lane] = excl + a_len;
+                            T.pred[vt] = ppred;
+                            T.set_fu(vt, pflow, !pup);
+                            T.set_parent(vt, vp);
+                            T.sz[vt] = (IX)(S - excl);
+                        }
+                    }
+                } else if (lane == 0) {
+                    // long path: the same steps on one lane, segments in global memory
+                    int32_t* gs = I.seg;
                     int32_t ns = 0, out = 0;
-                    seg_start[ns] = I.pos[q];
-                    seg_len[ns] = I.size[q];
-                    seg_out[ns] = out;
-                    seg_dd[ns] = dr + 1 - I.depth[q];
-                    out += seg_len[ns];
+                    gs[ns] = T.ps[q];
+                    gs[SEGN + ns] = T.sz[q];
+                    gs[2 * SEGN + ns] = out;
+                    out += T.sz[q];
                     ns++;
                     for (int32_t t = 1; t <= k; t++) {
                         int32_t vt = PV(t), vp = PV(t - 1);
-                        int32_t dd = dr + 1 + t - I.depth[vt];
-                        int32_t a_len = I.pos[vp] - I.pos[vt];
-                        int32_t b_st = I.pos[vp] + I.size[vp];
-                        int32_t b_len = I.pos[vt] + I.size[vt] - b_st;
-                        seg_start[ns] = I.pos[vt];
-                        seg_len[ns] = a_len;
-                        seg_out[ns] = out;
-                        seg_dd[ns] = dd;
+                        int32_t a_len = (int32_t)T.ps[vp] - (int32_t)T.ps[vt];
+                        int32_t b_st = (int32_t)T.ps[vp] + (int32_t)T.sz[vp];
+                        int32_t b_len = (int32_t)T.ps[vt] + (int32_t)T.sz[vt] - b_st;
+                        gs[ns] = T.ps[vt];
+                        gs[SEGN + ns] = a_len;
+                        gs[2 * SEGN + ns] = out;
+                        I.tmp[t] = out;  // offset of A_t; new size of v_t is S minus it
                         out += a_len;
                         ns++;
-                        seg_start[ns] = b_st;
-                        seg_len[ns] = b_len;
-                        seg_out[ns] = out;
-                        seg_dd[ns] = dd;
+                        gs[ns] = b_st;
+                        gs[SEGN + ns] = b_len;
+                        gs[2 * SEGN + ns] = out;
                         out += b_len;
                         ns++;
                     }
-                    // new subtree sizes along the path (suffix sums of A_t + B_t)
-                    int32_t acc = 0;
-                    for (int32_t t = k; t >= 1; t--) {
-                        acc += seg_len[2 * t - 1] + seg_len[2 * t];
-                        I.tmp[t] = acc;
-                    }
-                    s_L0 = I.pos[leave];
-                    s_pr = I.pos[r];
-                    // parent / pred / direction / flow along the reversed path
-                    int64_t prev_pred = e;
-                    uint8_t prev_up = (uint8_t)(i == q ? 1 : 0);  // e runs i -> j
-                    int32_t prev_flow = (int32_t)delta;
+                    int32_t prev_pred = (int32_t)ent;
+                    bool prev_up = (i == q);
+                    int32_t prev_flow = delta;
                     int32_t prev_par = r;
                     for (int32_t t = 0; t <= k; t++) {
                         int32_t vt = PV(t);
-                        int64_t op = I.pred[vt];
-                        uint8_t ou = I.up[vt];
-                        int32_t of = I.flow[vt];
-                        I.pred[vt] = prev_pred;
-                        I.up[vt] = prev_up;
-                        I.flow[vt] = prev_flow;
-                        I.parent[vt] = prev_par;
+                        int32_t op = T.pred[vt];
+                        bool ou = T.up(vt);
+                        int32_t of = T.flow(vt);
+                        T.pred[vt] = prev_pred;
+                        T.set_fu(vt, prev_flow, prev_up);
+                        T.set_parent(vt, prev_par);
                         prev_pred = op;
-                        prev_up = (uint8_t)!ou;
+                        prev_up = !ou;
                         prev_flow = of;
                         prev_par = vt;
                     }
-                    I.size[q] = S;
-                    for (int32_t t = 1; t <= k; t++) I.size[PV(t)] = I.tmp[t];
-#undef PV
-                    s_k = k;
-                    s_nseg = ns;
-                    s_S = S;
-                    s_go = 1;
+                    T.sz[q] = (IX)S;
+                    for (int32_t t = 1; t <= k; t++) T.sz[PV(t)] = (IX)(S - I.tmp[t]);
                 }
+#undef PV
+                if (lane == 0) s_go = 1;
             }
 #undef PA
 #undef PB
@@ -429,7 +490,10 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
         {
             const int32_t L0 = s_L0, S = s_S, pr = s_pr, nseg = s_nseg;
             const int64_t dpi = s_dpi;
-            // new order over the affected index range [lo, hi)
+            const int32_t* sst = s_segsm ? sseg[0] : I.seg;
+            const int32_t* sln = s_segsm ? sseg[1] : I.seg + SEGN;
+            const int32_t* sot = s_segsm ? sseg[2] : I.seg + 2 * SEGN;
+            (void)sln;
             int32_t lo, hi, ins;  // ins: first index of the new segment in the new order
             if (pr < L0) {
                 lo = pr + 1;
@@ -440,60 +504,62 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
                 hi = pr + 1;
                 ins = pr + 1 - S;
             }
-            for (int32_t x = lo + tid; x < hi; x += NS_THREADS) {
-                int32_t node;
+            auto new_node = [&](int32_t x) -> int32_t {
                 if (x >= ins && x < ins + S) {
                     int32_t o = x - ins;
-                    int32_t sl = 0, sh = nseg - 1;  // last segment with seg_out <= o
+                    int32_t sl = 0, sh = nseg - 1;  // last segment with output offset <= o
                     while (sl < sh) {
                         int32_t mid = (sl + sh + 1) >> 1;
-                        if (seg_out[mid] <= o)
+                        if (sot[mid] <= o)
                             sl = mid;
                         else
                             sh = mid - 1;
                     }
-                    int32_t sidx = sl;
-                    node = I.ord[seg_start[sidx] + (o - seg_out[sidx])];
-                    I.depth[node] += seg_dd[sidx];
-                    I.pi[node] += dpi;
-                } else if (pr < L0) {
-                    // [pr+1, L0) shifted right by S
-                    node = I.ord[x - S];
-                } else {
-                    // [L0+S, pr] shifted left by S
-                    node = I.ord[x + S];
+                    int32_t node = T.od[sst[sl] + (o - sot[sl])];
+                    T.pi[node] += dpi;
+                    return node;
                 }
-                I.tmp[x] = node;
-            }
-            __syncthreads();
-            for (int32_t x = lo + tid; x < hi; x += NS_THREADS) {
-                int32_t node = I.tmp[x];
-                I.ord[x] = node;
-                I.pos[node] = x;
+                return pr < L0 ? (int32_t)T.od[x - S] : (int32_t)T.od[x + S];
+            };
+            if constexpr (sizeof(IX) == 2) {
+                int32_t vals[NS_REGS];
+#pragma unroll
+                for (int r2 = 0; r2 < NS_REGS; r2++) {
+                    int32_t x = lo + tid + r2 * NS_THREADS;
+                    vals[r2] = x < hi ? new_node(x) : 0;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int r2 = 0; r2 < NS_REGS; r2++) {
+                    int32_t x = lo + tid + r2 * NS_THREADS;
+                    if (x < hi) {
+                        T.od[x] = (IX)vals[r2];
+                        T.ps[vals[r2]] = (IX)x;
+                    }
+                }
+            } else {
+                for (int32_t x = lo + tid; x < hi; x += NS_THREADS) I.tmp[x] = new_node(x);
+                __syncthreads();
+                for (int32_t x = lo + tid; x < hi; x += NS_THREADS) {
+                    int32_t node = I.tmp[x];
+                    T.od[x] = (IX)node;
+                    T.ps[node] = (IX)x;
+                }
             }
             __syncthreads();
         }
     }
-    // ---- result ------------------------------------------------------------
+    // ---- result: node arrays back to the global record ---------------------
     __syncthreads();
-    if (I.smem_nodes) {
-        for (int32_t v = tid; v < N1; v += NS_THREADS) {
-            G.pi[v] = I.pi[v];
-            G.flow[v] = I.flow[v];
-            G.parent[v] = I.parent[v];
-            G.depth[v] = I.depth[v];
-            G.size[v] = I.size[v];
-            G.pos[v] = I.pos[v];
-            G.up[v] = I.up[v];
-        }
+    for (int32_t v = tid; v < N1; v += NS_THREADS) {
+        G.pi[v] = T.pi[v];
+        G.pred[v] = T.pred[v];
+        G.flow[v] = T.flow(v);
+        G.up[v] = T.up(v) ? 1 : 0;
+        G.parent[v] = T.parent(v);
+        G.size[v] = (int32_t)T.sz[v];
+        G.pos[v] = (int32_t)T.ps[v];
     }
-    if (tid == 0) {
-        G.pivots = pivots;
-        G.degenerate = degen;
-        G.scanned = nscan;
-        G.status = s_status;
-    }
-    // objective over tree arcs, and feasibility (no flow left on artificial arcs)
     __shared__ unsigned long long s_obj, s_art;
     if (tid == 0) {
         s_obj = 0;
@@ -502,7 +568,7 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
     __syncthreads();
     unsigned long long obj = 0, art = 0;
     for (int32_t v = tid; v < n; v += NS_THREADS) {
-        int64_t a = I.pred[v], f = I.flow[v];
+        int64_t a = T.pred[v], f = T.flow(v);
         if (a >= I.m) {
             if (f != 0) art++;
         } else if (f > 0) {
@@ -513,14 +579,62 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
     atomicAdd(&s_art, art);
     __syncthreads();
     if (tid == 0) {
+        G.pivots = pivots;
+        G.degenerate = degen;
+        G.scanned = nscan;
+        G.status = s_status;
         G.opt = (int64_t)s_obj;
         if (s_status == 0 && s_art) G.status = 1;
     }
 }
 
-}  // namespace pd
+__global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_t big) {
+    NSInst& G = insts[blockIdx.x];
+    NSInst I = G;
+    const int32_t N1 = I.n + 1;
+    if (I.smem_nodes) {
+        extern __shared__ __align__(16) unsigned char dyn[];
+        unsigned char* p = dyn;
+        Tree<uint16_t> T;
+        T.pi = (int64_t*)p;
+        p += sizeof(int64_t) * N1;
+        T.pred = (int32_t*)p;
+        p += sizeof(int32_t) * N1;
+        T.fu = (uint32_t*)p;
+        p += sizeof(uint32_t) * N1;
+        T.par = (uint16_t*)p;
+        p += sizeof(uint16_t) * N1;
+        T.sz = (uint16_t*)p;
+        p += sizeof(uint16_t) * N1;
+        T.ps = (uint16_t*)p;
+        p += sizeof(uint16_t) * N1;
+        T.od = (uint16_t*)p;
+        ns_body<uint16_t>(G, I, T, big);
+    } else {
+        Tree<int32_t> T;
+        T.pi = I.pi;
+        T.pred = I.pred;
+        T.fu = (uint32_t*)I.flow;  // packed flow / direction while solving; unpacked on exit
+        T.par = I.parent;
+        T.sz = I.size;
+        T.ps = I.pos;
+        T.od = I.ord;
+        ns_body<int32_t>(G, I, T, big);
+    }
+}
 
-namespace pd {
+// Bytes of dynamic shared memory for the compact node arrays of N1 nodes.
+size_t ns_smem_bytes(int64_t N1) { return (size_t)N1 * (8 + 4 + 4 + 2 + 2 + 2 + 2) + 64; }
+
+bool ns_smem_fits(int64_t N1, int max_optin) {
+    if (N1 > (int64_t)NS_REGS * NS_THREADS) return false;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_netsimplex) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return fa.sharedSizeBytes + ns_smem_bytes(N1) <= (size_t)max_optin;
+}
 
 __global__ void k_i64_to_i32_cost(const int64_t* __restrict__ c, int64_t m, int32_t* __restrict__ o,
                                   unsigned long long* __restrict__ bad) {
@@ -561,10 +675,10 @@ pd_status ns_solve_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS, i
     h.head = head;
     h.cost = cost;
     h.supply = supply;
+    h.vec_explicit = ((((uintptr_t)tail) | ((uintptr_t)head) | ((uintptr_t)cost)) & 15) == 0 ? 1 : 0;
     h.pi = bufT<int64_t>(c, B_NS_PI, N1);
     h.parent = bufT<int32_t>(c, B_NS_PARENT, N1);
-    h.pred = bufT<int64_t>(c, B_NS_PRED, N1);
-    h.depth = bufT<int32_t>(c, B_NS_DEPTH, N1);
+    h.pred = bufT<int32_t>(c, B_NS_PRED, N1);
     h.flow = bufT<int32_t>(c, B_NS_FLOW, N1);
     h.up = bufT<uint8_t>(c, B_NS_UP, N1);
     h.ord = bufT<int32_t>(c, B_NS_ORD, N1);
@@ -572,15 +686,17 @@ pd_status ns_solve_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS, i
     h.size = bufT<int32_t>(c, B_NS_SIZE, N1);
     h.tmp = bufT<int32_t>(c, B_NS_TMP, N1);
     h.path = bufT<int32_t>(c, B_NS_PATH, 2 * N1);
-    h.seg = bufT<int32_t>(c, B_NS_SEG, 4 * (2 * N1 + 3));
+    h.seg = bufT<int32_t>(c, B_NS_SEG, 3 * (2 * N1 + 3));
     NSInst* d = bufT<NSInst>(c, B_NS_INST, 1);
-    if (!h.pi || !h.parent || !h.pred || !h.depth || !h.flow || !h.up || !h.ord || !h.pos || !h.size || !h.tmp ||
+    if (!h.pi || !h.parent || !h.pred || !h.flow || !h.up || !h.ord || !h.pos || !h.size || !h.tmp ||
         !h.path || !h.seg || !d)
         return PD_ENOMEM;
     int64_t M = m + n;
-    int64_t blk = o.ns_block > 0 ? o.ns_block : (int64_t)sqrt((double)M);
-    if (blk < 2048) blk = 2048;
-    blk = (blk + 7) & ~(int64_t)7;  // blocks start at multiples of 8 (vector loads)
+    if (M >= (int64_t(1) << 31) - 1) return fail(c, PD_ECAPACITY, "network simplex needs fewer than 2^31 arcs");
+    // default block: one pass of the CTA (8 arcs per thread), more for very
+    // large networks; blocks start at multiples of 8 (vector loads)
+    int64_t blk = o.ns_block > 0 ? o.ns_block : std::max<int64_t>(8 * NS_THREADS, (int64_t)sqrt((double)M));
+    blk = (blk + 7) & ~(int64_t)7;
     h.block = blk;
     h.max_pivots = o.max_rounds > 0 ? o.max_rounds : (int64_t(1) << 40);
     h.time_limit_ns = (o.time_limit_ms > 0 ? (uint64_t)o.time_limit_ms : 60000ull) * 1000000ull;
@@ -601,7 +717,7 @@ pd_status ns_solve_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS, i
     size_t smem = ns_smem_bytes(N1);
     int max_optin = 0;
     PD_TRY_CUDA(c, cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    h.smem_nodes = (o.ns_smem != 0 && smem + 6144 <= (size_t)max_optin) ? 1 : 0;
+    h.smem_nodes = (o.ns_smem != 0 && ns_smem_fits(N1, max_optin)) ? 1 : 0;
     if (!h.smem_nodes) smem = 0;
     PD_TRY_CUDA(c, cudaFuncSetAttribute(k_netsimplex, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     PD_TRY_CUDA(c, cudaMemcpyAsync(d, &h, sizeof(NSInst), cudaMemcpyHostToDevice, st));

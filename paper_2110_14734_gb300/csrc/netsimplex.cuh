@@ -22,19 +22,18 @@ struct NSInst {
     const int64_t* supply;
     int64_t* pi;       // n + 1
     int32_t* parent;   // n + 1
-    int64_t* pred;     // n + 1 (arc id; artificial arc of node i is m + i)
-    int32_t* depth;    // n + 1
-    int32_t* flow;     // n + 1: flow on the pred arc (total supply < 2^31)
+    int32_t* pred;     // n + 1 (arc id; artificial arc of node i is m + i; m + n < 2^31)
+    int32_t* flow;     // n + 1: flow on the pred arc (total supply < 2^31; bit 31 = up while solving in global mode)
     uint8_t* up;       // n + 1: pred arc points from the node to its parent
     int32_t* ord;      // n + 1 preorder
     int32_t* pos;      // n + 1
     int32_t* size;     // n + 1
-    int32_t* tmp;      // n + 1 scratch
+    int32_t* tmp;      // n + 1 scratch (re-hang buffer of the global layout)
     int32_t* path;     // 2 (n + 1) scratch: the two half-cycles past the shared-memory part
-    int32_t* seg;      // 4 * (2n + 3) scratch: segment start, length, output offset, depth shift
+    int32_t* seg;      // 3 * (2n + 3) scratch: segment start, length, output offset
     int64_t block;     // pricing block (arcs)
     int32_t smem_nodes; // 1: hot node arrays live in shared memory
-    int32_t pad0;
+    int32_t vec_explicit; // 1: tail, head and cost are 16-byte aligned (vector loads)
     int64_t scanned;   // result: arcs priced
     int64_t max_pivots;
     uint64_t time_limit_ns;
@@ -48,6 +47,9 @@ struct NSInst {
 
 __global__ void k_netsimplex(NSInst* insts, int64_t big);
 size_t ns_smem_bytes(int64_t N1);
+// True if the compact node arrays of N1 nodes fit in shared memory beside the
+// kernel's static shared memory (max_optin: the device's opt-in limit per CTA).
+bool ns_smem_fits(int64_t N1, int max_optin);
 __global__ void k_i64_to_i32_cost(const int64_t* __restrict__ c, int64_t m, int32_t* __restrict__ o,
                                   unsigned long long* __restrict__ bad);
 __global__ void k_abs_sum(const int64_t* __restrict__ s, int64_t n, unsigned long long* __restrict__ out);

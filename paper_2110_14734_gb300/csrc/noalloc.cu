@@ -25,9 +25,8 @@ constexpr size_t OFF_TAIL = 0;
 constexpr size_t OFF_COST = OFF_TAIL + al(4 * NA_ARCS);
 constexpr size_t OFF_PI = OFF_COST + al(4 * NA_ARCS);
 constexpr size_t OFF_PRED = OFF_PI + al(8 * NA_NODES);
-constexpr size_t OFF_PARENT = OFF_PRED + al(8 * NA_NODES);
-constexpr size_t OFF_DEPTH = OFF_PARENT + al(4 * NA_NODES);
-constexpr size_t OFF_FLOW = OFF_DEPTH + al(4 * NA_NODES);
+constexpr size_t OFF_PARENT = OFF_PRED + al(4 * NA_NODES);
+constexpr size_t OFF_FLOW = OFF_PARENT + al(4 * NA_NODES);
 constexpr size_t OFF_UP = OFF_FLOW + al(4 * NA_NODES);
 constexpr size_t OFF_ORD = OFF_UP + al(NA_NODES);
 constexpr size_t OFF_POS = OFF_ORD + al(4 * NA_NODES);
@@ -35,7 +34,7 @@ constexpr size_t OFF_SIZE = OFF_POS + al(4 * NA_NODES);
 constexpr size_t OFF_TMP = OFF_SIZE + al(4 * NA_NODES);
 constexpr size_t OFF_PATH = OFF_TMP + al(4 * NA_NODES);
 constexpr size_t OFF_SEG = OFF_PATH + al(8 * NA_NODES);
-constexpr size_t OFF_INST = OFF_SEG + al(16 * (2 * NA_NODES + 3));
+constexpr size_t OFF_INST = OFF_SEG + al(12 * (2 * NA_NODES + 3));
 constexpr size_t OFF_FLAGS = OFF_INST + al(sizeof(NSInst));
 constexpr size_t SCRATCH_BYTES = OFF_FLAGS + al(64);
 static_assert(SCRATCH_BYTES <= (size_t)12 << 20, "scratch of the allocation-free solve exceeds 12 MiB");
@@ -137,10 +136,10 @@ extern "C" pd_status pd_mcf_solve_noalloc(const pd_network* net, int64_t* opt_ou
     h.head = net->head;
     h.cost = c32;
     h.supply = net->supply;
+    h.vec_explicit = ((((uintptr_t)tail) | ((uintptr_t)net->head) | ((uintptr_t)c32)) & 15) == 0 ? 1 : 0;
     h.pi = (int64_t*)(base + OFF_PI);
-    h.pred = (int64_t*)(base + OFF_PRED);
+    h.pred = (int32_t*)(base + OFF_PRED);
     h.parent = (int32_t*)(base + OFF_PARENT);
-    h.depth = (int32_t*)(base + OFF_DEPTH);
     h.flow = (int32_t*)(base + OFF_FLOW);
     h.up = (uint8_t*)(base + OFF_UP);
     h.ord = (int32_t*)(base + OFF_ORD);
@@ -151,7 +150,7 @@ extern "C" pd_status pd_mcf_solve_noalloc(const pd_network* net, int64_t* opt_ou
     h.seg = (int32_t*)(base + OFF_SEG);
     int64_t M = m + n;
     int64_t blk = (int64_t)sqrt((double)M);
-    if (blk < 2048) blk = 2048;
+    if (blk < 8 * NS_THREADS) blk = 8 * NS_THREADS;
     h.block = (blk + 7) & ~(int64_t)7;
     h.max_pivots = int64_t(1) << 40;
     h.time_limit_ns = 60000ull * 1000000ull;
@@ -159,7 +158,7 @@ extern "C" pd_status pd_mcf_solve_noalloc(const pd_network* net, int64_t* opt_ou
     NA_TRY(cudaGetDevice(&dev));
     NA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     size_t smem = ns_smem_bytes(N1);
-    h.smem_nodes = (smem + 6144 <= (size_t)max_optin) ? 1 : 0;
+    h.smem_nodes = ns_smem_fits(N1, max_optin) ? 1 : 0;
     if (!h.smem_nodes) smem = 0;
     NA_TRY(cudaFuncSetAttribute(k_netsimplex, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     NA_TRY(cudaMemcpyAsync(dinst, &h, sizeof(NSInst), cudaMemcpyHostToDevice, st));
