@@ -84,6 +84,8 @@ typedef struct {
     int64_t ns_block;       /* network simplex pricing block in arcs (0 = max(8192, sqrt(arcs))) */
     int32_t ns_transport;   /* W1 only: 1 = try the transportation form with its certificate first (default) */
     int32_t ns_smem;        /* network simplex: 1 = hot node arrays in shared memory when they fit (default) */
+    int32_t batch_slots;    /* pd_w1_approx_batch: pairs per simplex launch (0 = number of SMs) */
+    int32_t batch_threads;  /* pd_w1_approx_batch: host threads preprocessing pairs (0 = 8) */
 } pd_opts;
 
 void pd_opts_default(pd_opts* opts);
@@ -145,7 +147,8 @@ typedef struct {
     int64_t kernel_launches; /* kernels this call launched */
     float ns_kernel_ms;     /* device time of the network simplex kernel(s) of this call */
     int32_t reserved;
-    float stage_ms[8];      /* quantize+0-condense, RWMD, delta-condense, tree, WSPD, CSR, solve, total */
+    float stage_ms[8];      /* device time of quantize+0-condense, RWMD, delta-condense, tree, WSPD, CSR;
+                               host wall time of the solve (incl. certificate) and of the whole call */
 } pd_result;
 
 /*
@@ -184,9 +187,11 @@ pd_status pd_wspd_sparsify(pd_ctx* ctx, const pd_nodes* nodes, int32_t s, pd_net
 
 /*
  * Exact integer min-cost flow on an uncapacitated network (the min-cost flow
- * of the transshipment network definition), by cost scaling with push/relabel
- * rounds in one persistent kernel.  `net` is device memory in pd_network
- * layout: unique (tail, head) arcs, rows sorted by head, costs in [0, 2^31),
+ * of the transshipment network definition).  Default solver: primal network
+ * simplex with block pricing in one CTA (network-simplex section, run to
+ * optimality); opts->solver = 1 selects cost scaling with push/relabel rounds
+ * in one persistent kernel.  `net` is device memory in pd_network layout:
+ * unique (tail, head) arcs, rows sorted by head, costs in [0, 2^31),
  * supplies summing to 0.  *opt_out (host) receives the optimum; stats (host,
  * may be NULL) receives the solver counters.
  */
@@ -205,6 +210,25 @@ pd_status pd_mcf_solve(pd_ctx* ctx, const pd_network* net, const pd_opts* opts, 
  */
 pd_status pd_w1_approx(pd_ctx* ctx, pd_diagram A, pd_diagram B, double eps, const pd_opts* opts,
                        pd_result* out, void* stream);
+
+/*
+ * Approximate W1 of `count` independent pairs (A[i], B[i]), each computed
+ * exactly as pd_w1_approx computes it with the same eps and opts (so
+ * out[i].opt_quanta equals what pd_w1_approx returns for that pair).  The
+ * paper solves one pair at a time; this batched form has no counterpart
+ * there.  Pairs are processed in waves of W = opts->batch_slots (0 = the
+ * number of SMs) pairs: the preprocessing of each pair of a wave runs on the
+ * stream as in pd_w1_approx, then the network simplex solves of the wave
+ * share one launch with one CTA per pair, then each pair's certificate runs.
+ * A and B: host arrays of `count` descriptors; out: host array of `count`
+ * results (ns_kernel_ms and stage_ms[6] include the wave's shared launch).
+ * Device memory: one buffer set per slot, grown on demand and kept by the
+ * context until pd_destroy (the context's arena cap applies to each slot).
+ * opts->solver must be 0.  On an error the status of the first failing pair
+ * is returned (its index in pd_last_error) and out is unspecified.
+ */
+pd_status pd_w1_approx_batch(pd_ctx* ctx, const pd_diagram* A, const pd_diagram* B, int64_t count,
+                             double eps, const pd_opts* opts, pd_result* out, void* stream);
 
 /*
  * Allocation-free min-cost flow (no counterpart in the paper).

@@ -3,10 +3,17 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <mutex>
 #include <new>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "internal.h"
+#include "netsimplex.cuh"
 #include "prims.cuh"
 
 using namespace pd;
@@ -160,6 +167,47 @@ extern "C" void pd_opts_default(pd_opts* o) {
     o->ns_smem = 1;
 }
 
+namespace pd {
+
+static bool ctx_init(Ctx* c, int device, size_t cap) {
+    c->device = device;
+    c->cap = cap;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_small, 64 * sizeof(int64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+Ctx* ctx_new(int device, size_t cap) {
+    Ctx* c = new (std::nothrow) Ctx();
+    if (!c) return nullptr;
+    if (!ctx_init(c, device, cap)) {
+        ctx_free(c);
+        return nullptr;
+    }
+    return c;
+}
+
+void ctx_free(Ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    for (Ctx* sl : c->slots) ctx_free(sl);
+    c->slots.clear();
+    for (Ctx* wk : c->workers) ctx_free(wk);
+    c->workers.clear();
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    for (int i = 0; i < B_COUNT; i++)
+        if (c->ptr[i]) cudaFree(c->ptr[i]);
+    if (c->h_small) cudaFreeHost(c->h_small);
+    c->h_small = nullptr;
+    delete c;
+}
+
+}  // namespace pd
+
 extern "C" pd_status pd_create(pd_ctx** out, int device, size_t arena_bytes) {
     if (!out) return PD_EINVAL;
     *out = nullptr;
@@ -170,12 +218,8 @@ extern "C" pd_status pd_create(pd_ctx** out, int device, size_t arena_bytes) {
     }
     pd_ctx* c = new (std::nothrow) pd_ctx();
     if (!c) return PD_ENOMEM;
-    c->device = device;
-    c->cap = arena_bytes;
-    if (cudaSetDevice(device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaMallocHost((void**)&c->h_small, 64 * sizeof(int64_t)) != cudaSuccess) {
-        cudaGetLastError();
+    if (!ctx_init(c, device, arena_bytes)) {
+        if (c->h_small) cudaFreeHost(c->h_small);
         delete c;
         return PD_ECUDA;
     }
@@ -186,6 +230,10 @@ extern "C" pd_status pd_create(pd_ctx** out, int device, size_t arena_bytes) {
 extern "C" void pd_destroy(pd_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
+    for (Ctx* sl : c->slots) ctx_free(sl);
+    c->slots.clear();
+    for (Ctx* wk : c->workers) ctx_free(wk);
+    c->workers.clear();
     for (int i = 0; i < B_COUNT; i++)
         if (c->ptr[i]) cudaFree(c->ptr[i]);
     if (c->h_small) cudaFreeHost(c->h_small);
@@ -194,7 +242,7 @@ extern "C" void pd_destroy(pd_ctx* c) {
 
 extern "C" const char* pd_last_error(const pd_ctx* c) { return c ? c->err.c_str() : "no context"; }
 
-static pd_status check_diag(pd_ctx* c, const pd_diagram& d) {
+static pd_status check_diag(Ctx* c, const pd_diagram& d) {
     if (d.n < 0) return fail(c, PD_EINVAL, "negative diagram size");
     if (d.n > 0 && !d.bd) return fail(c, PD_EINVAL, "NULL diagram data");
     if (d.dtype != PD_F32 && d.dtype != PD_U8) return fail(c, PD_EINVAL, "unknown dtype");
@@ -204,7 +252,7 @@ static pd_status check_diag(pd_ctx* c, const pd_diagram& d) {
     return PD_OK;
 }
 
-static pd_status stage_inputs(pd_ctx* c, const pd_diagram& A, const pd_diagram& B, DevDiag* a, DevDiag* b,
+static pd_status stage_inputs(Ctx* c, const pd_diagram& A, const pd_diagram& B, DevDiag* a, DevDiag* b,
                               cudaStream_t st) {
     PD_TRY(check_diag(c, A));
     PD_TRY(check_diag(c, B));
@@ -332,86 +380,79 @@ extern "C" pd_status pd_mcf_solve(pd_ctx* c, const pd_network* net, const pd_opt
     return PD_OK;
 }
 
-extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double eps, const pd_opts* opts,
-                                  pd_result* out, void* stream) {
-    if (!c || !out) return PD_EINVAL;
-    c->err.clear();
-    pd_opts o = resolve_opts(opts);
-    if (!(eps > 0.0) && o.s_override <= 0) return fail(c, PD_EINVAL, "eps must be > 0 (or set s_override)");
-    c->last_ns_ms = 0.f;
-    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
-    cudaStream_t st = (cudaStream_t)stream;
-    pd_result r;
-    memset(&r, 0, sizeof(r));
-    const long long launches0 = launch_count_ref();
-    cudaEvent_t ev[5];
-    for (int q = 0; q < 5; q++) PD_TRY_CUDA(c, cudaEventCreate(&ev[q]));
+// Algorithm 4 up to the network handed to the solver: quantise, 0-condense,
+// RWMD, delta-condense, sparse network, diagonal merge.
+struct Front {
+    Hats h{};
+    int64_t L[3] = {0, 0, 0};
+    int64_t s = 0, G = 1, P = 0;
+    double delta = 0.0;
+    int k = 0;
+    pd_nodes nodes{};
+    pd_network net{}, mnet{};
+    float ms[6] = {};  // quantise+0-condense, RWMD, delta-condense, tree, WSPD, CSR
+};
+
+static pd_status front_half(Ctx* c, const pd_diagram& A, const pd_diagram& B, double eps, const pd_opts& o,
+                            Front* f, cudaStream_t st) {
+    cudaEvent_t ev[4];
+    for (int q = 0; q < 4; q++) PD_TRY_CUDA(c, cudaEventCreate(&ev[q]));
+    struct Guard {
+        cudaEvent_t* e;
+        ~Guard() {
+            for (int q = 0; q < 4; q++) cudaEventDestroy(e[q]);
+        }
+    } guard{ev};
     PD_TRY_CUDA(c, cudaEventRecord(ev[0], st));
     DevDiag a, b;
     PD_TRY(stage_inputs(c, A, B, &a, &b, st));
-    int k = o.coord_shift >= 0 ? o.coord_shift : default_shift(A.dtype);
-    Hats h;
-    PD_TRY(stage_condense0(c, a, b, k, &h, st));
+    f->k = o.coord_shift >= 0 ? o.coord_shift : default_shift(A.dtype);
+    PD_TRY(stage_condense0(c, a, b, f->k, &f->h, st));
     PD_TRY_CUDA(c, cudaEventRecord(ev[1], st));
-    int64_t L[3];
-    PD_TRY(stage_rwmd(c, h, L, st));
+    PD_TRY(stage_rwmd(c, f->h, f->L, st));
     PD_TRY_CUDA(c, cudaEventRecord(ev[2], st));
-    int64_t s = o.s_override > 0 ? o.s_override : s_for_eps(eps);
-    if (s < 1) return fail(c, PD_EINVAL, "no WSPD parameter s for this eps");
-    double delta = 0.0;
-    int64_t G = 1, P = 0;
-    if (o.condense) delta_for(L[0], L[1], h.FA, h.FB, s, &delta, &G, &P);
-    if (!o.perturb) P = 0;
-    pd_nodes nodes;
-    PD_TRY(stage_condense_delta(c, h, G, P, o.seed, &nodes, st));
-    c->nodes = nodes;
+    f->s = o.s_override > 0 ? o.s_override : s_for_eps(eps);
+    if (f->s < 1) return fail(c, PD_EINVAL, "no WSPD parameter s for this eps");
+    f->delta = 0.0;
+    f->G = 1;
+    f->P = 0;
+    if (o.condense) delta_for(f->L[0], f->L[1], f->h.FA, f->h.FB, f->s, &f->delta, &f->G, &f->P);
+    if (!o.perturb) f->P = 0;
+    PD_TRY(stage_condense_delta(c, f->h, f->G, f->P, o.seed, &f->nodes, st));
+    c->nodes = f->nodes;
     PD_TRY_CUDA(c, cudaEventRecord(ev[3], st));
-    pd_network net;
-    float mt = 0, mw = 0, mc = 0;
-    PD_TRY(stage_network(c, nodes, s, &net, &mt, &mw, &mc, st));
-    c->net = net;
-    cudaEvent_t e5, e6;
-    PD_TRY_CUDA(c, cudaEventCreate(&e5));
-    PD_TRY_CUDA(c, cudaEventCreate(&e6));
-    PD_TRY_CUDA(c, cudaEventRecord(e5, st));
+    PD_TRY(stage_network(c, f->nodes, f->s, &f->net, &f->ms[3], &f->ms[4], &f->ms[5], st));
+    c->net = f->net;
     // The solver sees ā and b̄ merged into one diagonal node (the zero-cost
     // arc b̄ -> ā contracted): every flow of the paper's network maps to one of
     // the same cost, and an optimal acyclic flow of the merged network sends at
     // most |A| units into and |B| units out of the diagonal, so it maps back.
-    pd_network mnet;
-    PD_TRY(merge_diagonal(c, net, nodes.n_nodes, &mnet, st));
-    SolveStats ss;
-    if (o.solver == 1)
-        PD_TRY(stage_solve(c, mnet, o, &ss, st));
-    else
-        PD_TRY(ns_solve_w1(c, nodes, net, mnet, o, &ss, st));
-    PD_TRY_CUDA(c, cudaEventRecord(e6, st));
-    PD_TRY_CUDA(c, cudaEventSynchronize(e6));
-    float ms[4];
-    cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
-    cudaEventElapsedTime(&ms[1], ev[1], ev[2]);
-    cudaEventElapsedTime(&ms[2], ev[2], ev[3]);
-    cudaEventElapsedTime(&ms[3], e5, e6);
-    float tot = 0;
-    cudaEventElapsedTime(&tot, ev[0], e6);
-    for (int q = 0; q < 5; q++) cudaEventDestroy(ev[q]);
-    cudaEventDestroy(e5);
-    cudaEventDestroy(e6);
+    PD_TRY(merge_diagonal(c, f->net, f->nodes.n_nodes, &f->mnet, st));
+    PD_TRY_CUDA(c, cudaEventSynchronize(ev[3]));
+    cudaEventElapsedTime(&f->ms[0], ev[0], ev[1]);
+    cudaEventElapsedTime(&f->ms[1], ev[1], ev[2]);
+    cudaEventElapsedTime(&f->ms[2], ev[2], ev[3]);
+    return PD_OK;
+}
+
+static void fill_result(const Front& f, const SolveStats& ss, pd_result* out) {
+    pd_result r;
+    memset(&r, 0, sizeof(r));
     r.opt_quanta = ss.opt;
-    r.w1 = ldexp((double)ss.opt, -k);
-    r.rwmd_A = L[0];
-    r.rwmd_B = L[1];
-    r.rwmd_quanta = L[2];
+    r.w1 = ldexp((double)ss.opt, -f.k);
+    r.rwmd_A = f.L[0];
+    r.rwmd_B = f.L[1];
+    r.rwmd_quanta = f.L[2];
     r.slack_quanta = ss.slack;
-    r.mass_A = h.FA;
-    r.mass_B = h.FB;
-    r.s = (int32_t)s;
-    r.coord_shift = k;
-    r.delta = delta;
-    r.cell_quanta = G;
-    r.shift_quanta = P;
-    r.n_nodes = nodes.n_nodes;
-    r.n_arcs = net.n_arcs;
+    r.mass_A = f.h.FA;
+    r.mass_B = f.h.FB;
+    r.s = (int32_t)f.s;
+    r.coord_shift = f.k;
+    r.delta = f.delta;
+    r.cell_quanta = f.G;
+    r.shift_quanta = f.P;
+    r.n_nodes = f.nodes.n_nodes;
+    r.n_arcs = f.net.n_arcs;
     r.phases = ss.phases;
     r.verified = ss.verified;
     r.rounds = ss.rounds;
@@ -425,16 +466,241 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
     r.arcs_priced = ss.scanned;
     r.solve_method = ss.method;
     r.cert_failures = (int32_t)ss.cert_failures;
-    r.stage_ms[0] = ms[0];
-    r.stage_ms[1] = ms[1];
-    r.stage_ms[2] = ms[2];
-    r.stage_ms[3] = mt;
-    r.stage_ms[4] = mw;
-    r.stage_ms[5] = mc;
-    r.stage_ms[6] = ms[3];
-    r.stage_ms[7] = tot;
-    r.kernel_launches = launch_count_ref() - launches0;
-    r.ns_kernel_ms = c->last_ns_ms;
+    for (int q = 0; q < 6; q++) r.stage_ms[q] = f.ms[q];
     *out = r;
+}
+
+static float elapsed_ms(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double eps, const pd_opts* opts,
+                                  pd_result* out, void* stream) {
+    if (!c || !out) return PD_EINVAL;
+    c->err.clear();
+    pd_opts o = resolve_opts(opts);
+    if (!(eps > 0.0) && o.s_override <= 0) return fail(c, PD_EINVAL, "eps must be > 0 (or set s_override)");
+    c->last_ns_ms = 0.f;
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long launches0 = launch_count_ref();
+    const auto t0 = std::chrono::steady_clock::now();
+    Front f;
+    PD_TRY(front_half(c, A, B, eps, o, &f, st));
+    const auto t1 = std::chrono::steady_clock::now();
+    SolveStats ss;
+    if (o.solver == 1)
+        PD_TRY(stage_solve(c, f.mnet, o, &ss, st));
+    else
+        PD_TRY(ns_solve_w1(c, f.nodes, f.net, f.mnet, o, &ss, st));
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    fill_result(f, ss, out);
+    out->stage_ms[6] = elapsed_ms(t1);
+    out->stage_ms[7] = elapsed_ms(t0);
+    out->kernel_launches = launch_count_ref() - launches0;
+    out->ns_kernel_ms = c->last_ns_ms;
     return PD_OK;
+}
+
+// A pair of a batch between its preprocessing and its certificate: the
+// transportation instance lives in the pair's slot, with copies of what the
+// certificate reads (node coordinates, sparse network rows and heads).
+struct BatchPair {
+    Front f;
+    W1Prep w;
+    pd_nodes nodes{};   // slot copies: n_nodes, X, Y
+    pd_network ws{};    // slot copies: n_nodes, n_arcs, row_ptr, head
+    bool done = false;  // solved during preprocessing (no transportation form)
+    SolveStats ss;
+    float front_ms = 0.f, solve_ms = 0.f;
+    long long launches = 0;
+    int inst = -1;      // index in the wave's launch
+};
+
+static pd_status persist_for_certificate(Ctx* slot, const Front& f, BatchPair* bp, cudaStream_t st) {
+    const int64_t N = f.nodes.n_nodes, n = f.net.n_nodes, m = f.net.n_arcs;
+    int32_t* X = bufT<int32_t>(slot, B_NX, N);
+    int32_t* Y = bufT<int32_t>(slot, B_NY, N);
+    int64_t* rp = bufT<int64_t>(slot, B_ROWPTR, n + 1);
+    int32_t* hd = bufT<int32_t>(slot, B_HEAD, m);
+    if (!X || !Y || !rp || !hd) return PD_ENOMEM;
+    if (N > 0) {
+        PD_TRY_CUDA(slot, cudaMemcpyAsync(X, f.nodes.X, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st));
+        PD_TRY_CUDA(slot, cudaMemcpyAsync(Y, f.nodes.Y, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st));
+    }
+    PD_TRY_CUDA(slot, cudaMemcpyAsync(rp, f.net.row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, st));
+    if (m > 0) PD_TRY_CUDA(slot, cudaMemcpyAsync(hd, f.net.head, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, st));
+    bp->nodes = pd_nodes{N, X, Y, nullptr, nullptr, nullptr};
+    bp->ws = pd_network{n, m, rp, hd, nullptr, nullptr};
+    return PD_OK;
+}
+
+// Preprocessing of one pair on a worker context: front half, then the
+// transportation instance in the pair's slot (or, without one, the solve of
+// the sparse network right here).
+static pd_status batch_prepare(Ctx* work, Ctx* slot, const pd_diagram& A, const pd_diagram& B, double eps,
+                               const pd_opts& o, BatchPair* bp) {
+    cudaStream_t st = work->own_stream;
+    const long long l0 = launch_count_ref();
+    const auto t0 = std::chrono::steady_clock::now();
+    work->last_ns_ms = 0.f;
+    slot->last_ns_ms = 0.f;
+    PD_TRY(front_half(work, A, B, eps, o, &bp->f, st));
+    PD_TRY(ns_prepare_w1(slot, bp->f.nodes, bp->f.net, bp->f.mnet, o, &bp->w, st));
+    if (bp->w.ns.ready) {
+        PD_TRY(persist_for_certificate(slot, bp->f, bp, st));
+    } else {
+        const auto t1 = std::chrono::steady_clock::now();
+        PD_TRY(ns_finish_w1(work, bp->f.nodes, bp->f.net, &bp->f.mnet, o, bp->w, nullptr, NSInst{}, &bp->ss, st));
+        bp->solve_ms = elapsed_ms(t1);
+        bp->done = true;
+    }
+    PD_TRY_CUDA(work, cudaStreamSynchronize(st));
+    bp->front_ms = elapsed_ms(t0) - bp->solve_ms;
+    bp->launches = launch_count_ref() - l0;
+    if (bp->done) slot->last_ns_ms = work->last_ns_ms;
+    return PD_OK;
+}
+
+extern "C" pd_status pd_w1_approx_batch(pd_ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t count,
+                                        double eps, const pd_opts* opts, pd_result* out, void* stream) {
+    if (!c) return PD_EINVAL;
+    c->err.clear();
+    if (count < 0 || (count > 0 && (!A || !B || !out))) return fail(c, PD_EINVAL, "bad batch arguments");
+    if (count == 0) return PD_OK;
+    pd_opts o = resolve_opts(opts);
+    if (!(eps > 0.0) && o.s_override <= 0) return fail(c, PD_EINVAL, "eps must be > 0 (or set s_override)");
+    if (o.solver == 1) return fail(c, PD_EINVAL, "the batched solve runs the network simplex only");
+    if (o.batch_slots < 0 || o.batch_threads < 0) return fail(c, PD_EINVAL, "batch_slots and batch_threads must be >= 0");
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t W = std::min<int64_t>(count, o.batch_slots > 0 ? o.batch_slots : std::max(c->sm_count, 1));
+    const int nthr = (int)std::min<int64_t>(W, o.batch_threads > 0 ? o.batch_threads : 8);
+    while ((int64_t)c->slots.size() < W) {
+        Ctx* sl = ctx_new(c->device, c->cap);
+        if (!sl) return fail(c, PD_ECUDA, "cannot create the buffers of a batch slot");
+        c->slots.push_back(sl);
+    }
+    while ((int)c->workers.size() < nthr) {
+        Ctx* wk = ctx_new(c->device, c->cap);
+        if (!wk) return fail(c, PD_ECUDA, "cannot create a batch worker");
+        if (cudaStreamCreateWithFlags(&wk->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            ctx_free(wk);
+            return fail(c, PD_ECUDA, "cannot create a batch worker stream");
+        }
+        c->workers.push_back(wk);
+    }
+    NSInst* d = bufT<NSInst>(c, B_NS_INST, W);
+    if (!d) return PD_ENOMEM;
+    // the workers start after everything already queued on the caller's stream
+    cudaEvent_t ready;
+    PD_TRY_CUDA(c, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    std::vector<BatchPair> bp((size_t)W);
+    std::vector<NSInst> hin, hout;
+    pd_status status = PD_OK;
+    for (int64_t base = 0; base < count && status == PD_OK; base += W) {
+        const int64_t nw = std::min<int64_t>(W, count - base);
+        for (int64_t j = 0; j < nw; j++) bp[(size_t)j] = BatchPair{};
+        // ---- preprocessing: host threads, one worker context and stream each
+        cudaEventRecord(ready, st);
+        std::atomic<int64_t> next{0};
+        std::mutex mu;
+        pd_status first = PD_OK;
+        std::string first_msg;
+        auto run = [&](int t) {
+            Ctx* wk = c->workers[(size_t)t];
+            cudaSetDevice(c->device);
+            cudaStreamWaitEvent(wk->own_stream, ready, 0);
+            for (;;) {
+                const int64_t j = next.fetch_add(1);
+                if (j >= nw) break;
+                {
+                    std::lock_guard<std::mutex> g(mu);
+                    if (first != PD_OK) break;
+                }
+                Ctx* sl = c->slots[(size_t)j];
+                wk->err.clear();
+                sl->err.clear();
+                pd_status e = batch_prepare(wk, sl, A[base + j], B[base + j], eps, o, &bp[(size_t)j]);
+                if (e != PD_OK) {
+                    std::lock_guard<std::mutex> g(mu);
+                    if (first == PD_OK) {
+                        first = e;
+                        first_msg = "pair " + std::to_string(base + j) + ": " + (wk->err.empty() ? sl->err : wk->err);
+                    }
+                    break;
+                }
+            }
+        };
+        std::vector<std::thread> th;
+        for (int t = 1; t < nthr; t++) th.emplace_back(run, t);
+        run(0);
+        for (auto& x : th) x.join();
+        if (first != PD_OK) {
+            status = fail(c, first, first_msg);
+            break;
+        }
+        // ---- one launch for the wave, one CTA per pair
+        hin.clear();
+        size_t smem = 0;
+        for (int64_t j = 0; j < nw; j++) {
+            BatchPair& p = bp[(size_t)j];
+            if (p.done) continue;
+            p.inst = (int)hin.size();
+            hin.push_back(p.w.ns.h);
+            smem = std::max(smem, p.w.ns.smem);
+        }
+        hout.assign(hin.size(), NSInst{});
+        c->last_ns_ms = 0.f;
+        const auto tl = std::chrono::steady_clock::now();
+        const long long lw = launch_count_ref();
+        status = ns_run(c, hin.data(), (int)hin.size(), smem, d, hout.data(), st);
+        if (status != PD_OK) break;
+        const float wave_ms = elapsed_ms(tl), wave_ns = c->last_ns_ms;
+        const long long wave_launches = launch_count_ref() - lw;
+        // ---- certificates; a pair whose certificate fails is preprocessed
+        // again and solved on its sparse network
+        for (int64_t j = 0; j < nw && status == PD_OK; j++) {
+            BatchPair& p = bp[(size_t)j];
+            Ctx* sl = c->slots[(size_t)j];
+            if (!p.done) {
+                const long long l0 = launch_count_ref();
+                const auto t0 = std::chrono::steady_clock::now();
+                sl->last_ns_ms = 0.f;
+                status = ns_finish_w1(sl, p.nodes, p.ws, nullptr, o, p.w, d + p.inst, hout[(size_t)p.inst], &p.ss, st);
+                if (status == PD_OK && p.ss.method == -1) {
+                    Ctx* wk = c->workers[0];
+                    Front f2;
+                    const SolveStats first_try = p.ss;
+                    status = front_half(wk, A[base + j], B[base + j], eps, o, &f2, wk->own_stream);
+                    if (status == PD_OK) status = ns_solve_network(wk, f2.mnet, o, &p.ss, wk->own_stream);
+                    if (status == PD_OK) status = cudaStreamSynchronize(wk->own_stream) == cudaSuccess ? PD_OK : PD_ECUDA;
+                    if (status != PD_OK) {
+                        status = fail(c, status, "pair " + std::to_string(base + j) + ": " + wk->err);
+                        break;
+                    }
+                    p.ss.pivots += first_try.pivots;
+                    p.ss.degenerate += first_try.degenerate;
+                    p.ss.scanned += first_try.scanned;
+                    p.ss.cert_failures = first_try.cert_failures;
+                    sl->last_ns_ms += wk->last_ns_ms;
+                }
+                if (status != PD_OK) {
+                    status = fail(c, status, "pair " + std::to_string(base + j) + ": " + sl->err);
+                    break;
+                }
+                p.solve_ms = wave_ms + elapsed_ms(t0);
+                p.launches += wave_launches + (launch_count_ref() - l0);
+            }
+            pd_result& res = out[base + j];
+            fill_result(p.f, p.ss, &res);
+            res.stage_ms[6] = p.solve_ms;
+            res.stage_ms[7] = p.front_ms + p.solve_ms;
+            res.kernel_launches = p.launches;
+            res.ns_kernel_ms = (p.done ? 0.f : wave_ns) + sl->last_ns_ms;
+        }
+    }
+    cudaEventDestroy(ready);
+    return status;
 }

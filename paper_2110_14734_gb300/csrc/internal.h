@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/pdw1.h"
 
@@ -42,8 +43,14 @@ struct Ctx {
     pd_nodes nodes{};
     pd_network net{};
     int sm_count = 0;
-    float last_ns_ms = 0.f;  // device time of the last network simplex kernel
+    float last_ns_ms = 0.f;  // device time of the network simplex kernels since it was last reset
+    std::vector<Ctx*> slots;    // pd_w1_approx_batch: per-pair buffers kept from preprocessing to solve
+    std::vector<Ctx*> workers;  // pd_w1_approx_batch: preprocessing contexts, one per host thread
+    cudaStream_t own_stream = nullptr;  // stream of a worker context
 };
+
+Ctx* ctx_new(int device, size_t cap);  // nullptr on failure
+void ctx_free(Ctx* c);
 
 // Returns a device buffer of at least `bytes` bytes (contents undefined), or
 // nullptr (ctx->err set) when allocation fails or the cap is reached.
@@ -89,11 +96,6 @@ struct SolveStats {
     int64_t opt = 0, slack = 0, rounds = 0, pushes = 0, relabels = 0, repairs = 0, updates = 0, update_passes = 0;
     int64_t pivots = 0, degenerate = 0, cert_failures = 0, scanned = 0;
     int32_t phases = 0, verified = 0, method = 0;  // method: 0 cost scaling, 1 simplex on the network, 2 transport form
-};
-
-struct NSOut {
-    int64_t opt = 0, pivots = 0, degenerate = 0, scanned = 0;
-    int32_t status = 0;
 };
 
 pd_status stage_condense0(Ctx* c, const DevDiag& A, const DevDiag& B, int k, Hats* out, cudaStream_t st);

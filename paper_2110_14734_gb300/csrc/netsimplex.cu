@@ -94,18 +94,22 @@ constexpr int NS_SEGSM = 65;     // re-hang segments kept in shared memory (path
 constexpr int NS_REGS = 9;       // shared-memory layout: at most 9 * 1024 nodes (re-hang buffered in registers)
 
 template <typename IX>
-__device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T, int64_t big) {
+__device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
+    constexpr unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int32_t n = I.n, root = n, N1 = n + 1;
-    const int64_t M = I.m + n;  // arcs including the artificial ones
+    const int64_t M = I.m + n;  // arcs including the artificial ones (< 2^31)
+    const int64_t big = I.big;
     __shared__ int32_t pa[NS_LMAX], pb[NS_LMAX];
     int32_t* gpa = I.path;
     int32_t* gpb = I.path + N1;
     __shared__ int32_t s_la, s_lb;
-    __shared__ int64_t s_ce;
-    __shared__ int64_t s_val[32];
-    __shared__ int64_t s_idx[32];
-    __shared__ int64_t s_next, s_dpi, s_e;
+    __shared__ int32_t s_wkey[2][32];    // per-warp pricing minima (clamped), double-buffered
+    __shared__ uint32_t s_widx[2][32];
+    __shared__ int64_t s_wval[2][32];    // exact reduced cost of each warp's winner
+    __shared__ uint32_t s_mask[2][32][NS_REGS];  // path discovery ballots, i-side and j-side
+    __shared__ int32_t s_cnt[2][32];
+    __shared__ int64_t s_dpi;
     __shared__ int32_t s_go, s_status;
     __shared__ int32_t s_L0, s_S, s_pr, s_nseg, s_segsm;
     __shared__ int32_t sseg[3][NS_SEGSM];
@@ -130,34 +134,40 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T, int64
         T.od[0] = (IX)root;
         T.ps[root] = 0;
         T.sz[root] = (IX)N1;
-        s_next = 0;
         s_status = 0;
     }
     __syncthreads();
     const uint64_t t0 = ns_now();
     int64_t pivots = 0, degen = 0, nscan = 0;
     const int64_t B = I.block < 1 ? 1 : I.block;
+    int64_t next = 0;  // first arc of the next pricing block (same in every thread)
+    int pb_buf = 0;
 
     for (;;) {
-        // ---- pricing: blocks of B arcs from s_next; the most negative reduced
-        // cost of the first block that has one enters -------------------------
-        int64_t scanned = 0, a0 = s_next;
-        bool found = false;
+        // ---- pricing: blocks of B arcs from `next`; the most negative reduced
+        // cost of the first block that has one enters.  Every thread ends with
+        // the same (ent, rc).  Across threads the reduction compares a 32-bit
+        // key, -bits(float(-rc)), which is monotone in rc (equal only within
+        // float rounding; ties go to the smallest arc index): any arc of
+        // negative reduced cost is a valid entering arc, and the choice stays
+        // deterministic.
+        int64_t scanned = 0, a0 = next;
+        int64_t ent = -1, rc = 0;
         while (scanned < M) {
             const int64_t aend = a0 + B < M ? a0 + B : M;
             const int64_t len = aend - a0;
             int64_t lb = 0, li = -1;
             for (int64_t c0 = a0 + 8 * (int64_t)tid; c0 < aend; c0 += 8 * NS_THREADS) {
                 if (c0 + 8 <= aend && c0 + 8 <= I.mst) {
-                    int4 w0 = __ldcs((const int4*)(I.cmat + c0));
-                    int4 w1 = __ldcs((const int4*)(I.cmat + c0 + 4));
+                    int4 w0 = __ldcg((const int4*)(I.cmat + c0));
+                    int4 w1 = __ldcg((const int4*)(I.cmat + c0 + 4));
                     int32_t cv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
                     int32_t i = (int32_t)c0 / (int32_t)I.nT, j = (int32_t)c0 - i * (int32_t)I.nT;
                     int64_t pt = T.pi[i];
 #pragma unroll
                     for (int q = 0; q < 8; q++) {
-                        int64_t rc = (int64_t)cv[q] - pt + T.pi[I.nS + j];
-                        take_min(rc, c0 + q, lb, li);
+                        int64_t r = (int64_t)cv[q] - pt + T.pi[I.nS + j];
+                        take_min(r, c0 + q, lb, li);
                         if (++j == (int32_t)I.nT) {
                             j = 0;
                             ++i;
@@ -167,9 +177,9 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T, int64
                 } else if (I.vec_explicit && c0 >= I.mst && c0 + 8 <= aend && c0 + 8 <= I.m &&
                            ((c0 - I.mst) & 7) == 0) {
                     const int64_t x = c0 - I.mst;
-                    int4 t0v = __ldcs((const int4*)(I.tail + x)), t1v = __ldcs((const int4*)(I.tail + x + 4));
-                    int4 h0 = __ldcs((const int4*)(I.head + x)), h1 = __ldcs((const int4*)(I.head + x + 4));
-                    int4 k0 = __ldcs((const int4*)(I.cost + x)), k1 = __ldcs((const int4*)(I.cost + x + 4));
+                    int4 t0v = __ldcg((const int4*)(I.tail + x)), t1v = __ldcg((const int4*)(I.tail + x + 4));
+                    int4 h0 = __ldcg((const int4*)(I.head + x)), h1 = __ldcg((const int4*)(I.head + x + 4));
+                    int4 k0 = __ldcg((const int4*)(I.cost + x)), k1 = __ldcg((const int4*)(I.cost + x + 4));
                     int32_t tv[8] = {t0v.x, t0v.y, t0v.z, t0v.w, t1v.x, t1v.y, t1v.z, t1v.w};
                     int32_t hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
                     int32_t cv[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
@@ -184,94 +194,132 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T, int64
                     }
                 }
             }
-            for (int off = 16; off > 0; off >>= 1) {
-                int64_t ov = __shfl_xor_sync(0xffffffffu, lb, off);
-                int64_t oi = __shfl_xor_sync(0xffffffffu, li, off);
-                if (ov < lb || (ov == lb && oi >= 0 && (li < 0 || oi < li))) {
-                    lb = ov;
-                    li = oi;
-                }
-            }
+            const int32_t key = lb < 0 ? -__float_as_int((float)(-lb)) : 0;
+            const int32_t wmin = __reduce_min_sync(FULL, key);
+            const uint32_t cand = (wmin < 0 && key == wmin) ? (uint32_t)li : 0xffffffffu;
+            const uint32_t widx = __reduce_min_sync(FULL, cand);
             if (lane == 0) {
-                s_val[wid] = lb;
-                s_idx[wid] = li;
+                s_wkey[pb_buf][wid] = wmin;
+                s_widx[pb_buf][wid] = widx;
             }
+            if (wmin < 0 && cand == widx) s_wval[pb_buf][wid] = lb;
             __syncthreads();
+            const int32_t k2 = s_wkey[pb_buf][lane];
+            const uint32_t i2 = s_widx[pb_buf][lane];
+            const int32_t bmin = __reduce_min_sync(FULL, k2);
+            const uint32_t c2 = (bmin < 0 && k2 == bmin) ? i2 : 0xffffffffu;
+            const uint32_t bidx = __reduce_min_sync(FULL, c2);
             scanned += len;
             nscan += len;
             a0 = aend >= M ? 0 : aend;
-            if (wid == 0) {
-                int64_t bv = s_val[lane], bi = s_idx[lane];
-                for (int off = 16; off > 0; off >>= 1) {
-                    int64_t ov = __shfl_xor_sync(0xffffffffu, bv, off);
-                    int64_t oi = __shfl_xor_sync(0xffffffffu, bi, off);
-                    if (ov < bv || (ov == bv && oi >= 0 && (bi < 0 || oi < bi))) {
-                        bv = ov;
-                        bi = oi;
-                    }
-                }
-                if (lane == 0) {
-                    s_e = bv < 0 ? bi : -1;
-                    if (bv < 0) s_next = a0;
-                }
-            }
-            __syncthreads();
-            if (s_e >= 0) {
-                found = true;
+            if (bmin < 0) {
+                const int wl = __ffs(__ballot_sync(FULL, c2 == bidx)) - 1;
+                rc = s_wval[pb_buf][wl];
+                ent = bidx;
+                next = a0;
+                pb_buf ^= 1;
                 break;
             }
+            pb_buf ^= 1;
         }
-        if (!found) break;  // no arc with a negative reduced cost: optimal
-        const int64_t ent = s_e;
-        if (tid == 0) s_go = (pivots < I.max_pivots && ns_now() - t0 <= I.time_limit_ns) ? 1 : 0;
-        __syncthreads();
-        if (!s_go) {
+        if (ent < 0) break;  // no arc with a negative reduced cost: optimal
+        if (pivots >= I.max_pivots) {
             if (tid == 0) s_status = 2;
-            __syncthreads();
             break;
         }
         pivots++;
 
-        // ---- pivot ----------------------------------------------------------
-        if (wid == 0) {
-            // the two half-cycles, walked concurrently by lanes 0 and 1: from i
-            // up to the first ancestor of j, and from j up to the first ancestor
-            // of i -- both stop at the apex
-            int32_t i, j;
-            arc_ends(I, ent, &i, &j);
+        // ---- the two half-cycles: from i up to (not including) the apex, and
+        // from j up to the apex.  PA(0) = i, PA(la - 1) = the child of the apex
+        // on i's side; PB likewise from j.
+        int32_t i, j;
+        arc_ends(I, ent, &i, &j);
+        if constexpr (sizeof(IX) == 2) {
+            // whole CTA: a node is on i's side iff it is an ancestor of i (or i)
+            // and not of j, by the preorder test pos(v) <= pos(x) < pos(v) +
+            // size(v).  Each warp scans a contiguous range of preorder positions
+            // (so matches come out ordered from the apex down); ballots are kept
+            // for the second pass, which writes each match at its rank.
+            const int32_t pi_ = T.ps[i], pj = T.ps[j];
+            const int32_t C = (((N1 + 31) / 32) + 31) & ~31;  // positions per warp, <= 32 * NS_REGS
+            const int32_t iters = C >> 5;
+            const int32_t x0 = wid * C;
+            int32_t cI = 0, cJ = 0;
+            for (int32_t it = 0; it < iters; it++) {
+                const int32_t x = x0 + (it << 5) + lane;
+                bool inI = false, inJ = false;
+                if (x < N1) {
+                    const int32_t e = x + (int32_t)T.sz[T.od[x]];
+                    const bool ai = x <= pi_ && pi_ < e, aj = x <= pj && pj < e;
+                    inI = ai && !aj;
+                    inJ = aj && !ai;
+                }
+                const uint32_t bI = __ballot_sync(FULL, inI), bJ = __ballot_sync(FULL, inJ);
+                if (lane == 0) {
+                    s_mask[0][wid][it] = bI;
+                    s_mask[1][wid][it] = bJ;
+                }
+                cI += __popc(bI);
+                cJ += __popc(bJ);
+            }
             if (lane == 0) {
-                s_ce = arc_cost(I, ent, big);
-                const int32_t pj = T.ps[j];
-                int32_t u = i, la = 0;
-                for (;;) {
-                    if (u < 0 || la >= n) {  // no ancestor found within n steps: corrupt tree
-                        la = -1;
-                        break;
-                    }
-                    int32_t pu = T.ps[u];
-                    if (pu <= pj && pj < pu + (int32_t)T.sz[u]) break;
-                    if (la < NS_LMAX) pa[la] = u; else gpa[la] = u;
-                    la++;
-                    u = T.parent(u);
+                s_cnt[0][wid] = cI;
+                s_cnt[1][wid] = cJ;
+            }
+            __syncthreads();
+            const int32_t mI = s_cnt[0][lane], mJ = s_cnt[1][lane];
+            int32_t oI = __reduce_add_sync(FULL, lane < wid ? mI : 0);
+            int32_t oJ = __reduce_add_sync(FULL, lane < wid ? mJ : 0);
+            const int32_t la = __reduce_add_sync(FULL, mI), lb = __reduce_add_sync(FULL, mJ);
+            const uint32_t below = (1u << lane) - 1u;
+            for (int32_t it = 0; it < iters; it++) {
+                const uint32_t bI = s_mask[0][wid][it], bJ = s_mask[1][wid][it];
+                const int32_t x = x0 + (it << 5) + lane;
+                if ((bI >> lane) & 1u) {
+                    const int32_t t = la - 1 - (oI + __popc(bI & below));
+                    const int32_t v = T.od[x];
+                    if (t < NS_LMAX) pa[t] = v; else gpa[t] = v;
                 }
+                if ((bJ >> lane) & 1u) {
+                    const int32_t t = lb - 1 - (oJ + __popc(bJ & below));
+                    const int32_t v = T.od[x];
+                    if (t < NS_LMAX) pb[t] = v; else gpb[t] = v;
+                }
+                oI += __popc(bI);
+                oJ += __popc(bJ);
+            }
+            if (tid == 0) {
                 s_la = la;
-            } else if (lane == 1) {
-                const int32_t pi_ = T.ps[i];
-                int32_t v = j, lb = 0;
-                for (;;) {
-                    if (v < 0 || lb >= n) {  // no ancestor found within n steps: corrupt tree
-                        lb = -1;
-                        break;
-                    }
-                    int32_t pv = T.ps[v];
-                    if (pv <= pi_ && pi_ < pv + (int32_t)T.sz[v]) break;
-                    if (lb < NS_LMAX) pb[lb] = v; else gpb[lb] = v;
-                    lb++;
-                    v = T.parent(v);
-                }
                 s_lb = lb;
             }
+            __syncthreads();
+        } else if (wid == 0) {
+            // large trees (global memory): lanes 0 and 1 walk up from i and j
+            // until they reach an ancestor of the other end
+            if (lane < 2) {
+                int32_t u = lane == 0 ? i : j;
+                const int32_t tgt = lane == 0 ? (int32_t)T.ps[j] : (int32_t)T.ps[i];
+                int32_t* sp = lane == 0 ? pa : pb;
+                int32_t* gp = lane == 0 ? gpa : gpb;
+                int32_t len = 0;
+                for (;;) {
+                    if (u < 0 || len >= n) {  // no ancestor found within n steps: corrupt tree
+                        len = -1;
+                        break;
+                    }
+                    const int32_t pu = T.ps[u];
+                    if (pu <= tgt && tgt < pu + (int32_t)T.sz[u]) break;
+                    if (len < NS_LMAX) sp[len] = u; else gp[len] = u;
+                    len++;
+                    u = T.parent(u);
+                }
+                if (lane == 0) s_la = len; else s_lb = len;
+            }
             __syncwarp();
+        }
+
+        // ---- pivot (one warp): leaving arc, flow change, re-rooting ----------
+        if (wid == 0) {
             const int32_t la = s_la, lb = s_lb;
 #define PA(t) ((t) < NS_LMAX ? pa[t] : gpa[t])
 #define PB(t) ((t) < NS_LMAX ? pb[t] : gpb[t])
@@ -301,14 +349,14 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T, int64
                 }
             }
             for (int off = 16; off > 0; off >>= 1) {
-                int32_t of = __shfl_xor_sync(0xffffffffu, fi, off);
-                int32_t ot = __shfl_xor_sync(0xffffffffu, ti, off);
+                int32_t of = __shfl_xor_sync(FULL, fi, off);
+                int32_t ot = __shfl_xor_sync(FULL, ti, off);
                 if (of < fi || (of == fi && ot < ti)) {
                     fi = of;
                     ti = ot;
                 }
-                of = __shfl_xor_sync(0xffffffffu, fj, off);
-                ot = __shfl_xor_sync(0xffffffffu, tj, off);
+                of = __shfl_xor_sync(FULL, fj, off);
+                ot = __shfl_xor_sync(FULL, tj, off);
                 if (of < fj || (of == fj && ot > tj)) {
                     fj = of;
                     tj = ot;
@@ -367,7 +415,8 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T, int64
                 const int32_t k = tl;  // path q = v0 .. vk = leave
 #define PV(t) (side == 1 ? PA(t) : PB(t))
                 if (lane == 0) {
-                    int64_t rc = s_ce - T.pi[i] + T.pi[j];
+                    // potentials of the cut subtree shift so that the entering
+                    // arc gets reduced cost 0
                     s_dpi = side == 1 ? rc : -rc;
                     s_L0 = T.ps[leave];
                     s_pr = T.ps[r];
@@ -402,13 +451,13 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T, int64
                     }
                     int32_t incl = L;
                     for (int off = 1; off < 32; off <<= 1) {
-                        int32_t o = __shfl_up_sync(0xffffffffu, incl, off);
+                        int32_t o = __shfl_up_sync(FULL, incl, off);
                         if (lane >= off) incl += o;
                     }
                     const int32_t excl = incl - L;  // output offset of A_t
-                    const int32_t ppred = __shfl_up_sync(0xffffffffu, opred, 1);
-                    const int32_t pflow = __shfl_up_sync(0xffffffffu, oflow, 1);
-                    const int32_t pup = __shfl_up_sync(0xffffffffu, oup, 1);
+                    const int32_t ppred = __shfl_up_sync(FULL, opred, 1);
+                    const int32_t pflow = __shfl_up_sync(FULL, oflow, 1);
+                    const int32_t pup = __shfl_up_sync(FULL, oup, 1);
                     __syncwarp();
                     if (on) {
                         if (lane == 0) {
@@ -479,7 +528,12 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T, int64
                     for (int32_t t = 1; t <= k; t++) T.sz[PV(t)] = (IX)(S - I.tmp[t]);
                 }
 #undef PV
-                if (lane == 0) s_go = 1;
+                if (lane == 0) {
+                    // wall-clock limit, checked every 128 pivots: stop after this pivot
+                    const bool late = (pivots & 127) == 0 && ns_now() - t0 > I.time_limit_ns;
+                    s_go = late ? 0 : 1;
+                    if (late) s_status = 2;
+                }
             }
 #undef PA
 #undef PB
@@ -491,9 +545,7 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T, int64
             const int32_t L0 = s_L0, S = s_S, pr = s_pr, nseg = s_nseg;
             const int64_t dpi = s_dpi;
             const int32_t* sst = s_segsm ? sseg[0] : I.seg;
-            const int32_t* sln = s_segsm ? sseg[1] : I.seg + SEGN;
             const int32_t* sot = s_segsm ? sseg[2] : I.seg + 2 * SEGN;
-            (void)sln;
             int32_t lo, hi, ins;  // ins: first index of the new segment in the new order
             if (pr < L0) {
                 lo = pr + 1;
@@ -521,6 +573,9 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T, int64
                 }
                 return pr < L0 ? (int32_t)T.od[x - S] : (int32_t)T.od[x + S];
             };
+            // new order of [lo, hi) computed from the old one, then written; the
+            // next pricing reads only potentials (final before the barrier), and
+            // every later reader of the order passes a pricing barrier first
             if constexpr (sizeof(IX) == 2) {
                 int32_t vals[NS_REGS];
 #pragma unroll
@@ -546,7 +601,6 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T, int64
                     T.ps[node] = (IX)x;
                 }
             }
-            __syncthreads();
         }
     }
     // ---- result: node arrays back to the global record ---------------------
@@ -588,7 +642,7 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T, int64
     }
 }
 
-__global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_t big) {
+__global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts) {
     NSInst& G = insts[blockIdx.x];
     NSInst I = G;
     const int32_t N1 = I.n + 1;
@@ -609,7 +663,7 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
         T.ps = (uint16_t*)p;
         p += sizeof(uint16_t) * N1;
         T.od = (uint16_t*)p;
-        ns_body<uint16_t>(G, I, T, big);
+        ns_body<uint16_t>(G, I, T);
     } else {
         Tree<int32_t> T;
         T.pi = I.pi;
@@ -619,7 +673,7 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, int64_
         T.sz = I.size;
         T.ps = I.pos;
         T.od = I.ord;
-        ns_body<int32_t>(G, I, T, big);
+        ns_body<int32_t>(G, I, T);
     }
 }
 
@@ -657,14 +711,15 @@ __global__ void k_abs_sum(const int64_t* __restrict__ s, int64_t n, unsigned lon
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
 }
 
-// Network simplex on an arc list (one CTA).  cmax = largest arc cost.
-pd_status ns_solve_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS, int64_t nT, const int32_t* cmat,
-                        const int32_t* tail, const int32_t* head, const int32_t* cost, const int64_t* supply,
-                        int64_t cmax, const pd_opts& o, NSOut* out, cudaStream_t st) {
-    *out = NSOut{};
+// One network simplex instance on an arc list, ready to launch (buffers of
+// this context; nothing is launched).  cmax = largest arc cost.
+pd_status ns_prepare_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS, int64_t nT, const int32_t* cmat,
+                          const int32_t* tail, const int32_t* head, const int32_t* cost, const int64_t* supply,
+                          int64_t cmax, const pd_opts& o, NSPrep* p, cudaStream_t st) {
+    *p = NSPrep{};
     if (n <= 0) return PD_OK;
     int64_t N1 = (int64_t)n + 1;
-    NSInst h{};
+    NSInst& h = p->h;
     h.n = n;
     h.m = m;
     h.mst = mst;
@@ -687,9 +742,8 @@ pd_status ns_solve_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS, i
     h.tmp = bufT<int32_t>(c, B_NS_TMP, N1);
     h.path = bufT<int32_t>(c, B_NS_PATH, 2 * N1);
     h.seg = bufT<int32_t>(c, B_NS_SEG, 3 * (2 * N1 + 3));
-    NSInst* d = bufT<NSInst>(c, B_NS_INST, 1);
-    if (!h.pi || !h.parent || !h.pred || !h.flow || !h.up || !h.ord || !h.pos || !h.size || !h.tmp ||
-        !h.path || !h.seg || !d)
+    if (!h.pi || !h.parent || !h.pred || !h.flow || !h.up || !h.ord || !h.pos || !h.size || !h.tmp || !h.path ||
+        !h.seg)
         return PD_ENOMEM;
     int64_t M = m + n;
     if (M >= (int64_t(1) << 31) - 1) return fail(c, PD_ECAPACITY, "network simplex needs fewer than 2^31 arcs");
@@ -713,39 +767,59 @@ pd_status ns_solve_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS, i
     }
     // big-M: more than any path cost; |potentials| stay below ~3 big
     if (cmax > (INT64_MAX / 8) / N1) return fail(c, PD_EOVERFLOW, "network simplex big-M would overflow");
-    int64_t big = N1 * (cmax + 1) + 1;
-    size_t smem = ns_smem_bytes(N1);
+    h.big = N1 * (cmax + 1) + 1;
     int max_optin = 0;
     PD_TRY_CUDA(c, cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     h.smem_nodes = (o.ns_smem != 0 && ns_smem_fits(N1, max_optin)) ? 1 : 0;
-    if (!h.smem_nodes) smem = 0;
+    p->smem = h.smem_nodes ? ns_smem_bytes(N1) : 0;
+    p->ready = true;
+    return PD_OK;
+}
+
+pd_status ns_run(Ctx* c, const NSInst* h, int count, size_t smem, NSInst* d, NSInst* r, cudaStream_t st) {
+    if (count <= 0) return PD_OK;
     PD_TRY_CUDA(c, cudaFuncSetAttribute(k_netsimplex, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PD_TRY_CUDA(c, cudaMemcpyAsync(d, &h, sizeof(NSInst), cudaMemcpyHostToDevice, st));
+    PD_TRY_CUDA(c, cudaMemcpyAsync(d, h, sizeof(NSInst) * count, cudaMemcpyHostToDevice, st));
     cudaEvent_t e0, e1;
     PD_TRY_CUDA(c, cudaEventCreate(&e0));
     PD_TRY_CUDA(c, cudaEventCreate(&e1));
     PD_TRY_CUDA(c, cudaEventRecord(e0, st));
-    k_netsimplex<<<1, NS_THREADS, smem, st>>>(d, big); pd::count_launch();
-    PD_TRY_CUDA(c, cudaGetLastError());
-    PD_TRY_CUDA(c, cudaEventRecord(e1, st));
-    NSInst r;
-    PD_TRY_CUDA(c, cudaMemcpyAsync(&r, d, sizeof(NSInst), cudaMemcpyDeviceToHost, st));
-    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    k_netsimplex<<<count, NS_THREADS, smem, st>>>(d); pd::count_launch();
+    cudaError_t le = cudaGetLastError();
+    cudaEventRecord(e1, st);
+    if (le == cudaSuccess) le = cudaMemcpyAsync(r, d, sizeof(NSInst) * count, cudaMemcpyDeviceToHost, st);
+    if (le == cudaSuccess) le = cudaStreamSynchronize(st);
     float nms = 0.f;
-    cudaEventElapsedTime(&nms, e0, e1);
-    c->last_ns_ms += nms;
+    if (le == cudaSuccess) cudaEventElapsedTime(&nms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    out->opt = r.opt;
-    out->pivots = r.pivots;
-    out->degenerate = r.degenerate;
-    out->scanned = r.scanned;
-    out->status = r.status;
+    if (le != cudaSuccess) return cuda_fail(c, le, "k_netsimplex");
+    c->last_ns_ms += nms;
+    return PD_OK;
+}
+
+pd_status ns_status(Ctx* c, const NSInst& r) {
     if (r.status == 2) return fail(c, PD_ETIMEOUT, "network simplex pivot cap or time limit reached");
     if (r.status == 1) return fail(c, PD_EINFEASIBLE, "network has no feasible flow");
     if (r.status == 3) return fail(c, PD_EINFEASIBLE, "network simplex found an unbounded cycle");
     if (r.status != 0) return fail(c, PD_ECUDA, "network simplex failed");
     return PD_OK;
+}
+
+// Network simplex on an arc list (one CTA), result in this context's
+// instance record.
+static pd_status ns_solve_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS, int64_t nT,
+                               const int32_t* cmat, const int32_t* tail, const int32_t* head, const int32_t* cost,
+                               const int64_t* supply, int64_t cmax, const pd_opts& o, NSInst* out,
+                               cudaStream_t st) {
+    *out = NSInst{};
+    NSPrep p;
+    PD_TRY(ns_prepare_arcs(c, n, m, mst, nS, nT, cmat, tail, head, cost, supply, cmax, o, &p, st));
+    if (!p.ready) return PD_OK;
+    NSInst* d = bufT<NSInst>(c, B_NS_INST, 1);
+    if (!d) return PD_ENOMEM;
+    PD_TRY(ns_run(c, &p.h, 1, p.smem, d, out, st));
+    return ns_status(c, *out);
 }
 
 // ---------------------------------------------------------------------------
@@ -884,7 +958,7 @@ pd_status ns_solve_network(Ctx* c, const pd_network& net, const pd_opts& o, Solv
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     if (c->h_small[0]) return fail(c, PD_EOVERFLOW, "arc cost outside [0, 2^31)");
     int64_t cmax = c->h_small[1];
-    NSOut r;
+    NSInst r;
     PD_TRY(ns_solve_arcs(c, (int32_t)n, m, 0, 0, 1, nullptr, tail, net.head, c32, net.supply, cmax, o, &r, st));
     PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, sizeof(unsigned long long), st));
     k_tree_flow<<<grid_for(n, 256), 256, 0, st>>>(bufT<NSInst>(c, B_NS_INST, 1), sm); pd::count_launch();
@@ -900,14 +974,15 @@ pd_status ns_solve_network(Ctx* c, const pd_network& net, const pd_opts& o, Solv
     return PD_OK;
 }
 
-// The W1 network: try the transportation form with the certificate first
-// when it is not much larger than the sparse network, else (or if the
-// certificate fails) run the simplex on the sparse network itself.
-pd_status ns_solve_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const pd_network& merged,
-                      const pd_opts& o, SolveStats* out, cudaStream_t st) {
-    *out = SolveStats{};
+// The W1 network: the transportation form is tried first when it is not
+// much larger than the sparse network (prepared here, launched by the caller,
+// checked by ns_finish_w1); otherwise, or if its certificate fails, the
+// simplex runs on the sparse network itself.
+pd_status ns_prepare_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const pd_network& merged,
+                        const pd_opts& o, W1Prep* w, cudaStream_t st) {
+    *w = W1Prep{};
     int64_t N = nodes.n_nodes;
-    if (N == 0) return ns_solve_network(c, merged, o, out, st);
+    if (N == 0 || o.ns_transport == 0) return PD_OK;
     int64_t* fs = bufT<int64_t>(c, B_WSFLAG, N);
     int64_t* ft = bufT<int64_t>(c, B_WSOFF, N);
     unsigned long long* sm = bufT<unsigned long long>(c, B_SMALL, 64);
@@ -924,58 +999,87 @@ pd_status ns_solve_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     int64_t mst = nS * nT;
     int64_t mt = mst + (dsup < 0 ? nS : (dsup > 0 ? nT : 0));
-    bool try_transport = o.ns_transport != 0 && mt <= 2 * ws.n_arcs + 4096 && mt < (int64_t(1) << 31);
-    if (try_transport) {
-        int64_t nt = nS + nT + 1;
-        int32_t* S = bufT<int32_t>(c, B_TR_S, nS);
-        int32_t* T = bufT<int32_t>(c, B_TR_T, nT);
-        int64_t* sup = bufT<int64_t>(c, B_TR_SUP, nt);
-        int64_t mx = mt - mst;
-        int32_t* cmat = bufT<int32_t>(c, B_NS_COST, mst);
-        int32_t* tail = bufT<int32_t>(c, B_S_TAIL, mx);
-        int32_t* head = bufT<int32_t>(c, B_S_HEAD, mx);
-        int32_t* cost = bufT<int32_t>(c, B_TR_XCOST, mx);
-        if (!S || !T || !sup || !tail || !head || !cost || !cmat) return PD_ENOMEM;
-        k_side_lists<<<grid_for(N, 256), 256, 0, st>>>(nodes.cntA, nodes.cntB, N, fs, ft, S, T, sup, nS); pd::count_launch();
-        PD_TRY_CUDA(c, cudaMemcpyAsync(sup + nS + nT, &dsup, sizeof(int64_t), cudaMemcpyHostToDevice, st));
-        PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, 8 * sizeof(unsigned long long), st));
-        if (mt > 0)
-            k_transport_arcs<<<grid_for(mt, 256), 256, 0, st>>>(S, T, nS, nT, dsup < 0 ? -1 : (dsup > 0 ? 1 : 0),
-                                                                  nodes.X, nodes.Y, cmat, tail, head, cost, sm); pd::count_launch();
+    if (!(mt <= 2 * ws.n_arcs + 4096 && mt < (int64_t(1) << 31))) return PD_OK;
+    int64_t nt = nS + nT + 1;
+    int32_t* S = bufT<int32_t>(c, B_TR_S, nS);
+    int32_t* T = bufT<int32_t>(c, B_TR_T, nT);
+    int64_t* sup = bufT<int64_t>(c, B_TR_SUP, nt);
+    int64_t mx = mt - mst;
+    int32_t* cmat = bufT<int32_t>(c, B_NS_COST, mst);
+    int32_t* tail = bufT<int32_t>(c, B_S_TAIL, mx);
+    int32_t* head = bufT<int32_t>(c, B_S_HEAD, mx);
+    int32_t* cost = bufT<int32_t>(c, B_TR_XCOST, mx);
+    if (!S || !T || !sup || !tail || !head || !cost || !cmat) return PD_ENOMEM;
+    k_side_lists<<<grid_for(N, 256), 256, 0, st>>>(nodes.cntA, nodes.cntB, N, fs, ft, S, T, sup, nS); pd::count_launch();
+    PD_TRY_CUDA(c, cudaMemcpyAsync(sup + nS + nT, &dsup, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, 8 * sizeof(unsigned long long), st));
+    if (mt > 0)
+        k_transport_arcs<<<grid_for(mt, 256), 256, 0, st>>>(S, T, nS, nT, dsup < 0 ? -1 : (dsup > 0 ? 1 : 0),
+                                                              nodes.X, nodes.Y, cmat, tail, head, cost, sm); pd::count_launch();
+    PD_TRY_CUDA(c, cudaGetLastError());
+    if (mst > 0) k_max_cost32<<<grid_for(mst, 256), 256, 0, st>>>(cmat, mst, sm + 1); pd::count_launch();
+    if (mx > 0) k_max_cost32<<<grid_for(mx, 256), 256, 0, st>>>(cost, mx, sm + 1); pd::count_launch();
+    PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    if (c->h_small[0] != 0) return PD_OK;  // a cost does not fit in int32: solve the sparse network
+    PD_TRY(ns_prepare_arcs(c, (int32_t)nt, mt, mst, nS, nT, cmat, tail, head, cost, sup, c->h_small[1], o, &w->ns,
+                           st));
+    w->S = S;
+    w->T = T;
+    w->nS = nS;
+    w->nT = nT;
+    w->nt = nt;
+    return PD_OK;
+}
+
+pd_status ns_finish_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const pd_network* merged,
+                       const pd_opts& o, const W1Prep& w, const NSInst* d_res, const NSInst& r, SolveStats* out,
+                       cudaStream_t st) {
+    *out = SolveStats{};
+    if (w.ns.ready) {
+        PD_TRY(ns_status(c, r));
+        unsigned long long* sm = bufT<unsigned long long>(c, B_SMALL, 64);
+        if (!sm) return PD_ENOMEM;
+        PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, 4 * sizeof(unsigned long long), st));
+        k_certify_transport<<<grid_for(w.nt, 256), 256, 0, st>>>(d_res, w.S, w.T, w.nS, w.nT, nodes.X, nodes.Y,
+                                                                  ws.row_ptr, ws.head, sm); pd::count_launch();
         PD_TRY_CUDA(c, cudaGetLastError());
-        if (mst > 0) k_max_cost32<<<grid_for(mst, 256), 256, 0, st>>>(cmat, mst, sm + 1); pd::count_launch();
-        if (mx > 0) k_max_cost32<<<grid_for(mx, 256), 256, 0, st>>>(cost, mx, sm + 1); pd::count_launch();
         PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+        out->pivots = r.pivots;
+        out->degenerate = r.degenerate;
+        out->scanned = r.scanned;
         if (c->h_small[0] == 0) {
-            NSOut r;
-            PD_TRY(ns_solve_arcs(c, (int32_t)nt, mt, mst, nS, nT, cmat, tail, head, cost, sup, c->h_small[1], o, &r,
-                                 st));
-            PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, 4 * sizeof(unsigned long long), st));
-            k_certify_transport<<<grid_for(nt, 256), 256, 0, st>>>(bufT<NSInst>(c, B_NS_INST, 1), S, T, nS, nT,
-                                                                    nodes.X, nodes.Y, ws.row_ptr, ws.head, sm); pd::count_launch();
-            PD_TRY_CUDA(c, cudaGetLastError());
-            PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-            PD_TRY_CUDA(c, cudaStreamSynchronize(st));
-            out->pivots = r.pivots;
-            out->degenerate = r.degenerate;
-            out->scanned = r.scanned;
-            if (c->h_small[0] == 0) {
-                out->opt = r.opt;
-                out->slack = c->h_small[1];
-                out->verified = 1;
-                out->method = 2;
-                return PD_OK;
-            }
-            out->cert_failures = c->h_small[0];
+            out->opt = r.opt;
+            out->slack = c->h_small[1];
+            out->verified = 1;
+            out->method = 2;
+            return PD_OK;
         }
+        out->cert_failures = c->h_small[0];
     }
-    int64_t piv = out->pivots, fails = out->cert_failures, scn = out->scanned;
-    PD_TRY(ns_solve_network(c, merged, o, out, st));
+    if (!merged) {  // the caller solves the sparse network
+        out->method = -1;
+        return PD_OK;
+    }
+    int64_t piv = out->pivots, fails = out->cert_failures, scn = out->scanned, deg = out->degenerate;
+    PD_TRY(ns_solve_network(c, *merged, o, out, st));
     out->pivots += piv;
     out->scanned += scn;
+    out->degenerate += deg;
     out->cert_failures = fails;
     return PD_OK;
+}
+
+pd_status ns_solve_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const pd_network& merged,
+                      const pd_opts& o, SolveStats* out, cudaStream_t st) {
+    W1Prep w;
+    PD_TRY(ns_prepare_w1(c, nodes, ws, merged, o, &w, st));
+    NSInst r{};
+    NSInst* d = bufT<NSInst>(c, B_NS_INST, 1);
+    if (!d) return PD_ENOMEM;
+    if (w.ns.ready) PD_TRY(ns_run(c, &w.ns.h, 1, w.ns.smem, d, &r, st));
+    return ns_finish_w1(c, nodes, ws, &merged, o, w, d, r, out, st);
 }
 
 }  // namespace pd

@@ -3,6 +3,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "internal.h"
+
 namespace pd {
 
 constexpr int NS_THREADS = 1024;
@@ -32,6 +34,7 @@ struct NSInst {
     int32_t* path;     // 2 (n + 1) scratch: the two half-cycles past the shared-memory part
     int32_t* seg;      // 3 * (2n + 3) scratch: segment start, length, output offset
     int64_t block;     // pricing block (arcs)
+    int64_t big;       // cost of the artificial arcs (more than any path cost)
     int32_t smem_nodes; // 1: hot node arrays live in shared memory
     int32_t vec_explicit; // 1: tail, head and cost are 16-byte aligned (vector loads)
     int64_t scanned;   // result: arcs priced
@@ -45,7 +48,8 @@ struct NSInst {
     int32_t pad;
 };
 
-__global__ void k_netsimplex(NSInst* insts, int64_t big);
+// One CTA per instance record; results are written back into the records.
+__global__ void k_netsimplex(NSInst* insts);
 size_t ns_smem_bytes(int64_t N1);
 // True if the compact node arrays of N1 nodes fit in shared memory beside the
 // kernel's static shared memory (max_optin: the device's opt-in limit per CTA).
@@ -55,5 +59,37 @@ __global__ void k_i64_to_i32_cost(const int64_t* __restrict__ c, int64_t m, int3
 __global__ void k_abs_sum(const int64_t* __restrict__ s, int64_t n, unsigned long long* __restrict__ out);
 __global__ void k_check_network(const int64_t* __restrict__ rp, const int32_t* __restrict__ hd, int64_t n, int64_t m,
                                 unsigned long long* __restrict__ bad);
+
+// An instance ready to launch (buffers of the context that prepared it).
+struct NSPrep {
+    NSInst h{};
+    size_t smem = 0;     // dynamic shared memory it needs
+    bool ready = false;  // false: nothing to solve
+};
+
+// The transportation form of one W1 network, prepared for the simplex.
+struct W1Prep {
+    NSPrep ns;           // ns.ready false: solve the sparse network instead
+    const int32_t* S = nullptr;
+    const int32_t* T = nullptr;
+    int64_t nS = 0, nT = 0, nt = 0;
+};
+
+pd_status ns_prepare_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS, int64_t nT, const int32_t* cmat,
+                          const int32_t* tail, const int32_t* head, const int32_t* cost, const int64_t* supply,
+                          int64_t cmax, const pd_opts& o, NSPrep* p, cudaStream_t st);
+// Runs `count` prepared instances in one launch (one CTA each): h -> device
+// records d -> results r (host), synchronising the stream; smem = the largest
+// dynamic shared memory of the instances.
+pd_status ns_run(Ctx* c, const NSInst* h, int count, size_t smem, NSInst* d, NSInst* r, cudaStream_t st);
+pd_status ns_status(Ctx* c, const NSInst& r);
+pd_status ns_prepare_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const pd_network& merged,
+                        const pd_opts& o, W1Prep* w, cudaStream_t st);
+// Certificate and fallback after the launch; d_res = the device record of the
+// solved instance, r = its host copy.  merged == nullptr: no fallback here --
+// out->method = -1 tells the caller to solve the sparse network itself.
+pd_status ns_finish_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const pd_network* merged,
+                       const pd_opts& o, const W1Prep& w, const NSInst* d_res, const NSInst& r, SolveStats* out,
+                       cudaStream_t st);
 
 }  // namespace pd

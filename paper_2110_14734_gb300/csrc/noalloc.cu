@@ -123,7 +123,6 @@ extern "C" pd_status pd_mcf_solve_noalloc(const pd_network* net, int64_t* opt_ou
     const int64_t N1 = n + 1;
     const int64_t cmax = (int64_t)hf[2];
     if (cmax > (INT64_MAX / 8) / N1) return PD_EOVERFLOW;
-    const int64_t big = N1 * (cmax + 1) + 1;
 
     NSInst h{};
     h.n = (int32_t)n;
@@ -136,6 +135,7 @@ extern "C" pd_status pd_mcf_solve_noalloc(const pd_network* net, int64_t* opt_ou
     h.head = net->head;
     h.cost = c32;
     h.supply = net->supply;
+    h.big = N1 * (cmax + 1) + 1;
     h.vec_explicit = ((((uintptr_t)tail) | ((uintptr_t)net->head) | ((uintptr_t)c32)) & 15) == 0 ? 1 : 0;
     h.pi = (int64_t*)(base + OFF_PI);
     h.pred = (int32_t*)(base + OFF_PRED);
@@ -162,7 +162,7 @@ extern "C" pd_status pd_mcf_solve_noalloc(const pd_network* net, int64_t* opt_ou
     if (!h.smem_nodes) smem = 0;
     NA_TRY(cudaFuncSetAttribute(k_netsimplex, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     NA_TRY(cudaMemcpyAsync(dinst, &h, sizeof(NSInst), cudaMemcpyHostToDevice, st));
-    k_netsimplex<<<1, NS_THREADS, smem, st>>>(dinst, big); pd::count_launch();
+    k_netsimplex<<<1, NS_THREADS, smem, st>>>(dinst); pd::count_launch();
     NA_TRY(cudaGetLastError());
     NSInst r;
     NA_TRY(cudaMemcpyAsync(&r, dinst, sizeof(NSInst), cudaMemcpyDeviceToHost, st));

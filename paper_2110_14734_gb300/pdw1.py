@@ -35,7 +35,8 @@ class pd_opts(C.Structure):
                 ("perturb", C.c_int32), ("seed", C.c_uint64), ("alpha", C.c_int32), ("verify", C.c_int32),
                 ("max_rounds", C.c_int64), ("time_limit_ms", C.c_int64), ("update_every", C.c_int64),
                 ("seq_threshold", C.c_int32), ("solver", C.c_int32), ("ns_block", C.c_int64),
-                ("ns_transport", C.c_int32), ("ns_smem", C.c_int32)]
+                ("ns_transport", C.c_int32), ("ns_smem", C.c_int32), ("batch_slots", C.c_int32),
+                ("batch_threads", C.c_int32)]
 
 
 class pd_nodes(C.Structure):
@@ -89,6 +90,9 @@ _lib.pd_mcf_solve.argtypes = [C.c_void_p, C.POINTER(pd_network), C.POINTER(pd_op
 _lib.pd_w1_approx.restype = C.c_int
 _lib.pd_w1_approx.argtypes = [C.c_void_p, pd_diagram, pd_diagram, C.c_double, C.POINTER(pd_opts),
                               C.POINTER(pd_result), C.c_void_p]
+_lib.pd_w1_approx_batch.restype = C.c_int
+_lib.pd_w1_approx_batch.argtypes = [C.c_void_p, C.POINTER(pd_diagram), C.POINTER(pd_diagram), C.c_int64,
+                                    C.c_double, C.POINTER(pd_opts), C.POINTER(pd_result), C.c_void_p]
 
 _lib.pd_mcf_solve_noalloc.restype = C.c_int
 _lib.pd_mcf_solve_noalloc.argtypes = [C.POINTER(pd_network), C.POINTER(C.c_int64), C.c_void_p]
@@ -255,6 +259,29 @@ def pd_w1_approx(ctx: Context, A, B, eps: float, o: pd_opts | None = None, strea
     ctx.check(_lib.pd_w1_approx(ctx.ptr, da, db, float(eps), C.byref(o) if o else None, C.byref(res),
                                 C.c_void_p(_stream(stream))))
     return res.to_dict()
+
+
+def pd_w1_approx_batch(ctx: Context, As, Bs, eps: float, o: pd_opts | None = None, stream=None) -> list:
+    """W1 of the pairs (As[i], Bs[i]); one dict per pair, as pd_w1_approx."""
+    if len(As) != len(Bs):
+        raise ValueError("As and Bs differ in length")
+    n = len(As)
+    da = (pd_diagram * max(n, 1))()
+    db = (pd_diagram * max(n, 1))()
+    keep = []
+    for i in range(n):
+        da[i], ka = diagram(As[i])
+        db[i], kb = diagram(Bs[i])
+        keep += [ka, kb]
+    res = (pd_result * max(n, 1))()
+    ctx.check(_lib.pd_w1_approx_batch(ctx.ptr, da, db, n, float(eps), C.byref(o) if o else None, res,
+                                      C.c_void_p(_stream(stream))))
+    return [res[i].to_dict() for i in range(n)]
+
+
+def pd_w1_approx_batch_raw(ctx: Context, da, db, n: int, eps: float, o, res, stream: int):
+    """Allocation-free batched call for timing loops: prebuilt ctypes arrays."""
+    return _lib.pd_w1_approx_batch(ctx.ptr, da, db, n, eps, C.byref(o) if o else None, res, C.c_void_p(stream))
 
 
 def pd_w1_approx_raw(ctx: Context, da: pd_diagram, db: pd_diagram, eps: float, o, res: pd_result, stream: int):
