@@ -1,9 +1,13 @@
 #!/usr/bin/env python3
-"""Benchmark: approximate W1 between two persistence diagrams of 100,000 uint8
+"""Benchmark: approximate W1 between persistence diagrams of 100,000 uint8
 lower-star points each (eps = 0.05, WSPD parameter s = 327), in pairs/s.
 
-One step = one pd_w1_approx call on one pair: quantise, 0-condense, RWMD,
-delta-condense, radix tree, WSPD, diagonal arcs, CSR, exact min-cost flow.
+One step = one pd_w1_approx_batch call over a batch of distinct pairs (by
+default twice as many pairs as the GPU has SMs): per pair quantise,
+0-condense, RWMD, delta-condense, radix tree, WSPD (arcs counted), diagonal
+arcs, transportation instance; one persistent network simplex launch for the
+whole batch; per pair the optimality certificate against the WSPD.  The plain one-pair path
+(pd_w1_approx, one pair after the other) is timed beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -32,13 +36,16 @@ SAMPLE_N = 10000  # points per diagram of the CPU-oracle sample
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=100000)
     ap.add_argument("--eps", type=float, default=0.05)
-    ap.add_argument("--pool", type=int, default=6, help="distinct seeded pairs cycled over the steps")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=0, help="pairs per step (0 = twice the number of SMs)")
+    ap.add_argument("--diagrams", type=int, default=26, help="seeded diagrams; steps cycle over their pairs")
+    ap.add_argument("--plain-pairs", type=int, default=3, help="pairs timed through the one-pair path")
+    ap.add_argument("--threads", type=int, default=0, help="host threads preprocessing pairs (0 = library default)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -181,55 +188,66 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def _gen(args):
+    from paper_2110_14734_gb300 import synth
+    return synth.lowerstar_u8(*args)
+
+
 def run_ours(args):
     import ctypes as C
-
-    import numpy as np
-    import torch
+    import multiprocessing as mp
 
     ws, rank, local = dist_env()
+    # seeded diagrams, generated in spawned processes before any GPU work
+    seeds = [1000 + 1000 * rank + i for i in range(max(2, args.diagrams))]
+    from paper_2110_14734_gb300 import synth
+    synth.build_helper()
+    with mp.get_context("spawn").Pool(min(len(seeds), os.cpu_count() or 1)) as pool:
+        diags = pool.map(_gen, [(args.n, sd) for sd in seeds])
+    pairs_all = [(i, j) for i in range(len(diags)) for j in range(i + 1, len(diags))]
+
+    import torch
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_2110_14734_gb300 import build
     build.build()
-    from paper_2110_14734_gb300 import pdw1, synth
+    from paper_2110_14734_gb300 import pdw1
 
     dev = torch.device("cuda", local)
     ctx = pdw1.pd_create(local)
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
-    opts = pdw1.opts()
-
-    # seeded pairs, resident in HBM before the timed region
-    pool = []
-    for i in range(max(1, min(args.pool, args.warmup + args.steps))):
-        sa, sb = synth.pair_seeds(i + 1000 * rank)
-        A = synth.lowerstar_u8(args.n, sa)
-        B = synth.lowerstar_u8(args.n, sb)
-        pool.append((A, B, torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)))
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    P = args.batch if args.batch > 0 else 2 * nsm
+    P = min(P, len(pairs_all))
+    opts = pdw1.opts(batch_slots=P, batch_threads=args.threads)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
-    def diag(t):
-        d, _ = pdw1.diagram(t)
-        return d
+    dev_t = [torch.from_numpy(d).to(dev) for d in diags]  # resident in HBM before timing
+    host_t = [torch.from_numpy(d).pin_memory() for d in diags]
+    dev_d = [pdw1.diagram(t)[0] for t in dev_t]
+    host_d = [pdw1.diagram(t)[0] for t in host_t]
 
-    res = pdw1.pd_result()
+    def batch_arrays(k, host=False):
+        sel = [pairs_all[(k * P + q) % len(pairs_all)] for q in range(P)]
+        src = host_d if host else dev_d
+        da = (pdw1.pd_diagram * P)(*[src[i] for i, _ in sel])
+        db = (pdw1.pd_diagram * P)(*[src[j] for _, j in sel])
+        return da, db
 
-    def step(i, host=False):
-        A, B, dA, dB = pool[i % len(pool)]
-        if host:
-            da, db = host_diags[i % len(pool)]
-        else:
-            da, db = diag(dA), diag(dB)
-        st = pdw1.pd_w1_approx_raw(ctx, da, db, args.eps, opts, res, sptr)
+    res = (pdw1.pd_result * P)()
+
+    def step(k, host=False):
+        da, db = batch_arrays(k, host)
+        st = pdw1.pd_w1_approx_batch_raw(ctx, da, db, P, args.eps, opts, res, sptr)
         if st != 0:
             raise pdw1.PDError(st, pdw1._lib.pd_last_error(ctx.ptr).decode())
-        return res.to_dict()
+        return [res[q].to_dict() for q in range(P)]
 
-    for i in range(args.warmup):
-        step(i)
+    for k in range(args.warmup):
+        step(k)
     torch.cuda.synchronize()
 
     # ---- device-resident timed region ------------------------------------
@@ -238,15 +256,17 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    launches0 = pdw1.pd_kernel_launches()
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
-        for i in range(args.steps):
+        for k in range(args.steps):
             flush.zero_()  # L2 flush between timed steps (outside the event pair)
-            ev[i][0].record(stream)
-            results.append(step(args.warmup + i))
-            ev[i][1].record(stream)
+            ev[k][0].record(stream)
+            results.append(step(args.warmup + k))
+            ev[k][1].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
+    launches = pdw1.pd_kernel_launches() - launches0
     if ws > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -255,33 +275,39 @@ def run_ours(args):
         t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tot_ms = float(t.item())
-    pairs = args.steps * ws
+    pairs = args.steps * P * ws
     value = pairs / (tot_ms / 1000.0)
 
+    # ---- the plain one-pair path, one pair after the other ------------------
+    one = pdw1.pd_result()
+    plain_ms = []
+    for q in range(max(1, args.plain_pairs)):
+        i, j = pairs_all[q]
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st = pdw1.pd_w1_approx_raw(ctx, dev_d[i], dev_d[j], args.eps, pdw1.opts(), one, sptr)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if st != 0:
+            raise pdw1.PDError(st, pdw1._lib.pd_last_error(ctx.ptr).decode())
+        plain_ms.append(a.elapsed_time(b))
+
     # ---- end to end through the C ABI with pinned host buffers -------------
-    host_diags = []
-    keep = []
-    for A, B, _, _ in pool:
-        hA = torch.from_numpy(A).pin_memory()
-        hB = torch.from_numpy(B).pin_memory()
-        keep += [hA, hB]
-        host_diags.append((diag(hA), diag(hB)))
     e2e_steps = max(1, min(args.e2e_steps, args.steps))
-    step(0, host=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for i in range(e2e_steps):
-        step(args.warmup + i, host=True)
+    for k in range(e2e_steps):
+        step(args.warmup + k, host=True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    h2d = 2 * args.n * 2
-    d2h = C.sizeof(pdw1.pd_result)
+    h2d = 2 * P * args.n * 2  # two uint8 (b, d) diagrams per pair
+    d2h = P * C.sizeof(pdw1.pd_result)
 
-    # ---- roofline of the dominant kernel (network simplex) ----------------
-    ns_ms = [r["ns_kernel_ms"] for r in results]
-    priced = [r["arcs_priced"] for r in results]
-    launches = sum(r["kernel_launches"] for r in results)
-    avg_ns_ms = statistics.mean(ns_ms)
+    # ---- roofline of the dominant kernel (network simplex, one launch per step)
+    wave_ms = [r[0]["ns_kernel_ms"] for r in results]
+    priced = [sum(x["arcs_priced"] for x in r) for r in results]
+    avg_ns_ms = statistics.mean(wave_ms)
     algo_bytes = 4.0 * statistics.mean(priced)  # one int32 cost streamed per priced arc
     achieved = algo_bytes / (avg_ns_ms / 1000.0) / 1e9
     pk, pk_src = peaks()
@@ -290,24 +316,34 @@ def run_ours(args):
             "algorithmic_bytes_per_launch": algo_bytes, "avg_launch_ms": avg_ns_ms,
             "share_of_step": avg_ns_ms / statistics.mean(step_ms)}
 
-    r0 = results[0]
+    flat = [x for r in results for x in r]
+    r0 = flat[0]
     stage_names = ["condense0", "rwmd", "delta_condense", "tree", "wspd", "csr", "solve", "total"]
-    stages = {k: statistics.mean(r["stage_ms"][i] for r in results) for i, k in enumerate(stage_names)}
+    stages = {k: statistics.mean(x["stage_ms"][i] for x in flat) for i, k in enumerate(stage_names)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak" if ws > 1 else "weak", "vs_baseline": None, "dtype": "int64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic (seeded lower-star uint8 diagrams of Gaussian-smoothed noise images)",
             "config": {"workload": WORKLOAD, "n_points": args.n, "eps": args.eps, "s": r0["s"],
-                       "pairs_in_pool": len(pool), "l2": "flushed between timed steps (256 MiB write)",
+                       "pairs_per_step": P, "diagrams": len(diags), "distinct_pairs": len(pairs_all),
+                       "form": "batched: one persistent simplex launch per step (one CTA per SM, pairs "
+                               "largest first)",
+                       "l2": "flushed between timed steps (256 MiB write); inputs of a step > L2",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "nodes": r0["n_nodes"], "arcs": r0["n_arcs"]},
-            "e2e": {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": e2e_steps},
+                       "nodes_mean": statistics.mean(x["n_nodes"] for x in flat),
+                       "arcs_mean": statistics.mean(x["n_arcs"] for x in flat)},
+            "plain": {"value": 1000.0 / statistics.mean(plain_ms), "unit": UNIT, "pairs": len(plain_ms),
+                      "ms_per_pair": statistics.mean(plain_ms),
+                      "form": "pd_w1_approx, one pair per call, device-resident inputs"},
+            "e2e": {"value": e2e_steps * P / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
             "gpu_launches": launches,
             "roofline": roof,
-            "stage_ms": stages,
-            "solver": {"method": r0["solve_method"], "pivots": statistics.mean(r["pivots"] for r in results),
-                       "arcs_priced": statistics.mean(priced)},
+            "stage_ms_per_pair": stages,
+            "solver": {"method": statistics.mean(x["solve_method"] for x in flat),
+                       "pivots_mean": statistics.mean(x["pivots"] for x in flat),
+                       "pivots_max": max(x["pivots"] for x in flat),
+                       "arcs_priced_per_step": statistics.mean(priced)},
             "wall_s": t_wall}
     if rank == 0:
         line["clocks"] = clk.summary()

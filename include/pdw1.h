@@ -54,6 +54,10 @@ void pd_destroy(pd_ctx* ctx);
 /* Message of the last error on this context ("" after success). */
 const char* pd_last_error(const pd_ctx* ctx);
 
+/* Kernels launched by this library in this process so far, over all contexts
+ * and threads (a utility for measurement; no counterpart in the paper). */
+int64_t pd_kernel_launches(void);
+
 typedef enum { PD_F32 = 0, PD_U8 = 1 } pd_dtype;
 
 /* A persistence diagram: n points stored as interleaved (birth, death) pairs,
@@ -84,8 +88,12 @@ typedef struct {
     int64_t ns_block;       /* network simplex pricing block in arcs (0 = max(8192, sqrt(arcs))) */
     int32_t ns_transport;   /* W1 only: 1 = try the transportation form with its certificate first (default) */
     int32_t ns_smem;        /* network simplex: 1 = hot node arrays in shared memory when they fit (default) */
-    int32_t batch_slots;    /* pd_w1_approx_batch: pairs per simplex launch (0 = number of SMs) */
+    int32_t batch_slots;    /* pairs per simplex launch (pd_w1_approx_batch: 0 = twice the number of SMs;
+                               pd_nn_search: 0 = the number of SMs) */
     int32_t batch_threads;  /* pd_w1_approx_batch: host threads preprocessing pairs (0 = 8) */
+    int32_t nn_prune;       /* pd_nn_search: 1 = skip pairs whose lower bound exceeds the best optimum
+                               (default); 0 = solve every pair */
+    int32_t reserved1;
 } pd_opts;
 
 void pd_opts_default(pd_opts* opts);
@@ -216,10 +224,12 @@ pd_status pd_w1_approx(pd_ctx* ctx, pd_diagram A, pd_diagram B, double eps, cons
  * exactly as pd_w1_approx computes it with the same eps and opts (so
  * out[i].opt_quanta equals what pd_w1_approx returns for that pair).  The
  * paper solves one pair at a time; this batched form has no counterpart
- * there.  Pairs are processed in waves of W = opts->batch_slots (0 = the
- * number of SMs) pairs: the preprocessing of each pair of a wave runs on the
- * stream as in pd_w1_approx, then the network simplex solves of the wave
- * share one launch with one CTA per pair, then each pair's certificate runs.
+ * there.  Pairs are processed in waves of W = opts->batch_slots (0 = twice
+ * the number of SMs) pairs: host worker threads (opts->batch_threads) run the
+ * preprocessing of the wave's pairs, each on its own stream after the work
+ * already queued on `stream`; then the network simplex solves of the wave
+ * share one persistent launch (one CTA per SM takes the pairs, largest
+ * first); then each pair's certificate runs.
  * A and B: host arrays of `count` descriptors; out: host array of `count`
  * results (ns_kernel_ms and stage_ms[6] include the wave's shared launch).
  * Device memory: one buffer set per slot, grown on demand and kept by the
@@ -229,6 +239,49 @@ pd_status pd_w1_approx(pd_ctx* ctx, pd_diagram A, pd_diagram B, double eps, cons
  */
 pd_status pd_w1_approx_batch(pd_ctx* ctx, const pd_diagram* A, const pd_diagram* B, int64_t count,
                              double eps, const pd_opts* opts, pd_result* out, void* stream);
+
+/* Result of pd_nn_search (host). */
+typedef struct {
+    int64_t nn_index;       /* argmin over the database of OPT_int(query, db[i]); ties -> lowest i; -1 if empty */
+    int64_t nn_opt_quanta;  /* OPT_int of that pair (-1 if the database is empty) */
+    double nn_w1;           /* nn_opt_quanta * 2^-coord_shift */
+    int64_t solved;         /* pairs whose W1 was computed */
+    int64_t pruned;         /* pairs skipped: lower bound above the best optimum */
+    int32_t waves;          /* batched solves issued */
+    int32_t coord_shift;    /* k used */
+    float lb_ms;            /* device time of the query's condensation and all lower bounds */
+    float solve_ms;         /* host wall time of the waves */
+    float total_ms;         /* host wall time of the call */
+    int32_t reserved;
+} pd_nn_result;
+
+/*
+ * Database for nearest-neighbour search (the NN-search application of the
+ * experiments section; the batched database form has no counterpart in the
+ * paper).  Records the n_db descriptors -- the caller keeps their memory
+ * valid until the database is rebuilt or the context destroyed -- and
+ * 0-condenses each diagram once (quantum 2^-k, k from opts->coord_shift or the
+ * dtype; all diagrams share one dtype).  Replaces any previous database.
+ */
+pd_status pd_db_build(pd_ctx* ctx, const pd_diagram* dbs, int64_t n_db, const pd_opts* opts, void* stream);
+
+/*
+ * Nearest neighbour of `query` in the database: the index i minimising the
+ * approximate W1 of (query, db[i]) as pd_w1_approx computes it (OPT_int;
+ * ties -> lowest i).  Lower bounds: LB_i = floor((1 - eps_c) * RWMD_i) with
+ * RWMD_i the relaxed-flow bound (Algorithm 1, diagonal included) of the
+ * 0-condensed diagrams, evaluated in float32 with every distance rounded down,
+ * and eps_c = 8 / (s - 4) (0 without condensation): delta-condensation moves
+ * the points by at most eps_c * RWMD in total, so LB_i <= OPT_int(query, db[i]).
+ * Pairs are solved in ascending LB_i (ties by index), opts->batch_slots pairs
+ * per batched solve (pd_w1_approx_batch); with opts->nn_prune (default) the
+ * search stops at the first pair whose bound exceeds the best optimum found,
+ * which leaves the answer unchanged.  opt_out (host, n_db entries, may be
+ * NULL): OPT_int of every solved pair, -1 for pruned pairs; lb_out (host,
+ * n_db, may be NULL): LB_i.  An empty database gives nn_index = -1.
+ */
+pd_status pd_nn_search(pd_ctx* ctx, pd_diagram query, double eps, const pd_opts* opts, pd_nn_result* out,
+                       int64_t* opt_out, int64_t* lb_out, void* stream);
 
 /*
  * Allocation-free min-cost flow (no counterpart in the paper).

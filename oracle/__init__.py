@@ -381,3 +381,15 @@ def w1_approx(A, B, dtype, eps=0.1, k=None, s_override=0, perturb=True, seed=0,
         opt, flow, pot = mcf(net)
         out.update(opt=opt, flow=flow, pot=pot, slack=int(flow.sum()), w1=math.ldexp(opt, -k))
     return out
+
+
+def nn_search(query, db, dtype, eps=0.05, **kw):
+    """Nearest neighbour of `query` among the diagrams of `db` (the NN-search
+    application of the experiments section): the index minimising the
+    approximate W1 of w1_approx(query, db[i]) -- OPT_int, ties to the lowest
+    index -- computed by solving every pair.  Returns (index, [OPT_int])."""
+    opts = [w1_approx(query, d, dtype, eps=eps, **kw)["opt"] for d in db]
+    if not opts:
+        return -1, []
+    best = min(range(len(opts)), key=lambda i: (opts[i], i))
+    return best, opts

@@ -18,7 +18,6 @@
 
 using namespace pd;
 
-struct pd_ctx : public pd::Ctx {};
 
 namespace pd {
 
@@ -26,6 +25,9 @@ long long& launch_count_ref() {
     static thread_local long long n = 0;
     return n;
 }
+
+static std::atomic<long long> g_launches{0};
+void count_launch_total() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 __global__ void k_fill_i64(int64_t* p, int64_t n, int64_t v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -109,7 +111,7 @@ static double s_bound(int64_t s) {
     return a * b;
 }
 
-static int64_t s_for_eps(double eps) {
+int64_t s_for_eps(double eps) {
     if (!(eps > 0.0)) return -1;
     for (int64_t s = 13; s < (int64_t(1) << 40); s++)
         if (s_bound(s) <= 1.0 + eps) return s;
@@ -145,7 +147,9 @@ static void delta_for(int64_t LA, int64_t LB, int64_t FA, int64_t FB, int64_t s,
 
 // ---------------------------------------------------------------------------
 
-static int default_shift(int dtype) { return dtype == PD_U8 ? 12 : 20; }
+namespace pd {
+int default_shift(int dtype) { return dtype == PD_U8 ? 12 : 20; }
+}  // namespace pd
 
 extern "C" void pd_opts_default(pd_opts* o) {
     if (!o) return;
@@ -165,6 +169,7 @@ extern "C" void pd_opts_default(pd_opts* o) {
     o->ns_block = 0;
     o->ns_transport = 1;
     o->ns_smem = 1;
+    o->nn_prune = 1;
 }
 
 namespace pd {
@@ -242,7 +247,9 @@ extern "C" void pd_destroy(pd_ctx* c) {
 
 extern "C" const char* pd_last_error(const pd_ctx* c) { return c ? c->err.c_str() : "no context"; }
 
-static pd_status check_diag(Ctx* c, const pd_diagram& d) {
+extern "C" int64_t pd_kernel_launches(void) { return g_launches.load(); }
+
+pd_status pd::check_diag(Ctx* c, const pd_diagram& d) {
     if (d.n < 0) return fail(c, PD_EINVAL, "negative diagram size");
     if (d.n > 0 && !d.bd) return fail(c, PD_EINVAL, "NULL diagram data");
     if (d.dtype != PD_F32 && d.dtype != PD_U8) return fail(c, PD_EINVAL, "unknown dtype");
@@ -252,7 +259,7 @@ static pd_status check_diag(Ctx* c, const pd_diagram& d) {
     return PD_OK;
 }
 
-static pd_status stage_inputs(Ctx* c, const pd_diagram& A, const pd_diagram& B, DevDiag* a, DevDiag* b,
+pd_status pd::stage_inputs(Ctx* c, const pd_diagram& A, const pd_diagram& B, DevDiag* a, DevDiag* b,
                               cudaStream_t st) {
     PD_TRY(check_diag(c, A));
     PD_TRY(check_diag(c, B));
@@ -389,12 +396,16 @@ struct Front {
     double delta = 0.0;
     int k = 0;
     pd_nodes nodes{};
-    pd_network net{}, mnet{};
+    pd_network net{}, mnet{};  // count-only front half: net holds only the counts, mnet is empty
+    WsTree tree{};
+    bool counted = false;
     float ms[6] = {};  // quantise+0-condense, RWMD, delta-condense, tree, WSPD, CSR
 };
 
+// count_only: the sparse network is enumerated and counted but not stored
+// (enough for the transportation form and its certificate).
 static pd_status front_half(Ctx* c, const pd_diagram& A, const pd_diagram& B, double eps, const pd_opts& o,
-                            Front* f, cudaStream_t st) {
+                            Front* f, cudaStream_t st, bool count_only) {
     cudaEvent_t ev[4];
     for (int q = 0; q < 4; q++) PD_TRY_CUDA(c, cudaEventCreate(&ev[q]));
     struct Guard {
@@ -421,8 +432,16 @@ static pd_status front_half(Ctx* c, const pd_diagram& A, const pd_diagram& B, do
     PD_TRY(stage_condense_delta(c, f->h, f->G, f->P, o.seed, &f->nodes, st));
     c->nodes = f->nodes;
     PD_TRY_CUDA(c, cudaEventRecord(ev[3], st));
-    PD_TRY(stage_network(c, f->nodes, f->s, &f->net, &f->ms[3], &f->ms[4], &f->ms[5], st));
+    PD_TRY(stage_network(c, f->nodes, f->s, &f->net, &f->ms[3], &f->ms[4], &f->ms[5], st, count_only, &f->tree));
+    f->counted = count_only;
     c->net = f->net;
+    if (count_only) {
+        PD_TRY_CUDA(c, cudaEventSynchronize(ev[3]));
+        cudaEventElapsedTime(&f->ms[0], ev[0], ev[1]);
+        cudaEventElapsedTime(&f->ms[1], ev[1], ev[2]);
+        cudaEventElapsedTime(&f->ms[2], ev[2], ev[3]);
+        return PD_OK;
+    }
     // The solver sees ā and b̄ merged into one diagonal node (the zero-cost
     // arc b̄ -> ā contracted): every flow of the paper's network maps to one of
     // the same cost, and an optimal acyclic flow of the merged network sends at
@@ -486,13 +505,38 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
     const long long launches0 = launch_count_ref();
     const auto t0 = std::chrono::steady_clock::now();
     Front f;
-    PD_TRY(front_half(c, A, B, eps, o, &f, st));
+    const bool transport = o.solver != 1 && o.ns_transport != 0;
+    PD_TRY(front_half(c, A, B, eps, o, &f, st, transport));
     const auto t1 = std::chrono::steady_clock::now();
     SolveStats ss;
-    if (o.solver == 1)
+    if (o.solver == 1) {
         PD_TRY(stage_solve(c, f.mnet, o, &ss, st));
-    else
-        PD_TRY(ns_solve_w1(c, f.nodes, f.net, f.mnet, o, &ss, st));
+    } else {
+        W1Prep w;
+        if (transport) PD_TRY(ns_prepare_w1(c, f.nodes, f.net.n_arcs, f.h.FB - f.h.FA, o, &w, st));
+        if (w.ns.ready) {
+            NSInst* d = bufT<NSInst>(c, B_NS_INST, 1);
+            if (!d) return PD_ENOMEM;
+            NSInst r{};
+            PD_TRY(ns_run(c, &w.ns.h, 1, w.ns.smem, d, &r, st));
+            PD_TRY(ns_finish_w1(c, f.tree, f.s, nullptr, o, w, d, r, &ss, st));
+        }
+        if (!w.ns.ready || ss.method == -1) {
+            // the sparse network itself: build it (the nodes are still in place) and solve it
+            const SolveStats first = ss;
+            pd_network mnet = f.mnet;
+            if (f.counted) {
+                pd_network net;
+                PD_TRY(stage_network(c, f.nodes, f.s, &net, nullptr, nullptr, nullptr, st));
+                PD_TRY(merge_diagonal(c, net, f.nodes.n_nodes, &mnet, st));
+            }
+            PD_TRY(ns_solve_network(c, mnet, o, &ss, st));
+            ss.pivots += first.pivots;
+            ss.degenerate += first.degenerate;
+            ss.scanned += first.scanned;
+            ss.cert_failures = first.cert_failures;
+        }
+    }
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     fill_result(f, ss, out);
     out->stage_ms[6] = elapsed_ms(t1);
@@ -508,8 +552,7 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
 struct BatchPair {
     Front f;
     W1Prep w;
-    pd_nodes nodes{};   // slot copies: n_nodes, X, Y
-    pd_network ws{};    // slot copies: n_nodes, n_arcs, row_ptr, head
+    WsTree tree{};      // slot copies of the node coordinates and the WSPD tree
     bool done = false;  // solved during preprocessing (no transportation form)
     SolveStats ss;
     float front_ms = 0.f, solve_ms = 0.f;
@@ -517,21 +560,39 @@ struct BatchPair {
     int inst = -1;      // index in the wave's launch
 };
 
+// What the certificate reads, copied from the worker into the pair's slot:
+// node coordinates and the WSPD tree (about 36 bytes per node).
 static pd_status persist_for_certificate(Ctx* slot, const Front& f, BatchPair* bp, cudaStream_t st) {
-    const int64_t N = f.nodes.n_nodes, n = f.net.n_nodes, m = f.net.n_arcs;
+    const int64_t N = f.nodes.n_nodes, M = N > 1 ? N - 1 : 1;
     int32_t* X = bufT<int32_t>(slot, B_NX, N);
     int32_t* Y = bufT<int32_t>(slot, B_NY, N);
-    int64_t* rp = bufT<int64_t>(slot, B_ROWPTR, n + 1);
-    int32_t* hd = bufT<int32_t>(slot, B_HEAD, m);
-    if (!X || !Y || !rp || !hd) return PD_ENOMEM;
+    int32_t* l = bufT<int32_t>(slot, B_T_LEFT, M);
+    int32_t* r = bufT<int32_t>(slot, B_T_RIGHT, M);
+    int4* bb = bufT<int4>(slot, B_T_BB, M);
+    int32_t* rep = bufT<int32_t>(slot, B_T_REP, M);
+    if (!X || !Y || !l || !r || !bb || !rep) return PD_ENOMEM;
     if (N > 0) {
         PD_TRY_CUDA(slot, cudaMemcpyAsync(X, f.nodes.X, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st));
         PD_TRY_CUDA(slot, cudaMemcpyAsync(Y, f.nodes.Y, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st));
     }
-    PD_TRY_CUDA(slot, cudaMemcpyAsync(rp, f.net.row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, st));
-    if (m > 0) PD_TRY_CUDA(slot, cudaMemcpyAsync(hd, f.net.head, sizeof(int32_t) * m, cudaMemcpyDeviceToDevice, st));
-    bp->nodes = pd_nodes{N, X, Y, nullptr, nullptr, nullptr};
-    bp->ws = pd_network{n, m, rp, hd, nullptr, nullptr};
+    if (N > 1) {
+        PD_TRY_CUDA(slot, cudaMemcpyAsync(l, f.tree.left, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, st));
+        PD_TRY_CUDA(slot, cudaMemcpyAsync(r, f.tree.right, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, st));
+        PD_TRY_CUDA(slot, cudaMemcpyAsync(bb, f.tree.bb, sizeof(int4) * M, cudaMemcpyDeviceToDevice, st));
+        PD_TRY_CUDA(slot, cudaMemcpyAsync(rep, f.tree.rep, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, st));
+    }
+    bp->tree = WsTree{N, X, Y, l, r, bb, rep};
+    return PD_OK;
+}
+
+// The sparse network of a pair, built in full and solved (no transportation
+// form, or its certificate failed).
+static pd_status solve_sparse(Ctx* c, const pd_diagram& A, const pd_diagram& B, double eps, const pd_opts& o,
+                              SolveStats* ss, cudaStream_t st) {
+    Front f;
+    PD_TRY(front_half(c, A, B, eps, o, &f, st, false));
+    PD_TRY(ns_solve_network(c, f.mnet, o, ss, st));
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     return PD_OK;
 }
 
@@ -545,13 +606,15 @@ static pd_status batch_prepare(Ctx* work, Ctx* slot, const pd_diagram& A, const 
     const auto t0 = std::chrono::steady_clock::now();
     work->last_ns_ms = 0.f;
     slot->last_ns_ms = 0.f;
-    PD_TRY(front_half(work, A, B, eps, o, &bp->f, st));
-    PD_TRY(ns_prepare_w1(slot, bp->f.nodes, bp->f.net, bp->f.mnet, o, &bp->w, st));
+    const bool transport = o.ns_transport != 0;
+    PD_TRY(front_half(work, A, B, eps, o, &bp->f, st, transport));
+    if (transport)
+        PD_TRY(ns_prepare_w1(slot, bp->f.nodes, bp->f.net.n_arcs, bp->f.h.FB - bp->f.h.FA, o, &bp->w, st));
     if (bp->w.ns.ready) {
         PD_TRY(persist_for_certificate(slot, bp->f, bp, st));
     } else {
         const auto t1 = std::chrono::steady_clock::now();
-        PD_TRY(ns_finish_w1(work, bp->f.nodes, bp->f.net, &bp->f.mnet, o, bp->w, nullptr, NSInst{}, &bp->ss, st));
+        PD_TRY(solve_sparse(work, A, B, eps, o, &bp->ss, st));
         bp->solve_ms = elapsed_ms(t1);
         bp->done = true;
     }
@@ -569,12 +632,19 @@ extern "C" pd_status pd_w1_approx_batch(pd_ctx* c, const pd_diagram* A, const pd
     if (count < 0 || (count > 0 && (!A || !B || !out))) return fail(c, PD_EINVAL, "bad batch arguments");
     if (count == 0) return PD_OK;
     pd_opts o = resolve_opts(opts);
+    return pd::batch_solve(c, A, B, count, eps, o, out, (cudaStream_t)stream);
+}
+
+namespace pd {
+
+pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t count, double eps,
+                      const pd_opts& o, pd_result* out, cudaStream_t st) {
+    if (count <= 0) return PD_OK;
     if (!(eps > 0.0) && o.s_override <= 0) return fail(c, PD_EINVAL, "eps must be > 0 (or set s_override)");
     if (o.solver == 1) return fail(c, PD_EINVAL, "the batched solve runs the network simplex only");
     if (o.batch_slots < 0 || o.batch_threads < 0) return fail(c, PD_EINVAL, "batch_slots and batch_threads must be >= 0");
     if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
-    cudaStream_t st = (cudaStream_t)stream;
-    const int64_t W = std::min<int64_t>(count, o.batch_slots > 0 ? o.batch_slots : std::max(c->sm_count, 1));
+    const int64_t W = std::min<int64_t>(count, o.batch_slots > 0 ? o.batch_slots : 2 * std::max(c->sm_count, 1));
     const int nthr = (int)std::min<int64_t>(W, o.batch_threads > 0 ? o.batch_threads : 8);
     while ((int64_t)c->slots.size() < W) {
         Ctx* sl = ctx_new(c->device, c->cap);
@@ -668,14 +738,12 @@ extern "C" pd_status pd_w1_approx_batch(pd_ctx* c, const pd_diagram* A, const pd
                 const long long l0 = launch_count_ref();
                 const auto t0 = std::chrono::steady_clock::now();
                 sl->last_ns_ms = 0.f;
-                status = ns_finish_w1(sl, p.nodes, p.ws, nullptr, o, p.w, d + p.inst, hout[(size_t)p.inst], &p.ss, st);
+                status = ns_finish_w1(sl, p.tree, p.f.s, nullptr, o, p.w, d + p.inst, hout[(size_t)p.inst], &p.ss, st);
                 if (status == PD_OK && p.ss.method == -1) {
                     Ctx* wk = c->workers[0];
-                    Front f2;
                     const SolveStats first_try = p.ss;
-                    status = front_half(wk, A[base + j], B[base + j], eps, o, &f2, wk->own_stream);
-                    if (status == PD_OK) status = ns_solve_network(wk, f2.mnet, o, &p.ss, wk->own_stream);
-                    if (status == PD_OK) status = cudaStreamSynchronize(wk->own_stream) == cudaSuccess ? PD_OK : PD_ECUDA;
+                    wk->last_ns_ms = 0.f;
+                    status = solve_sparse(wk, A[base + j], B[base + j], eps, o, &p.ss, wk->own_stream);
                     if (status != PD_OK) {
                         status = fail(c, status, "pair " + std::to_string(base + j) + ": " + wk->err);
                         break;
@@ -704,3 +772,5 @@ extern "C" pd_status pd_w1_approx_batch(pd_ctx* c, const pd_diagram* A, const pd
     cudaEventDestroy(ready);
     return status;
 }
+
+}  // namespace pd

@@ -8,9 +8,14 @@
 
 namespace pd {
 
-// Kernel launches issued by this library in this process (host-side count).
+// Kernel launches issued by this library: per host thread (for the per-call
+// counts in pd_result) and in total over the process (pd_kernel_launches).
 long long& launch_count_ref();
-inline void count_launch() { launch_count_ref()++; }
+void count_launch_total();
+inline void count_launch() {
+    launch_count_ref()++;
+    count_launch_total();
+}
 
 // Error bits raised by kernels into a device status word (host reads it back).
 enum : uint32_t {

@@ -27,7 +27,9 @@ enum Buf : int {
     B_RS_COUNTS, B_RS_PART, B_SCAN_PART,
     B_M_ROWPTR, B_M_SUPPLY,
     B_NS_PI, B_NS_PARENT, B_NS_PRED, B_NS_DEPTH, B_NS_FLOW, B_NS_UP, B_NS_ORD, B_NS_POS, B_NS_SIZE, B_NS_TMP,
-    B_NS_PATH, B_NS_SEG, B_NS_INST, B_NS_COST, B_TR_S, B_TR_T, B_TR_SUP, B_TR_XCOST,
+    B_NS_PATH, B_NS_SEG, B_NS_INST, B_NS_ORDER, B_NS_COST, B_TR_S, B_TR_T, B_TR_SUP, B_TR_XCOST,
+    B_DB_SXY, B_DB_SCNT, B_DB_SID,  // nearest-neighbour database: staging
+    B_DB_XY, B_DB_CNT, B_DB_ID, B_DB_OFF, B_DB_ROFF, B_Q_XY, B_Q_CNT, B_DB_LA, B_DB_BIG,
     B_SMALL,                        // small device scalars
     B_COUNT
 };
@@ -47,6 +49,13 @@ struct Ctx {
     std::vector<Ctx*> slots;    // pd_w1_approx_batch: per-pair buffers kept from preprocessing to solve
     std::vector<Ctx*> workers;  // pd_w1_approx_batch: preprocessing contexts, one per host thread
     cudaStream_t own_stream = nullptr;  // stream of a worker context
+    // nearest-neighbour database (pd_db_build): caller-owned diagrams and
+    // their 0-condensed nodes packed in B_DB_XY / B_DB_CNT / B_DB_ID / B_DB_OFF
+    std::vector<pd_diagram> db;
+    std::vector<int64_t> db_hats;
+    int64_t db_total = 0;
+    int db_k = 0, db_dtype = 0;
+    bool db_big = false;  // a database coordinate is not exact in float32
 };
 
 Ctx* ctx_new(int device, size_t cap);  // nullptr on failure
@@ -102,8 +111,25 @@ pd_status stage_condense0(Ctx* c, const DevDiag& A, const DevDiag& B, int k, Hat
 pd_status stage_rwmd(Ctx* c, const Hats& h, int64_t L[3], cudaStream_t st);
 pd_status stage_condense_delta(Ctx* c, const Hats& h, int64_t G, int64_t P, uint64_t seed, pd_nodes* out,
                                cudaStream_t st);
+// Hierarchical tree of the WSPD (device arrays of the context that built it):
+// internal nodes 0..N-2 with children (c >= 0 internal, c < 0 leaf ~c), tight
+// boxes (min x, max x, min y, max y) and leftmost representatives.
+struct WsTree {
+    int64_t N;
+    const int32_t* X;
+    const int32_t* Y;
+    const int32_t* left;
+    const int32_t* right;
+    const int4* bb;
+    const int32_t* rep;
+};
+
+// count_only: the WSPD is enumerated and its arcs counted (out->n_arcs,
+// n_nodes), but no arc is stored and out's arrays are null.  tree (may be
+// null) receives the hierarchical tree.
 pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* out, float* ms_tree,
-                        float* ms_wspd, float* ms_csr, cudaStream_t st);
+                        float* ms_wspd, float* ms_csr, cudaStream_t st, bool count_only = false,
+                        WsTree* tree = nullptr);
 pd_status merge_diagonal(Ctx* c, const pd_network& net, int64_t N, pd_network* out, cudaStream_t st);
 pd_status stage_solve(Ctx* c, const pd_network& net, const pd_opts& o, SolveStats* out, cudaStream_t st);
 
@@ -111,13 +137,20 @@ pd_status validate_nodes(Ctx* c, const pd_nodes& nodes, cudaStream_t st);
 pd_status validate_network(Ctx* c, const pd_network& net, cudaStream_t st);
 
 pd_status ns_solve_network(Ctx* c, const pd_network& net, const pd_opts& o, SolveStats* out, cudaStream_t st);
-pd_status ns_solve_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const pd_network& merged,
-                      const pd_opts& o, SolveStats* out, cudaStream_t st);
 __global__ void k_arc_tails(const int64_t* __restrict__ rp, int64_t n, int64_t m, int32_t* __restrict__ tail);
 __global__ void k_max_cost(const int64_t* __restrict__ cost, int64_t m, unsigned long long* __restrict__ out);
 __global__ void k_max_cost32(const int32_t* __restrict__ cost, int64_t m, unsigned long long* __restrict__ out);
 
 __global__ void k_row_ptr(const uint64_t* key, int64_t m, int hb, int64_t nrows, int64_t* row_ptr);
+
+// entry-point helpers shared by the C ABI files
+int default_shift(int dtype);                // k of the quantum for a dtype
+int64_t s_for_eps(double eps);               // WSPD parameter s from eps (-1 if none)
+pd_status check_diag(Ctx* c, const pd_diagram& d);
+pd_status stage_inputs(Ctx* c, const pd_diagram& A, const pd_diagram& B, DevDiag* a, DevDiag* b, cudaStream_t st);
+// pd_w1_approx_batch after argument checks (opts resolved)
+pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t count, double eps,
+                      const pd_opts& o, pd_result* out, cudaStream_t st);
 
 // radix sort / scan with context scratch
 pd_status sort_u64(Ctx* c, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n,
@@ -125,3 +158,6 @@ pd_status sort_u64(Ctx* c, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, u
 pd_status scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev, cudaStream_t st);
 
 }  // namespace pd
+
+// The opaque context of the C ABI.
+struct pd_ctx : public pd::Ctx {};

@@ -19,6 +19,7 @@
 // and the leaving arc is the last blocking arc met when the cycle is walked
 // from the apex in the direction of the entering arc, which rules out cycling.
 #include <algorithm>
+#include <vector>
 
 #include "internal.h"
 #include "netsimplex.cuh"
@@ -642,8 +643,7 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
     }
 }
 
-__global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts) {
-    NSInst& G = insts[blockIdx.x];
+__device__ __forceinline__ void ns_instance(NSInst& G) {
     NSInst I = G;
     const int32_t N1 = I.n + 1;
     if (I.smem_nodes) {
@@ -674,6 +674,22 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts) {
         T.ps = I.pos;
         T.od = I.ord;
         ns_body<int32_t>(G, I, T);
+    }
+}
+
+// Persistent: every CTA takes the next instance of `order` (largest first, so
+// the batch finishes close to its total work / CTAs) until none is left.
+__global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, const int32_t* __restrict__ order,
+                                                           int32_t count, int32_t* __restrict__ next) {
+    __shared__ int32_t s_k;
+    for (;;) {
+        if (threadIdx.x == 0) s_k = atomicAdd(next, 1);
+        __syncthreads();
+        const int32_t k = s_k;
+        __syncthreads();
+        if (k >= count) break;
+        ns_instance(insts[order[k]]);
+        __syncthreads();
     }
 }
 
@@ -779,12 +795,26 @@ pd_status ns_prepare_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS,
 pd_status ns_run(Ctx* c, const NSInst* h, int count, size_t smem, NSInst* d, NSInst* r, cudaStream_t st) {
     if (count <= 0) return PD_OK;
     PD_TRY_CUDA(c, cudaFuncSetAttribute(k_netsimplex, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PD_TRY_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_netsimplex, NS_THREADS, smem));
+    if (per_sm < 1) return fail(c, PD_ECAPACITY, "network simplex kernel does not fit on an SM");
+    const int grid = std::min(count, per_sm * std::max(c->sm_count, 1));
+    // largest instances first (nodes, then arcs), ties by position
+    std::vector<int32_t> order((size_t)count);
+    for (int q = 0; q < count; q++) order[(size_t)q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return h[x].n != h[y].n ? h[x].n > h[y].n : h[x].m > h[y].m;
+    });
+    int32_t* dord = bufT<int32_t>(c, B_NS_ORDER, count + 1);
+    if (!dord) return PD_ENOMEM;
     PD_TRY_CUDA(c, cudaMemcpyAsync(d, h, sizeof(NSInst) * count, cudaMemcpyHostToDevice, st));
+    PD_TRY_CUDA(c, cudaMemcpyAsync(dord, order.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, st));
+    PD_TRY_CUDA(c, cudaMemsetAsync(dord + count, 0, sizeof(int32_t), st));
     cudaEvent_t e0, e1;
     PD_TRY_CUDA(c, cudaEventCreate(&e0));
     PD_TRY_CUDA(c, cudaEventCreate(&e1));
     PD_TRY_CUDA(c, cudaEventRecord(e0, st));
-    k_netsimplex<<<count, NS_THREADS, smem, st>>>(d); pd::count_launch();
+    k_netsimplex<<<grid, NS_THREADS, smem, st>>>(d, dord, count, dord + count); pd::count_launch();
     cudaError_t le = cudaGetLastError();
     cudaEventRecord(e1, st);
     if (le == cudaSuccess) le = cudaMemcpyAsync(r, d, sizeof(NSInst) * count, cudaMemcpyDeviceToHost, st);
@@ -889,50 +919,6 @@ __global__ void k_transport_arcs(const int32_t* __restrict__ S, const int32_t* _
     cost[a - mst] = (int32_t)c;
 }
 
-// Certificate: every source->sink pair that carries flow on its direct route
-// must be an arc of the sparse network (then the transport optimum, a lower
-// bound on the sparse optimum, is attained on the sparse network).  Also
-// counts the arcs of the sparse network the flow uses (rounding slack).
-__global__ void k_certify_transport(const NSInst* __restrict__ I, const int32_t* __restrict__ S,
-                                    const int32_t* __restrict__ T, int64_t nS, int64_t nT,
-                                    const int32_t* __restrict__ X, const int32_t* __restrict__ Y,
-                                    const int64_t* __restrict__ rp, const int32_t* __restrict__ hd,
-                                    unsigned long long* __restrict__ out) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= I->n) return;
-    int64_t a = I->pred[v], f = I->flow[v];
-    if (a >= I->m || f <= 0) return;
-    int64_t mst = nS * nT;
-    if (a >= mst) {  // arc of the diagonal node: one arc of the sparse network
-        atomicAdd(&out[1], (unsigned long long)f);
-        return;
-    }
-    int64_t i = a / nT, j = a - i * nT;
-    int32_t u = S[i], w = T[j];
-    int64_t d = cost_l2(X[u], Y[u], X[w], Y[w]);
-    int64_t g = cost_diag(X[u], Y[u]) + cost_diag(X[w], Y[w]);
-    if (g <= d) {  // through the diagonal node: u -> diag -> w, both arcs exist
-        atomicAdd(&out[1], (unsigned long long)(2 * f));
-        return;
-    }
-    int64_t lo = rp[u], hi = rp[u + 1] - 1;
-    bool found = false;
-    while (lo <= hi) {
-        int64_t mid = (lo + hi) >> 1;
-        int32_t h = hd[mid];
-        if (h == w) {
-            found = true;
-            break;
-        }
-        if (h < w)
-            lo = mid + 1;
-        else
-            hi = mid - 1;
-    }
-    if (!found) atomicAdd(&out[0], 1ull);
-    atomicAdd(&out[1], (unsigned long long)f);
-}
-
 // Total flow over the arcs of a solved arc-list network (rounding slack).
 __global__ void k_tree_flow(const NSInst* __restrict__ I, unsigned long long* __restrict__ out) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -977,9 +963,10 @@ pd_status ns_solve_network(Ctx* c, const pd_network& net, const pd_opts& o, Solv
 // The W1 network: the transportation form is tried first when it is not
 // much larger than the sparse network (prepared here, launched by the caller,
 // checked by ns_finish_w1); otherwise, or if its certificate fails, the
-// simplex runs on the sparse network itself.
-pd_status ns_prepare_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const pd_network& merged,
-                        const pd_opts& o, W1Prep* w, cudaStream_t st) {
+// simplex runs on the sparse network itself.  n_arcs = arcs of the sparse
+// network, dsup = |B| - |A| (supply of the merged diagonal node).
+pd_status ns_prepare_w1(Ctx* c, const pd_nodes& nodes, int64_t n_arcs, int64_t dsup, const pd_opts& o, W1Prep* w,
+                        cudaStream_t st) {
     *w = W1Prep{};
     int64_t N = nodes.n_nodes;
     if (N == 0 || o.ns_transport == 0) return PD_OK;
@@ -993,13 +980,9 @@ pd_status ns_prepare_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, con
     PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     int64_t nS = c->h_small[2], nT = c->h_small[3];
-    // masses: diagonal supply |B| - |A| from the merged network's last node
-    int64_t dsup = 0;
-    PD_TRY_CUDA(c, cudaMemcpyAsync(&dsup, merged.supply + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     int64_t mst = nS * nT;
     int64_t mt = mst + (dsup < 0 ? nS : (dsup > 0 ? nT : 0));
-    if (!(mt <= 2 * ws.n_arcs + 4096 && mt < (int64_t(1) << 31))) return PD_OK;
+    if (!(mt <= 2 * n_arcs + 4096 && mt < (int64_t(1) << 31))) return PD_OK;
     int64_t nt = nS + nT + 1;
     int32_t* S = bufT<int32_t>(c, B_TR_S, nS);
     int32_t* T = bufT<int32_t>(c, B_TR_T, nT);
@@ -1011,7 +994,8 @@ pd_status ns_prepare_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, con
     int32_t* cost = bufT<int32_t>(c, B_TR_XCOST, mx);
     if (!S || !T || !sup || !tail || !head || !cost || !cmat) return PD_ENOMEM;
     k_side_lists<<<grid_for(N, 256), 256, 0, st>>>(nodes.cntA, nodes.cntB, N, fs, ft, S, T, sup, nS); pd::count_launch();
-    PD_TRY_CUDA(c, cudaMemcpyAsync(sup + nS + nT, &dsup, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    c->h_small[20] = dsup;
+    PD_TRY_CUDA(c, cudaMemcpyAsync(sup + nS + nT, c->h_small + 20, sizeof(int64_t), cudaMemcpyHostToDevice, st));
     PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, 8 * sizeof(unsigned long long), st));
     if (mt > 0)
         k_transport_arcs<<<grid_for(mt, 256), 256, 0, st>>>(S, T, nS, nT, dsup < 0 ? -1 : (dsup > 0 ? 1 : 0),
@@ -1032,17 +1016,15 @@ pd_status ns_prepare_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, con
     return PD_OK;
 }
 
-pd_status ns_finish_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const pd_network* merged,
-                       const pd_opts& o, const W1Prep& w, const NSInst* d_res, const NSInst& r, SolveStats* out,
-                       cudaStream_t st) {
+pd_status ns_finish_w1(Ctx* c, const WsTree& tr, int64_t s, const pd_network* merged, const pd_opts& o,
+                       const W1Prep& w, const NSInst* d_res, const NSInst& r, SolveStats* out, cudaStream_t st) {
     *out = SolveStats{};
     if (w.ns.ready) {
         PD_TRY(ns_status(c, r));
         unsigned long long* sm = bufT<unsigned long long>(c, B_SMALL, 64);
         if (!sm) return PD_ENOMEM;
         PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, 4 * sizeof(unsigned long long), st));
-        k_certify_transport<<<grid_for(w.nt, 256), 256, 0, st>>>(d_res, w.S, w.T, w.nS, w.nT, nodes.X, nodes.Y,
-                                                                  ws.row_ptr, ws.head, sm); pd::count_launch();
+        k_certify_tree<<<grid_for(w.nt, 256), 256, 0, st>>>(d_res, w.S, w.T, w.nS, w.nT, tr, s, sm); pd::count_launch();
         PD_TRY_CUDA(c, cudaGetLastError());
         PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         PD_TRY_CUDA(c, cudaStreamSynchronize(st));
@@ -1069,17 +1051,6 @@ pd_status ns_finish_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, cons
     out->degenerate += deg;
     out->cert_failures = fails;
     return PD_OK;
-}
-
-pd_status ns_solve_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const pd_network& merged,
-                      const pd_opts& o, SolveStats* out, cudaStream_t st) {
-    W1Prep w;
-    PD_TRY(ns_prepare_w1(c, nodes, ws, merged, o, &w, st));
-    NSInst r{};
-    NSInst* d = bufT<NSInst>(c, B_NS_INST, 1);
-    if (!d) return PD_ENOMEM;
-    if (w.ns.ready) PD_TRY(ns_run(c, &w.ns.h, 1, w.ns.smem, d, &r, st));
-    return ns_finish_w1(c, nodes, ws, &merged, o, w, d, r, out, st);
 }
 
 }  // namespace pd

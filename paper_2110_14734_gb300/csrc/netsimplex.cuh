@@ -48,8 +48,10 @@ struct NSInst {
     int32_t pad;
 };
 
-// One CTA per instance record; results are written back into the records.
-__global__ void k_netsimplex(NSInst* insts);
+// Persistent over `count` instance records taken in `order` (next = a zeroed
+// device counter); results are written back into the records.
+__global__ void k_netsimplex(NSInst* insts, const int32_t* __restrict__ order, int32_t count,
+                             int32_t* __restrict__ next);
 size_t ns_smem_bytes(int64_t N1);
 // True if the compact node arrays of N1 nodes fit in shared memory beside the
 // kernel's static shared memory (max_optin: the device's opt-in limit per CTA).
@@ -83,13 +85,16 @@ pd_status ns_prepare_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS,
 // dynamic shared memory of the instances.
 pd_status ns_run(Ctx* c, const NSInst* h, int count, size_t smem, NSInst* d, NSInst* r, cudaStream_t st);
 pd_status ns_status(Ctx* c, const NSInst& r);
-pd_status ns_prepare_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const pd_network& merged,
-                        const pd_opts& o, W1Prep* w, cudaStream_t st);
-// Certificate and fallback after the launch; d_res = the device record of the
-// solved instance, r = its host copy.  merged == nullptr: no fallback here --
-// out->method = -1 tells the caller to solve the sparse network itself.
-pd_status ns_finish_w1(Ctx* c, const pd_nodes& nodes, const pd_network& ws, const pd_network* merged,
-                       const pd_opts& o, const W1Prep& w, const NSInst* d_res, const NSInst& r, SolveStats* out,
-                       cudaStream_t st);
+pd_status ns_prepare_w1(Ctx* c, const pd_nodes& nodes, int64_t n_arcs, int64_t dsup, const pd_opts& o, W1Prep* w,
+                        cudaStream_t st);
+// Certificate (on the WSPD tree of s) and fallback after the launch; d_res =
+// the device record of the solved instance, r = its host copy.  merged ==
+// nullptr: no fallback here -- out->method = -1 tells the caller to solve the
+// sparse network itself.
+pd_status ns_finish_w1(Ctx* c, const WsTree& tr, int64_t s, const pd_network* merged, const pd_opts& o,
+                       const W1Prep& w, const NSInst* d_res, const NSInst& r, SolveStats* out, cudaStream_t st);
+__global__ void k_certify_tree(const NSInst* __restrict__ I, const int32_t* __restrict__ S,
+                               const int32_t* __restrict__ T, int64_t nS, int64_t nT, WsTree tr, int64_t s,
+                               unsigned long long* __restrict__ out);
 
 }  // namespace pd

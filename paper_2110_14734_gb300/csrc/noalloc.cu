@@ -162,7 +162,8 @@ extern "C" pd_status pd_mcf_solve_noalloc(const pd_network* net, int64_t* opt_ou
     if (!h.smem_nodes) smem = 0;
     NA_TRY(cudaFuncSetAttribute(k_netsimplex, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     NA_TRY(cudaMemcpyAsync(dinst, &h, sizeof(NSInst), cudaMemcpyHostToDevice, st));
-    k_netsimplex<<<1, NS_THREADS, smem, st>>>(dinst); pd::count_launch();
+    int32_t* order = (int32_t*)(flags + 4);  // zeroed with the flags: order = {0}, next = 0
+    k_netsimplex<<<1, NS_THREADS, smem, st>>>(dinst, order, 1, order + 1); pd::count_launch();
     NA_TRY(cudaGetLastError());
     NSInst r;
     NA_TRY(cudaMemcpyAsync(&r, dinst, sizeof(NSInst), cudaMemcpyDeviceToHost, st));

@@ -2,6 +2,7 @@
 // (Algorithms 6-8 as a level-synchronous pair frontier), diagonal arcs
 // (Algorithm 9) and the CSR network.
 #include "internal.h"
+#include "netsimplex.cuh"
 #include "prims.cuh"
 
 namespace pd {
@@ -141,6 +142,83 @@ PD_D int64_t max_side(const TNode& a) {
     return wx > wy ? wx : wy;
 }
 
+// Is (a, b), a < b two leaves (Morton ranks), one of the biarcs of the
+// s-WSPD?  The pairs of the decomposition partition all leaf pairs, so (a, b)
+// lies in exactly one of them: start at the pair of children of the lowest
+// common ancestor and follow the same split rule as k_ws_expand (larger box
+// side, ties split the second node), always into the child holding a
+// (resp. b), until the pair is well separated.  (a, b) is an arc iff a and b
+// are the representatives of that pair.  A walk longer than any tree path
+// answers false, which the certificate treats as a failure (never as proof).
+PD_D bool ws_arc_exists(int32_t a, int32_t b, int64_t N, const int32_t* __restrict__ X,
+                        const int32_t* __restrict__ Y, const int4* __restrict__ bb, const int32_t* __restrict__ rep,
+                        const int32_t* __restrict__ left, const int32_t* __restrict__ right, int64_t s) {
+    if (N < 2 || a >= b || a < 0 || b >= N) return false;
+    int32_t z = 0;  // the root covers [0, N - 1]
+    int32_t sp = 0;
+    int depth = 0;
+    for (; depth < 130; depth++) {
+        const int32_t lc = left[z], rc = right[z];
+        sp = lc >= 0 ? lc : ~lc;  // left child covers [lo, sp], right child [sp + 1, hi]
+        if (b <= sp) {
+            if (lc < 0) return false;
+            z = lc;
+        } else if (a > sp) {
+            if (rc < 0) return false;
+            z = rc;
+        } else {
+            break;
+        }
+    }
+    if (depth >= 130) return false;
+    int32_t P = left[z], Q = right[z];
+    for (int it = 0; it < 260; it++) {
+        const TNode tp = load_tnode(P, X, Y, bb, rep, left, right);
+        const TNode tq = load_tnode(Q, X, Y, bb, rep, left, right);
+        if (well_separated(tp, tq, s)) return tp.rep == a && tq.rep == b;
+        if (max_side(tp) > max_side(tq)) {
+            if (P < 0) return false;
+            const int32_t c = tp.l >= 0 ? tp.l : ~tp.l;
+            P = a <= c ? tp.l : tp.r;
+        } else {
+            if (Q < 0) return false;
+            const int32_t c = tq.l >= 0 ? tq.l : ~tq.l;
+            Q = b <= c ? tq.l : tq.r;
+        }
+    }
+    return false;
+}
+
+// Certificate of a transportation optimum against the sparse network: every
+// source -> sink pair that carries flow on its direct route must be a WSPD
+// biarc (found by ws_arc_exists); routes through the diagonal use arcs that
+// always exist.  out[0] = pairs missing, out[1] = total flow over the arcs of
+// the sparse network that the flow uses (rounding slack).
+__global__ void k_certify_tree(const NSInst* __restrict__ I, const int32_t* __restrict__ S,
+                               const int32_t* __restrict__ T, int64_t nS, int64_t nT, WsTree tr, int64_t s,
+                               unsigned long long* __restrict__ out) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= I->n) return;
+    int64_t a = I->pred[v], f = I->flow[v];
+    if (a >= I->m || f <= 0) return;
+    int64_t mst = nS * nT;
+    if (a >= mst) {  // arc of the diagonal node: one arc of the sparse network
+        atomicAdd(&out[1], (unsigned long long)f);
+        return;
+    }
+    int64_t i = a / nT, j = a - i * nT;
+    int32_t u = S[i], w = T[j];
+    int64_t d = cost_l2(tr.X[u], tr.Y[u], tr.X[w], tr.Y[w]);
+    int64_t g = cost_diag(tr.X[u], tr.Y[u]) + cost_diag(tr.X[w], tr.Y[w]);
+    if (g <= d) {  // through the diagonal node: u -> diag -> w, both arcs exist
+        atomicAdd(&out[1], (unsigned long long)(2 * f));
+        return;
+    }
+    const int32_t lo = u < w ? u : w, hi = u < w ? w : u;
+    if (!ws_arc_exists(lo, hi, tr.N, tr.X, tr.Y, tr.bb, tr.rep, tr.left, tr.right, s)) atomicAdd(&out[0], 1ull);
+    atomicAdd(&out[1], (unsigned long long)f);
+}
+
 __global__ void k_frontier_init(int64_t N, const int32_t* __restrict__ left, const int32_t* __restrict__ right,
                                 int2* __restrict__ F) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -178,8 +256,10 @@ __global__ void k_ws_expand(const int2* __restrict__ F, int64_t nf, const int64_
     TNode v = load_tnode(p.y, X, Y, bb, rep, left, right);
     int64_t o = off[i];
     if (flag[i]) {
-        arcs[2 * o] = ((uint64_t)u.rep << hb) | (uint64_t)v.rep;
-        arcs[2 * o + 1] = ((uint64_t)v.rep << hb) | (uint64_t)u.rep;
+        if (arcs) {  // null: only the frontier is built (the arcs are counted by the caller)
+            arcs[2 * o] = ((uint64_t)u.rep << hb) | (uint64_t)v.rep;
+            arcs[2 * o + 1] = ((uint64_t)v.rep << hb) | (uint64_t)u.rep;
+        }
     } else {
         int64_t j = i - o;
         if (max_side(u) > max_side(v)) {
@@ -199,12 +279,14 @@ __global__ void k_diag_arcs(int64_t N, const int64_t* __restrict__ cntA, const i
     int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u > N) return;
     if (u == N) {
-        arcs[2 * N] = ((uint64_t)(N + 1) << hb) | (uint64_t)N;
+        if (arcs) arcs[2 * N] = ((uint64_t)(N + 1) << hb) | (uint64_t)N;
         return;
     }
     bool a = cntA[u] > 0, b = cntB[u] > 0;
-    arcs[2 * u] = a ? (((uint64_t)u << hb) | (uint64_t)N) : sent;
-    arcs[2 * u + 1] = b ? (((uint64_t)(N + 1) << hb) | (uint64_t)u) : sent;
+    if (arcs) {  // null: count only
+        arcs[2 * u] = a ? (((uint64_t)u << hb) | (uint64_t)N) : sent;
+        arcs[2 * u + 1] = b ? (((uint64_t)(N + 1) << hb) | (uint64_t)u) : sent;
+    }
     unsigned ma = __ballot_sync(__activemask(), a), mb = __ballot_sync(__activemask(), b);
     if ((threadIdx.x & 31) == (__ffs(__activemask()) - 1)) {
         atomicAdd(&counts[0], (unsigned long long)__popc(ma));
@@ -323,7 +405,7 @@ pd_status merge_diagonal(Ctx* c, const pd_network& net, int64_t N, pd_network* o
 }
 
 pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* out, float* ms_tree,
-                        float* ms_wspd, float* ms_csr, cudaStream_t st) {
+                        float* ms_wspd, float* ms_csr, cudaStream_t st, bool count_only, WsTree* tree) {
     int64_t N = nodes.n_nodes;
     if (N >= (int64_t(1) << 31) - 4) return fail(c, PD_ECAPACITY, "more than 2^31 - 4 condensed nodes");
     if (s < 1) return fail(c, PD_EINVAL, "WSPD parameter s must be >= 1");
@@ -347,6 +429,7 @@ pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* ou
         PD_TRY_CUDA(c, cudaGetLastError());
     }
     PD_TRY_CUDA(c, cudaEventRecord(ev[1], st));
+    if (tree) *tree = WsTree{N, nodes.X, nodes.Y, left, right, bb, rep};
 
     int hb = bits_for((uint64_t)(N + 2));
     int kb = 2 * hb;
@@ -372,7 +455,7 @@ pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* ou
         PD_TRY_CUDA(c, cudaStreamSynchronize(st));
         int64_t nws = h[0];
         int64_t need = narcs + 2 * nws + 2 * N + 1;
-        if (need > acap) {
+        if (!count_only && need > acap) {
             // grow the arc buffer, keeping what is there
             int64_t ncap = need + need / 2 + 1024;
             uint64_t* tmp = bufT<uint64_t>(c, B_ARCKEY2, ncap);
@@ -389,7 +472,7 @@ pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* ou
         if (!Fn) return PD_ENOMEM;
         // F may have moved if its buffer grew: it did not (only Fn's buffer is resized here)
         k_ws_expand<<<grid_for(nf, 256), 256, 0, st>>>(F, nf, flag, off, nodes.X, nodes.Y, bb, rep, left, right, hb,
-                                                        arcs + narcs, Fn); pd::count_launch();
+                                                        count_only ? nullptr : arcs + narcs, Fn); pd::count_launch();
         PD_TRY_CUDA(c, cudaGetLastError());
         narcs += 2 * nws;
         nf = nn;
@@ -397,6 +480,22 @@ pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* ou
         fb ^= 1;
     }
     PD_TRY_CUDA(c, cudaEventRecord(ev[2], st));
+    if (count_only) {
+        // only the counts: arcs of the WSPD, diagonal arcs and the masses
+        PD_TRY_CUDA(c, cudaMemsetAsync(cnts, 0, 8 * sizeof(unsigned long long), st));
+        k_diag_arcs<<<grid_for(N + 1, 256), 256, 0, st>>>(N, nodes.cntA, nodes.cntB, hb, sent, nullptr, cnts); pd::count_launch();
+        k_mass<<<grid_for(N, 256), 256, 0, st>>>(N, nodes.cntA, nodes.cntB, cnts); pd::count_launch();
+        PD_TRY_CUDA(c, cudaGetLastError());
+        PD_TRY_CUDA(c, cudaMemcpyAsync(h, cnts, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PD_TRY_CUDA(c, cudaEventRecord(ev[3], st));
+        PD_TRY_CUDA(c, cudaEventSynchronize(ev[3]));
+        *out = pd_network{N + 2, narcs + h[0] + h[1] + 1, nullptr, nullptr, nullptr, nullptr};
+        if (ms_tree) cudaEventElapsedTime(ms_tree, ev[0], ev[1]);
+        if (ms_wspd) cudaEventElapsedTime(ms_wspd, ev[1], ev[2]);
+        if (ms_csr) cudaEventElapsedTime(ms_csr, ev[2], ev[3]);
+        for (int q = 0; q < 4; q++) cudaEventDestroy(ev[q]);
+        return PD_OK;
+    }
     if (!arcs) {
         acap = 2 * N + 1;
         arcs = bufT<uint64_t>(c, B_ARCKEY, acap);

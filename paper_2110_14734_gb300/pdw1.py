@@ -36,7 +36,8 @@ class pd_opts(C.Structure):
                 ("max_rounds", C.c_int64), ("time_limit_ms", C.c_int64), ("update_every", C.c_int64),
                 ("seq_threshold", C.c_int32), ("solver", C.c_int32), ("ns_block", C.c_int64),
                 ("ns_transport", C.c_int32), ("ns_smem", C.c_int32), ("batch_slots", C.c_int32),
-                ("batch_threads", C.c_int32)]
+                ("batch_threads", C.c_int32),
+                ("nn_prune", C.c_int32), ("reserved1", C.c_int32)]
 
 
 class pd_nodes(C.Structure):
@@ -68,12 +69,23 @@ class pd_result(C.Structure):
         return d
 
 
+class pd_nn_result(C.Structure):
+    _fields_ = [("nn_index", C.c_int64), ("nn_opt_quanta", C.c_int64), ("nn_w1", C.c_double),
+                ("solved", C.c_int64), ("pruned", C.c_int64), ("waves", C.c_int32), ("coord_shift", C.c_int32),
+                ("lb_ms", C.c_float), ("solve_ms", C.c_float), ("total_ms", C.c_float), ("reserved", C.c_int32)]
+
+    def to_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib.pd_create.restype = C.c_int
 _lib.pd_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_size_t]
 _lib.pd_destroy.restype = None
 _lib.pd_destroy.argtypes = [C.c_void_p]
 _lib.pd_last_error.restype = C.c_char_p
 _lib.pd_last_error.argtypes = [C.c_void_p]
+_lib.pd_kernel_launches.restype = C.c_int64
+_lib.pd_kernel_launches.argtypes = []
 _lib.pd_opts_default.restype = None
 _lib.pd_opts_default.argtypes = [C.POINTER(pd_opts)]
 _lib.pd_condense.restype = C.c_int
@@ -93,6 +105,12 @@ _lib.pd_w1_approx.argtypes = [C.c_void_p, pd_diagram, pd_diagram, C.c_double, C.
 _lib.pd_w1_approx_batch.restype = C.c_int
 _lib.pd_w1_approx_batch.argtypes = [C.c_void_p, C.POINTER(pd_diagram), C.POINTER(pd_diagram), C.c_int64,
                                     C.c_double, C.POINTER(pd_opts), C.POINTER(pd_result), C.c_void_p]
+
+_lib.pd_db_build.restype = C.c_int
+_lib.pd_db_build.argtypes = [C.c_void_p, C.POINTER(pd_diagram), C.c_int64, C.POINTER(pd_opts), C.c_void_p]
+_lib.pd_nn_search.restype = C.c_int
+_lib.pd_nn_search.argtypes = [C.c_void_p, pd_diagram, C.c_double, C.POINTER(pd_opts), C.POINTER(pd_nn_result),
+                              C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_void_p]
 
 _lib.pd_mcf_solve_noalloc.restype = C.c_int
 _lib.pd_mcf_solve_noalloc.argtypes = [C.POINTER(pd_network), C.POINTER(C.c_int64), C.c_void_p]
@@ -132,6 +150,11 @@ def _stream(stream):
     if isinstance(stream, torch.cuda.Stream):
         return stream.cuda_stream
     return int(stream)
+
+
+def pd_kernel_launches() -> int:
+    """Kernels the library has launched in this process (all threads)."""
+    return int(_lib.pd_kernel_launches())
 
 
 def opts(**kw) -> pd_opts:
@@ -282,6 +305,35 @@ def pd_w1_approx_batch(ctx: Context, As, Bs, eps: float, o: pd_opts | None = Non
 def pd_w1_approx_batch_raw(ctx: Context, da, db, n: int, eps: float, o, res, stream: int):
     """Allocation-free batched call for timing loops: prebuilt ctypes arrays."""
     return _lib.pd_w1_approx_batch(ctx.ptr, da, db, n, eps, C.byref(o) if o else None, res, C.c_void_p(stream))
+
+
+def pd_db_build(ctx: Context, dbs, o: pd_opts | None = None, stream=None):
+    """Database for pd_nn_search; the tensors stay referenced by the context
+    wrapper until the next build."""
+    n = len(dbs)
+    arr = (pd_diagram * max(n, 1))()
+    keep = []
+    for i, d in enumerate(dbs):
+        arr[i], k = diagram(d)
+        keep.append(k)
+    ctx.check(_lib.pd_db_build(ctx.ptr, arr, n, C.byref(o) if o else None, C.c_void_p(_stream(stream))))
+    ctx._db_keep = keep  # the library reads these diagrams during searches
+
+
+def pd_nn_search(ctx: Context, query, eps: float, o: pd_opts | None = None, stream=None) -> dict:
+    """Nearest neighbour of `query` in the database: dict of pd_nn_result plus
+    per-diagram `opt` (-1 where pruned) and `lb` lists."""
+    dq, kq = diagram(query)
+    n = len(getattr(ctx, "_db_keep", []))
+    res = pd_nn_result()
+    opt = (C.c_int64 * max(n, 1))()
+    lb = (C.c_int64 * max(n, 1))()
+    ctx.check(_lib.pd_nn_search(ctx.ptr, dq, float(eps), C.byref(o) if o else None, C.byref(res), opt, lb,
+                                C.c_void_p(_stream(stream))))
+    d = res.to_dict()
+    d["opt"] = [int(opt[i]) for i in range(n)]
+    d["lb"] = [int(lb[i]) for i in range(n)]
+    return d
 
 
 def pd_w1_approx_raw(ctx: Context, da: pd_diagram, db: pd_diagram, eps: float, o, res: pd_result, stream: int):

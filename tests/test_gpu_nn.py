@@ -1,0 +1,88 @@
+"""Nearest-neighbour search (pd_db_build / pd_nn_search): the answer equals
+the oracle's argmin over every pair, with and without pruning, and every lower
+bound is below the optimum it prunes against.  Runs on a GPU only."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2110_14734_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pd():
+    from paper_2110_14734_gb300 import build
+    build.build()
+    from paper_2110_14734_gb300 import pdw1
+    return pdw1
+
+
+@pytest.fixture(scope="module")
+def ctx(pd):
+    c = pd.pd_create(0)
+    yield c
+    c.close()
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _db(count, seed, lo=20, hi=1500):
+    sizes = synth.db_sizes(count, seed, lo, hi)
+    return [synth.uniform_exp(int(n), 5000 + 7 * seed + i) for i, n in enumerate(sizes)]
+
+
+def test_nn_matches_oracle_with_and_without_pruning(pd, ctx):
+    db = _db(20, 3)
+    q = synth.uniform_exp(800, 42)
+    eps = 0.1
+    pd.pd_db_build(ctx, [_cuda(d) for d in db])
+    full = pd.pd_nn_search(ctx, _cuda(q), eps, pd.opts(nn_prune=0))
+    idx, opts = oracle.nn_search(q, db, "f32", eps=eps)
+    assert full["opt"] == opts
+    assert full["nn_index"] == idx and full["nn_opt_quanta"] == opts[idx]
+    assert full["solved"] == len(db) and full["pruned"] == 0
+    assert all(0 <= lb <= o for lb, o in zip(full["lb"], opts))
+    pr = pd.pd_nn_search(ctx, _cuda(q), eps, pd.opts(batch_slots=4))
+    assert pr["nn_index"] == idx and pr["nn_opt_quanta"] == opts[idx]
+    assert pr["solved"] + pr["pruned"] == len(db)
+    assert all(o_p in (-1, o) for o_p, o in zip(pr["opt"], opts))
+    assert pr["lb"] == full["lb"]
+
+
+def test_nn_duplicate_of_the_query_wins_at_its_lowest_index(pd, ctx):
+    db = _db(12, 9)
+    db[8] = db[3].copy()
+    pd.pd_db_build(ctx, db)  # host-memory diagrams
+    r = pd.pd_nn_search(ctx, db[3].copy(), 0.05, pd.opts(batch_slots=2))
+    assert r["nn_index"] == 3 and r["nn_opt_quanta"] == 0 and r["lb"][3] == 0
+    assert r["opt"][3] == 0 and r["opt"][8] in (-1, 0)
+
+
+def test_nn_lowerstar_u8(pd, ctx):
+    sizes = synth.db_sizes(8, 21, 500, 5000)
+    db = [synth.lowerstar_u8(int(n), 9000 + i) for i, n in enumerate(sizes)]
+    q = synth.lowerstar_u8(3000, 8999)
+    pd.pd_db_build(ctx, [_cuda(d) for d in db])
+    full = pd.pd_nn_search(ctx, _cuda(q), 0.05, pd.opts(nn_prune=0))
+    pr = pd.pd_nn_search(ctx, _cuda(q), 0.05)
+    idx, opts = oracle.nn_search(q, db, "u8", eps=0.05)
+    assert full["opt"] == opts and full["nn_index"] == idx
+    assert (pr["nn_index"], pr["nn_opt_quanta"]) == (idx, opts[idx])
+    assert all(lb <= o for lb, o in zip(full["lb"], opts))
+
+
+def test_nn_empty_database_and_bad_queries(pd, ctx):
+    pd.pd_db_build(ctx, [])
+    r = pd.pd_nn_search(ctx, _cuda(synth.uniform_exp(100, 1)), 0.1)
+    assert r["nn_index"] == -1 and r["solved"] == 0
+    pd.pd_db_build(ctx, [_cuda(synth.uniform_exp(50, 2))])
+    with pytest.raises(pd.PDError):
+        pd.pd_nn_search(ctx, _cuda(synth.lowerstar_u8(100, 3)), 0.1)  # dtype differs from the database
+    with pytest.raises(pd.PDError):
+        pd.pd_nn_search(ctx, _cuda(synth.uniform_exp(100, 1)), 0.0)
+    with pytest.raises(pd.PDError):
+        pd.pd_db_build(ctx, [_cuda(synth.uniform_exp(50, 2)), _cuda(synth.lowerstar_u8(60, 3))])

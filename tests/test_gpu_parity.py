@@ -285,3 +285,18 @@ def test_w1_approx_full_size_lowerstar_100k(pd, ctx):
     parity of every integer result with the oracle."""
     A, B = synth.lowerstar_u8(100000, 1000), synth.lowerstar_u8(100000, 1001)
     _check_w1(pd, ctx, A, B, "u8", 0.05)
+
+
+def test_w1_certificate_on_coarse_decompositions(pd, ctx):
+    """Small s gives a sparse network that misses many direct routes: the
+    transportation optimum must then fail its certificate (tree query of the
+    WSPD) and the sparse network be solved instead -- the optimum always
+    equals the oracle's OPT(WS)."""
+    A, B = synth.uniform_exp(700, 61), synth.uniform_exp(650, 62)
+    fails = 0
+    for s in (1, 2, 4, 13):
+        g, r = _check_w1(pd, ctx, A, B, "f32", 0.1, s_override=s)
+        fails += g["cert_failures"] > 0
+        if g["cert_failures"] > 0:
+            assert g["solve_method"] == 1
+    assert fails > 0

@@ -566,3 +566,25 @@ def test_contracting_the_zero_cost_diagonal_arc_keeps_the_optimum(orc, seed, eps
     msup = np.concatenate([sup[:N], [sup[N] + sup[N + 1]]])
     st, opt, flow, pot = orc.mcf_arcs(N + 1, t, head[keep], cost[keep], msup)
     assert st == 0 and opt == r["opt"]
+
+
+def test_nn_search_ties_and_dense_limit(orc):
+    """Nearest neighbour (the NN-search application): the argmin of OPT_int,
+    ties to the lowest index.  In the dense limit (no condensation, s huge)
+    OPT_int is the dense integer optimum on the 0-condensed diagrams, so the
+    answer must match brute force over dense_opt_int."""
+    db = [_small_pair(n, 700 + i)[0] for i, n in enumerate([40, 25, 60, 33, 50, 18])]
+    db.append(db[2].copy())  # a duplicate of diagram 2 at a higher index
+    q = db[2].copy()
+    idx, opts = orc.nn_search(q, db, "f32", eps=0.1)
+    assert idx == 2 and opts[2] == 0 and opts[6] == 0
+    q2 = _small_pair(45, 777)[0]
+    idx2, opts2 = orc.nn_search(q2, db, "f32", s_override=10**7, condense=False)
+    dense = []
+    for d in db:
+        XA, YA = orc.quantize(q2, "f32", 20)
+        XB, YB = orc.quantize(d, "f32", 20)
+        dense.append(orc.dense_opt_int(orc.condense0(XA, YA), orc.condense0(XB, YB)))
+    assert opts2 == dense
+    assert idx2 == min(range(len(dense)), key=lambda i: (dense[i], i))
+    assert orc.nn_search(q2, [], "f32") == (-1, [])
