@@ -93,7 +93,11 @@ typedef struct {
     int32_t batch_threads;  /* pd_w1_approx_batch: host threads preprocessing pairs (0 = 8) */
     int32_t nn_prune;       /* pd_nn_search: 1 = skip pairs whose lower bound exceeds the best optimum
                                (default); 0 = solve every pair */
-    int32_t reserved1;
+    int32_t warm_start;     /* network simplex on the transportation form: 0 = cold start (default);
+                               1 = start from the potentials predicted by the context's network
+                               (pd_ws_train / pd_ws_load); 2 = start from the exact potentials of a
+                               cold solve of the same pair (diagnostic: the best a prediction can do);
+                               3 = start from potentials 0 (the greedy on costs alone, no network) */
 } pd_opts;
 
 void pd_opts_default(pd_opts* opts);
@@ -154,7 +158,7 @@ typedef struct {
     int32_t cert_failures;  /* pairs of the transportation optimum missing from the sparse network */
     int64_t kernel_launches; /* kernels this call launched */
     float ns_kernel_ms;     /* device time of the network simplex kernel(s) of this call */
-    int32_t reserved;
+    int32_t warm_used;      /* 1 if the simplex started from a warm-start tree */
     float stage_ms[8];      /* device time of quantize+0-condense, RWMD, delta-condense, tree, WSPD, CSR;
                                host wall time of the solve (incl. certificate) and of the whole call */
 } pd_result;
@@ -282,6 +286,58 @@ pd_status pd_db_build(pd_ctx* ctx, const pd_diagram* dbs, int64_t n_db, const pd
  */
 pd_status pd_nn_search(pd_ctx* ctx, pd_diagram query, double eps, const pd_opts* opts, pd_nn_result* out,
                        int64_t* opt_out, int64_t* lb_out, void* stream);
+
+/* ---- learned warm start (no counterpart in the paper) ----------------------
+ *
+ * A network of 68 -> 128 -> 128 -> 1 units (ReLU) predicts, per node of the
+ * transportation form, its optimal potential (up to a common offset);
+ * the simplex then starts from a greedy flow on the arcs of smallest
+ * predicted reduced cost instead of the all-artificial tree (pd_opts
+ * warm_start = 1).  Weights are stored in bf16, products accumulate in
+ * float32; the float32 master parameters (PD_WS_NPARAMS floats) are laid out
+ * as W1[68][128], b1[128], W2[128][128], b2[128], w3[128], b3 (W[k][j] is the
+ * weight from input k to unit j).  Features of a node (68): its coordinates
+ * relative to the pair's node box and divided by the box's larger side,
+ * log(1 + cntA), log(1 + cntB), and an 8 x 8 window (offsets -4..3) of a
+ * 64 x 64 grid over the box holding sign(s) log(1 + |s|) of the summed supply
+ * s = cntA - cntB of the nodes in each cell.  Target: (potential of the node
+ * in the optimal tree - the mean potential of the tree's largest component
+ * below the root) / the box's side, for the nodes of that component.
+ */
+#define PD_WS_NFEAT 68
+#define PD_WS_NPARAMS 25473
+
+typedef struct {
+    int64_t rows;        /* training rows (transportation nodes) collected */
+    int32_t pairs;       /* pairs whose cold solve gave rows */
+    int32_t steps;       /* optimiser steps */
+    float loss_first;    /* mean squared error of the first step */
+    float loss_last;     /* ... of the last step */
+    float collect_ms;    /* host wall time of the cold solves and feature extraction */
+    float train_ms;      /* host wall time of the optimisation */
+    int64_t cold_pivots; /* pivots of the cold solves */
+} pd_ws_stats;
+
+/* Trains the context's network (initialised from `seed` on first use) on the
+ * potentials of cold solves of the n_pairs pairs (A[i], B[i]) at eps/opts:
+ * `epochs` passes of Adam (lr) over minibatches of 2048 rows, on the device. */
+pd_status pd_ws_train(pd_ctx* ctx, const pd_diagram* A, const pd_diagram* B, int64_t n_pairs, double eps,
+                      const pd_opts* opts, int32_t epochs, float lr, uint64_t seed, pd_ws_stats* out,
+                      void* stream);
+/* Master parameters (host, PD_WS_NPARAMS floats) out of / into the context. */
+pd_status pd_ws_get_params(pd_ctx* ctx, float* params);
+pd_status pd_ws_set_params(pd_ctx* ctx, const float* params);
+/* Network output for n feature rows (host n x PD_WS_NFEAT floats, rounded to
+ * bf16 on the way in) into y (host, n). */
+pd_status pd_ws_forward(pd_ctx* ctx, const float* feats, int64_t n, float* y, void* stream);
+/* Loss sum_i mask_i (y_i - t_i)^2 / n and its gradient with respect to the
+ * master parameters (host, PD_WS_NPARAMS), as the training step computes it
+ * (bf16 weights and features, float32 arithmetic).  mask may be NULL (all 1). */
+pd_status pd_ws_grad(pd_ctx* ctx, const float* feats, const float* target, const float* mask, int64_t n,
+                     float* grad, float* loss, void* stream);
+/* Parameters to / from a file (a 16-byte header, then the floats). */
+pd_status pd_ws_save(pd_ctx* ctx, const char* path);
+pd_status pd_ws_load(pd_ctx* ctx, const char* path);
 
 /*
  * Allocation-free min-cost flow (no counterpart in the paper).

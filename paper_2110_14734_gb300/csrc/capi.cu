@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "mlp.cuh"
 #include "netsimplex.cuh"
 #include "prims.cuh"
 
@@ -489,6 +490,39 @@ static void fill_result(const Front& f, const SolveStats& ss, pd_result* out) {
     *out = r;
 }
 
+// The warm start's greedy takes all arcs between the still unbalanced nodes
+// at once when there are at most this many (before that, rounds of top-k).
+constexpr int64_t WARM_MAX_RESIDUAL = int64_t(1) << 18;
+
+// Warm start of a prepared transportation instance (opts.warm_start): from
+// the network's prediction (1) or from the exact potentials of a cold solve
+// in `c`'s instance record (2).  *used: the start tree was installed.
+static pd_status warm_start(Ctx* c, const Front& f, W1Prep* w, const pd_opts& o, bool* used, cudaStream_t st) {
+    *used = false;
+    if (!w->ns.ready || o.warm_start == 0) return PD_OK;
+    std::vector<float> p;
+    if (o.warm_start == 1) {
+        PD_TRY(ws_predict(c, f.nodes, *w, &p, st));
+    } else if (o.warm_start == 2) {
+        NSInst* d = bufT<NSInst>(c, B_NS_INST, 1);
+        if (!d) return PD_ENOMEM;
+        NSInst r{};
+        PD_TRY(ns_run(c, &w->ns.h, 1, w->ns.smem, d, &r, st));
+        PD_TRY(ns_status(c, r));
+        const int64_t nt = w->nt;
+        std::vector<int64_t> pi((size_t)nt);
+        PD_TRY_CUDA(c, cudaMemcpyAsync(pi.data(), r.pi, sizeof(int64_t) * nt, cudaMemcpyDeviceToHost, st));
+        PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+        p.resize((size_t)nt);
+        for (int64_t v = 0; v < nt; v++) p[(size_t)v] = (float)(pi[(size_t)v] - pi[(size_t)(nt - 1)]);
+    } else if (o.warm_start == 3) {
+        p.assign((size_t)w->nt, 0.f);  // all potentials 0: the greedy ranks arcs by cost alone
+    } else {
+        return fail(c, PD_EINVAL, "warm_start must be 0, 1, 2 or 3");
+    }
+    return ns_warm_tree(c, &w->ns, p.data(), WARM_MAX_RESIDUAL, used, st);
+}
+
 static float elapsed_ms(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -505,6 +539,7 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
     const long long launches0 = launch_count_ref();
     const auto t0 = std::chrono::steady_clock::now();
     Front f;
+    bool warm_used = false;
     const bool transport = o.solver != 1 && o.ns_transport != 0;
     PD_TRY(front_half(c, A, B, eps, o, &f, st, transport));
     const auto t1 = std::chrono::steady_clock::now();
@@ -515,9 +550,13 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
         W1Prep w;
         if (transport) PD_TRY(ns_prepare_w1(c, f.nodes, f.net.n_arcs, f.h.FB - f.h.FA, o, &w, st));
         if (w.ns.ready) {
+            bool used = false;
+            PD_TRY(warm_start(c, f, &w, o, &used, st));
+            warm_used = used;
             NSInst* d = bufT<NSInst>(c, B_NS_INST, 1);
             if (!d) return PD_ENOMEM;
             NSInst r{};
+            if (o.warm_start == 2) c->last_ns_ms = 0.f;  // report the warm solve only
             PD_TRY(ns_run(c, &w.ns.h, 1, w.ns.smem, d, &r, st));
             PD_TRY(ns_finish_w1(c, f.tree, f.s, nullptr, o, w, d, r, &ss, st));
         }
@@ -543,6 +582,7 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
     out->stage_ms[7] = elapsed_ms(t0);
     out->kernel_launches = launch_count_ref() - launches0;
     out->ns_kernel_ms = c->last_ns_ms;
+    out->warm_used = warm_used ? 1 : 0;
     return PD_OK;
 }
 
@@ -554,6 +594,7 @@ struct BatchPair {
     W1Prep w;
     WsTree tree{};      // slot copies of the node coordinates and the WSPD tree
     bool done = false;  // solved during preprocessing (no transportation form)
+    bool warm = false;  // starts from a warm-start tree
     SolveStats ss;
     float front_ms = 0.f, solve_ms = 0.f;
     long long launches = 0;
@@ -611,6 +652,13 @@ static pd_status batch_prepare(Ctx* work, Ctx* slot, const pd_diagram& A, const 
     if (transport)
         PD_TRY(ns_prepare_w1(slot, bp->f.nodes, bp->f.net.n_arcs, bp->f.h.FB - bp->f.h.FA, o, &bp->w, st));
     if (bp->w.ns.ready) {
+        if (o.warm_start == 1) {
+            std::vector<float> p;
+            PD_TRY(ws_predict(work, bp->f.nodes, bp->w, &p, st));
+            PD_TRY(ns_warm_tree(slot, &bp->w.ns, p.data(), WARM_MAX_RESIDUAL, &bp->warm, st));
+        } else if (o.warm_start != 0) {
+            return fail(work, PD_EINVAL, "the batched solve takes warm_start 0 or 1");
+        }
         PD_TRY(persist_for_certificate(slot, bp->f, bp, st));
     } else {
         const auto t1 = std::chrono::steady_clock::now();
@@ -661,6 +709,8 @@ pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t 
         }
         c->workers.push_back(wk);
     }
+    for (Ctx* wk : c->workers) wk->mlp_owner = c;  // predictions use this context's network
+    if (o.warm_start == 1 && !c->mlp_ready) return fail(c, PD_EINVAL, "warm_start = 1 needs a trained network");
     NSInst* d = bufT<NSInst>(c, B_NS_INST, W);
     if (!d) return PD_ENOMEM;
     // the workers start after everything already queued on the caller's stream
@@ -767,6 +817,7 @@ pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t 
             res.stage_ms[7] = p.front_ms + p.solve_ms;
             res.kernel_launches = p.launches;
             res.ns_kernel_ms = (p.done ? 0.f : wave_ns) + sl->last_ns_ms;
+            res.warm_used = p.warm ? 1 : 0;
         }
     }
     cudaEventDestroy(ready);
@@ -774,3 +825,75 @@ pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t 
 }
 
 }  // namespace pd
+
+extern "C" pd_status pd_ws_train(pd_ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t n_pairs, double eps,
+                                 const pd_opts* opts, int32_t epochs, float lr, uint64_t seed, pd_ws_stats* out,
+                                 void* stream) {
+    if (!c || !out || n_pairs < 0 || (n_pairs > 0 && (!A || !B)) || epochs < 0 || !(lr > 0.f)) return PD_EINVAL;
+    c->err.clear();
+    pd_opts o = resolve_opts(opts);
+    o.warm_start = 0;
+    if (!(eps > 0.0) && o.s_override <= 0) return fail(c, PD_EINVAL, "eps must be > 0 (or set s_override)");
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    pd_ws_stats r;
+    memset(&r, 0, sizeof(r));
+    PD_TRY(mlp_init(c, seed, false, st));
+    // the data set: at most one row per point of every pair
+    int64_t cap = 0;
+    for (int64_t i = 0; i < n_pairs; i++) cap += std::max<int64_t>(A[i].n, 0) + std::max<int64_t>(B[i].n, 0);
+    cap = std::max<int64_t>(cap, 1);
+    if (!bufT<__nv_bfloat16>(c, B_WS_DF, cap * WS_IN) || !bufT<float>(c, B_WS_DT, cap) ||
+        !bufT<float>(c, B_WS_DM, cap))
+        return PD_ENOMEM;
+    c->ws_cap = cap;
+    c->ws_rows = 0;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int64_t i = 0; i < n_pairs; i++) {
+        Front f;
+        PD_TRY(front_half(c, A[i], B[i], eps, o, &f, st, true));
+        W1Prep w;
+        PD_TRY(ns_prepare_w1(c, f.nodes, f.net.n_arcs, f.h.FB - f.h.FA, o, &w, st));
+        if (!w.ns.ready) continue;
+        NSInst* d = bufT<NSInst>(c, B_NS_INST, 1);
+        if (!d) return PD_ENOMEM;
+        NSInst rec{};
+        PD_TRY(ns_run(c, &w.ns.h, 1, w.ns.smem, d, &rec, st));
+        PD_TRY(ns_status(c, rec));
+        const int64_t cmax = (rec.big - 1) / (int64_t)(rec.n + 1) - 1;
+        PD_TRY(ws_collect(c, f.nodes, w, d, rec, cmax, st));
+        r.pairs++;
+        r.cold_pivots += rec.pivots;
+    }
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    r.collect_ms = elapsed_ms(t0);
+    r.rows = c->ws_rows;
+    const auto t1 = std::chrono::steady_clock::now();
+    float* g = bufT<float>(c, B_MLP_G, WS_PART);
+    if (!g) return PD_ENOMEM;
+    const int64_t R = c->ws_rows, bs = 2048;
+    const __nv_bfloat16* F = (const __nv_bfloat16*)c->ptr[B_WS_DF];
+    const float* T = (const float*)c->ptr[B_WS_DT];
+    const float* M = (const float*)c->ptr[B_WS_DM];
+    for (int32_t e = 0; e < epochs && R > 0; e++) {
+        for (int64_t r0 = 0; r0 < R; r0 += bs) {
+            const int64_t nb = std::min<int64_t>(bs, R - r0);
+            PD_TRY(mlp_grad(c, F + r0 * WS_IN, T + r0, M + r0, nb, 1.f / (float)nb, g, st));
+            const bool first = r.steps == 0, last = e == epochs - 1 && r0 + bs >= R;
+            if (first || last) {
+                float lm[2];
+                PD_TRY_CUDA(c, cudaMemcpyAsync(lm, g + WS_NPARAMS, sizeof(lm), cudaMemcpyDeviceToHost, st));
+                PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+                const float l = lm[0] / (float)nb;
+                if (first) r.loss_first = l;
+                if (last) r.loss_last = l;
+            }
+            PD_TRY(mlp_adam(c, g, lr, st));
+            r.steps++;
+        }
+    }
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    r.train_ms = elapsed_ms(t1);
+    *out = r;
+    return PD_OK;
+}

@@ -30,6 +30,9 @@ enum Buf : int {
     B_NS_PATH, B_NS_SEG, B_NS_INST, B_NS_ORDER, B_NS_COST, B_TR_S, B_TR_T, B_TR_SUP, B_TR_XCOST,
     B_DB_SXY, B_DB_SCNT, B_DB_SID,  // nearest-neighbour database: staging
     B_DB_XY, B_DB_CNT, B_DB_ID, B_DB_OFF, B_DB_ROFF, B_Q_XY, B_Q_CNT, B_DB_LA, B_DB_BIG,
+    B_MLP_P, B_MLP_M, B_MLP_V, B_MLP_WB, B_MLP_PART, B_MLP_G,  // warm-start network
+    B_WS_GRID, B_WS_FEAT, B_WS_Y, B_WS_PS, B_WS_BOX, B_WS_DF, B_WS_DT, B_WS_DM, B_WS_IN, B_WS_TIN, B_WS_MIN,
+    B_WS_P, B_WS_ROWK, B_WS_COLK, B_WS_ARCS, B_WS_COST, B_WS_RS, B_WS_RT, B_WS_RC, B_WS_COMP, B_WS_CSIZE, B_WS_CSUM,
     B_SMALL,                        // small device scalars
     B_COUNT
 };
@@ -56,6 +59,12 @@ struct Ctx {
     int64_t db_total = 0;
     int db_k = 0, db_dtype = 0;
     bool db_big = false;  // a database coordinate is not exact in float32
+    // warm-start network: parameters in B_MLP_* (of mlp_owner when set, as
+    // for the batch workers), training rows in B_WS_DF / DT / DM
+    bool mlp_ready = false;
+    int64_t mlp_steps = 0;
+    int64_t ws_rows = 0, ws_cap = 0;
+    Ctx* mlp_owner = nullptr;
 };
 
 Ctx* ctx_new(int device, size_t cap);  // nullptr on failure

@@ -116,8 +116,22 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
     __shared__ int32_t sseg[3][NS_SEGSM];
     const int32_t SEGN = 2 * n + 3;
 
-    // ---- initial tree: the root star --------------------------------------
-    for (int32_t i = tid; i < n; i += NS_THREADS) {
+    // ---- initial tree: the one given in the record, or the root star -----
+    if (I.init_tree) {
+        for (int32_t v = tid; v < N1; v += NS_THREADS) {
+            const int32_t f = G.flow[v];
+            const bool u = G.up[v] != 0;
+            T.pi[v] = G.pi[v];
+            T.pred[v] = G.pred[v];
+            T.set_parent(v, G.parent[v]);
+            T.sz[v] = (IX)G.size[v];
+            T.ps[v] = (IX)G.pos[v];
+            T.od[v] = (IX)G.ord[v];
+            T.set_fu(v, f, u);
+        }
+        if (tid == 0) s_status = 0;
+    }
+    for (int32_t i = tid; i < n && !I.init_tree; i += NS_THREADS) {
         int64_t s = I.supply[i];
         T.set_parent(i, root);
         T.pred[i] = (int32_t)(I.m + i);
@@ -127,7 +141,7 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
         T.ps[i] = (IX)(1 + i);
         T.sz[i] = (IX)1;
     }
-    if (tid == 0) {
+    if (tid == 0 && !I.init_tree) {
         T.set_parent(root, -1);
         T.pred[root] = -1;
         T.set_fu(root, 0, false);
@@ -157,6 +171,14 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
         while (scanned < M) {
             const int64_t aend = a0 + B < M ? a0 + B : M;
             const int64_t len = aend - a0;
+            {
+                // the costs never change: pull the next block into L2 while this
+                // one is priced (and, when this block has the entering arc,
+                // while the pivot runs)
+                const int64_t pf = (aend >= M ? 0 : aend) + 8 * (int64_t)tid;
+                if (pf + 8 <= I.mst && 8 * (int64_t)tid < B)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(I.cmat + pf));
+            }
             int64_t lb = 0, li = -1;
             for (int64_t c0 = a0 + 8 * (int64_t)tid; c0 < aend; c0 += 8 * NS_THREADS) {
                 if (c0 + 8 <= aend && c0 + 8 <= I.mst) {

@@ -37,6 +37,8 @@ struct NSInst {
     int64_t big;       // cost of the artificial arcs (more than any path cost)
     int32_t smem_nodes; // 1: hot node arrays live in shared memory
     int32_t vec_explicit; // 1: tail, head and cost are 16-byte aligned (vector loads)
+    int32_t init_tree;  // 1: pi, pred, parent, flow, up, ord, pos, size hold a strongly feasible start
+    int32_t pad1;
     int64_t scanned;   // result: arcs priced
     int64_t max_pivots;
     uint64_t time_limit_ns;

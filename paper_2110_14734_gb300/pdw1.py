@@ -37,7 +37,7 @@ class pd_opts(C.Structure):
                 ("seq_threshold", C.c_int32), ("solver", C.c_int32), ("ns_block", C.c_int64),
                 ("ns_transport", C.c_int32), ("ns_smem", C.c_int32), ("batch_slots", C.c_int32),
                 ("batch_threads", C.c_int32),
-                ("nn_prune", C.c_int32), ("reserved1", C.c_int32)]
+                ("nn_prune", C.c_int32), ("warm_start", C.c_int32)]
 
 
 class pd_nodes(C.Structure):
@@ -61,7 +61,7 @@ class pd_result(C.Structure):
                 ("pivots", C.c_int64), ("degenerate", C.c_int64), ("arcs_priced", C.c_int64),
                 ("solve_method", C.c_int32),
                 ("cert_failures", C.c_int32), ("kernel_launches", C.c_int64), ("ns_kernel_ms", C.c_float),
-                ("reserved", C.c_int32), ("stage_ms", C.c_float * 8)]
+                ("warm_used", C.c_int32), ("stage_ms", C.c_float * 8)]
 
     def to_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "stage_ms"}
@@ -73,6 +73,19 @@ class pd_nn_result(C.Structure):
     _fields_ = [("nn_index", C.c_int64), ("nn_opt_quanta", C.c_int64), ("nn_w1", C.c_double),
                 ("solved", C.c_int64), ("pruned", C.c_int64), ("waves", C.c_int32), ("coord_shift", C.c_int32),
                 ("lb_ms", C.c_float), ("solve_ms", C.c_float), ("total_ms", C.c_float), ("reserved", C.c_int32)]
+
+    def to_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+WS_NFEAT = 68
+WS_NPARAMS = 25473
+
+
+class pd_ws_stats(C.Structure):
+    _fields_ = [("rows", C.c_int64), ("pairs", C.c_int32), ("steps", C.c_int32), ("loss_first", C.c_float),
+                ("loss_last", C.c_float), ("collect_ms", C.c_float), ("train_ms", C.c_float),
+                ("cold_pivots", C.c_int64)]
 
     def to_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -111,6 +124,24 @@ _lib.pd_db_build.argtypes = [C.c_void_p, C.POINTER(pd_diagram), C.c_int64, C.POI
 _lib.pd_nn_search.restype = C.c_int
 _lib.pd_nn_search.argtypes = [C.c_void_p, pd_diagram, C.c_double, C.POINTER(pd_opts), C.POINTER(pd_nn_result),
                               C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_void_p]
+
+_F32P = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+_lib.pd_ws_train.restype = C.c_int
+_lib.pd_ws_train.argtypes = [C.c_void_p, C.POINTER(pd_diagram), C.POINTER(pd_diagram), C.c_int64, C.c_double,
+                             C.POINTER(pd_opts), C.c_int32, C.c_float, C.c_uint64, C.POINTER(pd_ws_stats), C.c_void_p]
+_lib.pd_ws_get_params.restype = C.c_int
+_lib.pd_ws_get_params.argtypes = [C.c_void_p, _F32P]
+_lib.pd_ws_set_params.restype = C.c_int
+_lib.pd_ws_set_params.argtypes = [C.c_void_p, _F32P]
+_lib.pd_ws_forward.restype = C.c_int
+_lib.pd_ws_forward.argtypes = [C.c_void_p, _F32P, C.c_int64, _F32P, C.c_void_p]
+_lib.pd_ws_grad.restype = C.c_int
+_lib.pd_ws_grad.argtypes = [C.c_void_p, _F32P, _F32P, C.c_void_p, C.c_int64, _F32P, C.POINTER(C.c_float),
+                            C.c_void_p]
+_lib.pd_ws_save.restype = C.c_int
+_lib.pd_ws_save.argtypes = [C.c_void_p, C.c_char_p]
+_lib.pd_ws_load.restype = C.c_int
+_lib.pd_ws_load.argtypes = [C.c_void_p, C.c_char_p]
 
 _lib.pd_mcf_solve_noalloc.restype = C.c_int
 _lib.pd_mcf_solve_noalloc.argtypes = [C.POINTER(pd_network), C.POINTER(C.c_int64), C.c_void_p]
@@ -334,6 +365,60 @@ def pd_nn_search(ctx: Context, query, eps: float, o: pd_opts | None = None, stre
     d["opt"] = [int(opt[i]) for i in range(n)]
     d["lb"] = [int(lb[i]) for i in range(n)]
     return d
+
+
+def pd_ws_train(ctx: Context, As, Bs, eps: float, o: pd_opts | None = None, epochs: int = 20, lr: float = 1e-3,
+                seed: int = 0, stream=None) -> dict:
+    """Train the context's warm-start network on cold solves of the pairs."""
+    n = len(As)
+    da = (pd_diagram * max(n, 1))()
+    db = (pd_diagram * max(n, 1))()
+    keep = []
+    for i in range(n):
+        da[i], ka = diagram(As[i])
+        db[i], kb = diagram(Bs[i])
+        keep += [ka, kb]
+    st = pd_ws_stats()
+    ctx.check(_lib.pd_ws_train(ctx.ptr, da, db, n, float(eps), C.byref(o) if o else None, int(epochs), float(lr),
+                               int(seed), C.byref(st), C.c_void_p(_stream(stream))))
+    return st.to_dict()
+
+
+def pd_ws_get_params(ctx: Context) -> np.ndarray:
+    p = np.zeros(WS_NPARAMS, np.float32)
+    ctx.check(_lib.pd_ws_get_params(ctx.ptr, p))
+    return p
+
+
+def pd_ws_set_params(ctx: Context, p) -> None:
+    ctx.check(_lib.pd_ws_set_params(ctx.ptr, np.ascontiguousarray(p, np.float32)))
+
+
+def pd_ws_forward(ctx: Context, feats) -> np.ndarray:
+    f = np.ascontiguousarray(feats, np.float32).reshape(-1, WS_NFEAT)
+    y = np.zeros(len(f), np.float32)
+    ctx.check(_lib.pd_ws_forward(ctx.ptr, f, len(f), y, C.c_void_p(_stream(None))))
+    return y
+
+
+def pd_ws_grad(ctx: Context, feats, target, mask=None):
+    """(loss, gradient of the master parameters) on the device."""
+    f = np.ascontiguousarray(feats, np.float32).reshape(-1, WS_NFEAT)
+    t = np.ascontiguousarray(target, np.float32)
+    m = None if mask is None else np.ascontiguousarray(mask, np.float32)
+    g = np.zeros(WS_NPARAMS, np.float32)
+    loss = C.c_float()
+    ctx.check(_lib.pd_ws_grad(ctx.ptr, f, t, m.ctypes.data_as(C.c_void_p) if m is not None else None, len(f), g,
+                              C.byref(loss), C.c_void_p(_stream(None))))
+    return float(loss.value), g
+
+
+def pd_ws_save(ctx: Context, path: str) -> None:
+    ctx.check(_lib.pd_ws_save(ctx.ptr, path.encode()))
+
+
+def pd_ws_load(ctx: Context, path: str) -> None:
+    ctx.check(_lib.pd_ws_load(ctx.ptr, path.encode()))
 
 
 def pd_w1_approx_raw(ctx: Context, da: pd_diagram, db: pd_diagram, eps: float, o, res: pd_result, stream: int):

@@ -588,3 +588,39 @@ def test_nn_search_ties_and_dense_limit(orc):
     assert opts2 == dense
     assert idx2 == min(range(len(dense)), key=lambda i: (dense[i], i))
     assert orc.nn_search(q2, [], "f32") == (-1, [])
+
+
+def test_warm_start_network_oracle_gradient_and_bf16():
+    """The warm-start network's oracle: its gradient equals central finite
+    differences of its loss (float64, no rounding), and its bf16 rounding
+    equals torch's float32 -> bfloat16 conversion."""
+    torch = pytest.importorskip("torch")
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    p = (rng.standard_normal(mlp.NPARAMS) * 0.15).astype(np.float32)
+    x = rng.standard_normal((24, mlp.NIN)).astype(np.float32)
+    t = rng.standard_normal(24).astype(np.float32)
+    m = (rng.random(24) < 0.8).astype(np.float32)
+    loss, g = mlp.loss_grad(p, x, t, m, round_inputs=False)
+    idx = np.concatenate([rng.choice(mlp.NPARAMS, 150, replace=False),
+                          np.arange(mlp.OFF_B1, mlp.OFF_B1 + 5), np.arange(mlp.OFF_W3, mlp.OFF_W3 + 5),
+                          [mlp.OFF_B3]])
+    pd64 = p.astype(np.float64)
+
+    def L(q):
+        W1 = q[mlp.OFF_W1:mlp.OFF_B1].reshape(mlp.NIN, mlp.NH)
+        h1 = np.maximum(x.astype(np.float64) @ W1 + q[mlp.OFF_B1:mlp.OFF_W2], 0)
+        h2 = np.maximum(h1 @ q[mlp.OFF_W2:mlp.OFF_B2].reshape(mlp.NH, mlp.NH) + q[mlp.OFF_B2:mlp.OFF_W3], 0)
+        y = h2 @ q[mlp.OFF_W3:mlp.OFF_B3] + q[mlp.OFF_B3]
+        return np.sum(m * (y - t) ** 2) / len(y)
+
+    assert abs(L(pd64) - loss) < 1e-12 * max(1, abs(loss))
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(pd64)
+        e[i] = h
+        fd = (L(pd64 + e) - L(pd64 - e)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(fd), (i, fd, g[i])
+    v = rng.standard_normal(1000).astype(np.float32) * 100
+    ref = torch.from_numpy(v).to(torch.bfloat16).float().numpy().astype(np.float64)
+    np.testing.assert_array_equal(mlp.bf16(v), ref)
