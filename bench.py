@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--diagrams", type=int, default=26, help="seeded diagrams; steps cycle over their pairs")
     ap.add_argument("--plain-pairs", type=int, default=3, help="pairs timed through the one-pair path")
     ap.add_argument("--threads", type=int, default=0, help="host threads preprocessing pairs (0 = library default)")
+    ap.add_argument("--warm-pairs", type=int, default=2, help="pairs timed with the learned warm start (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -188,6 +189,21 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def replica_totals(local_ms, local_units, device=None):
+    """Whole-job timing over replicas: the slowest rank's timed-region duration
+    (max over ranks) and the units all ranks processed (sum).  Without an
+    initialised process group, the local values."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(local_ms), float(local_units)
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def _gen(args):
     from paper_2110_14734_gb300 import synth
     return synth.lowerstar_u8(*args)
@@ -270,12 +286,7 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    pairs = args.steps * P * ws
+    tot_ms, pairs = replica_totals(sum(step_ms), args.steps * P, dev)
     value = pairs / (tot_ms / 1000.0)
 
     # ---- the plain one-pair path, one pair after the other ------------------
@@ -292,6 +303,37 @@ def run_ours(args):
         if st != 0:
             raise pdw1.PDError(st, pdw1._lib.pd_last_error(ctx.ptr).decode())
         plain_ms.append(a.elapsed_time(b))
+
+    # ---- warm start: network trained on cold solves of 4 pool pairs, timed
+    # on pairs it has not seen (one pair per call), beside the cold path ------
+    warm = None
+    if args.warm_pairs > 0 and len(pairs_all) >= 4 + args.warm_pairs:
+        tr = pairs_all[-4:]
+        st = pdw1.pd_ws_train(ctx, [dev_t[i] for i, _ in tr], [dev_t[j] for _, j in tr], args.eps, epochs=600,
+                              lr=5e-4, seed=1)
+        rows = []
+        for q in range(args.warm_pairs):
+            i, j = pairs_all[q]
+            for mode in (0, 1, 2):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                s2 = pdw1.pd_w1_approx_raw(ctx, dev_d[i], dev_d[j], args.eps, pdw1.opts(warm_start=mode), one, sptr)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if s2 != 0:
+                    raise pdw1.PDError(s2, pdw1._lib.pd_last_error(ctx.ptr).decode())
+                rows.append((mode, a.elapsed_time(b), one.pivots, one.opt_quanta, one.warm_used))
+        def agg(mode):
+            sel = [r for r in rows if r[0] == mode]
+            return statistics.mean(r[1] for r in sel), sum(r[2] for r in sel)
+        (cm, cp), (wm, wp), (em, ep) = agg(0), agg(1), agg(2)
+        same = len({(r[3]) for r in rows if r[0] != 0} - {r[3] for r in rows if r[0] == 0}) == 0
+        warm = {"value": 1000.0 / wm, "unit": UNIT, "pairs": args.warm_pairs,
+                "form": "pd_w1_approx with warm_start=1 (network trained on 4 other pool pairs), one pair per call",
+                "cold_value": 1000.0 / cm, "pivots_cold": cp, "pivots_warm": wp,
+                "exact_potentials_value": 1000.0 / em, "pivots_exact_potentials": ep,
+                "same_optimum": same, "train_rows": st["rows"], "train_loss_last": st["loss_last"]}
 
     # ---- end to end through the C ABI with pinned host buffers -------------
     e2e_steps = max(1, min(args.e2e_steps, args.steps))
@@ -335,6 +377,7 @@ def run_ours(args):
             "plain": {"value": 1000.0 / statistics.mean(plain_ms), "unit": UNIT, "pairs": len(plain_ms),
                       "ms_per_pair": statistics.mean(plain_ms),
                       "form": "pd_w1_approx, one pair per call, device-resident inputs"},
+            "warm_start": warm,
             "e2e": {"value": e2e_steps * P / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps},
             "gpu_launches": launches,

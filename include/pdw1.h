@@ -88,8 +88,8 @@ typedef struct {
     int64_t ns_block;       /* network simplex pricing block in arcs (0 = max(8192, sqrt(arcs))) */
     int32_t ns_transport;   /* W1 only: 1 = try the transportation form with its certificate first (default) */
     int32_t ns_smem;        /* network simplex: 1 = hot node arrays in shared memory when they fit (default) */
-    int32_t batch_slots;    /* pairs per simplex launch (pd_w1_approx_batch: 0 = twice the number of SMs;
-                               pd_nn_search: 0 = the number of SMs) */
+    int32_t batch_slots;    /* pairs per simplex launch of pd_w1_approx_batch and pd_nn_search
+                               (0 = twice the number of SMs) */
     int32_t batch_threads;  /* pd_w1_approx_batch: host threads preprocessing pairs (0 = 8) */
     int32_t nn_prune;       /* pd_nn_search: 1 = skip pairs whose lower bound exceeds the best optimum
                                (default); 0 = solve every pair */

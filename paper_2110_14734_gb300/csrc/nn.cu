@@ -344,7 +344,7 @@ extern "C" pd_status pd_nn_search(pd_ctx* cx, pd_diagram query, double eps, cons
     std::vector<int64_t> order((size_t)n_db), opt((size_t)n_db, -1);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return lb[(size_t)x] < lb[(size_t)y]; });
-    const int64_t W = o.batch_slots > 0 ? o.batch_slots : std::max(c->sm_count, 1);
+    const int64_t W = o.batch_slots > 0 ? o.batch_slots : 2 * std::max(c->sm_count, 1);
     int64_t best = INT64_MAX, best_i = -1, pos = 0;
     std::vector<pd_diagram> qa, db;
     std::vector<pd_result> res;
