@@ -265,8 +265,11 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
             // for the second pass, which writes each match at its rank.
             const int32_t pi_ = T.ps[i], pj = T.ps[j];
             const int32_t C = (((N1 + 31) / 32) + 31) & ~31;  // positions per warp, <= 32 * NS_REGS
-            const int32_t iters = C >> 5;
             const int32_t x0 = wid * C;
+            // an ancestor's position is at most the descendant's: no warp looks
+            // past max(pos(i), pos(j))
+            const int32_t xmax = pi_ > pj ? pi_ : pj;
+            const int32_t iters = xmax < x0 ? 0 : min(C >> 5, ((xmax - x0) >> 5) + 1);
             int32_t cI = 0, cJ = 0;
             for (int32_t it = 0; it < iters; it++) {
                 const int32_t x = x0 + (it << 5) + lane;
@@ -295,8 +298,10 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
             int32_t oJ = __reduce_add_sync(FULL, lane < wid ? mJ : 0);
             const int32_t la = __reduce_add_sync(FULL, mI), lb = __reduce_add_sync(FULL, mJ);
             const uint32_t below = (1u << lane) - 1u;
-            for (int32_t it = 0; it < iters; it++) {
+            const int32_t iters2 = (s_cnt[0][wid] + s_cnt[1][wid]) > 0 ? iters : 0;  // warps without a match skip
+            for (int32_t it = 0; it < iters2; it++) {
                 const uint32_t bI = s_mask[0][wid][it], bJ = s_mask[1][wid][it];
+                if ((bI | bJ) == 0) continue;
                 const int32_t x = x0 + (it << 5) + lane;
                 if ((bI >> lane) & 1u) {
                     const int32_t t = la - 1 - (oI + __popc(bI & below));
@@ -350,41 +355,35 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
             // cycle -- on the i-side the one closest to i (smallest index), on
             // the j-side the one closest to the apex (largest index), j-side
             // preferred on ties.
-            int32_t fi = INT32_MAX, ti = INT32_MAX, fj = INT32_MAX, tj = -1;
+            uint32_t li_f = 0xffffffffu, li_t = 0xffffffffu;  // i-side: smallest flow, then smallest index
+            int32_t lj_f = INT32_MAX, lj_t = -1;                // j-side: smallest flow, then largest index
             for (int32_t t = lane; t < la; t += 32) {
-                int32_t x = PA(t);
-                if (T.up(x)) {
-                    int32_t f = T.flow(x);
-                    if (f < fi || (f == fi && t < ti)) {
-                        fi = f;
-                        ti = t;
+                const uint32_t w = T.fu[PA(t)];
+                if (w >> 31) {  // points up: against the cycle on the i-side
+                    const uint32_t f = w & 0x7fffffffu;
+                    if (f < li_f) {  // t grows within a lane: ties keep the smaller index
+                        li_f = f;
+                        li_t = (uint32_t)t;
                     }
                 }
             }
             for (int32_t t = lane; t < lb; t += 32) {
-                int32_t x = PB(t);
-                if (!T.up(x)) {
-                    int32_t f = T.flow(x);
-                    if (f < fj || (f == fj && t > tj)) {
-                        fj = f;
-                        tj = t;
+                const uint32_t w = T.fu[PB(t)];
+                if (!(w >> 31)) {
+                    const int32_t f = (int32_t)w;
+                    if (f <= lj_f) {  // ties take the larger index
+                        lj_f = f;
+                        lj_t = t;
                     }
                 }
             }
-            for (int off = 16; off > 0; off >>= 1) {
-                int32_t of = __shfl_xor_sync(FULL, fi, off);
-                int32_t ot = __shfl_xor_sync(FULL, ti, off);
-                if (of < fi || (of == fi && ot < ti)) {
-                    fi = of;
-                    ti = ot;
-                }
-                of = __shfl_xor_sync(FULL, fj, off);
-                ot = __shfl_xor_sync(FULL, tj, off);
-                if (of < fj || (of == fj && ot > tj)) {
-                    fj = of;
-                    tj = ot;
-                }
-            }
+            const uint32_t mfi = __reduce_min_sync(FULL, li_f);
+            const uint32_t mti = __reduce_min_sync(FULL, li_f == mfi ? li_t : 0xffffffffu);
+            const int32_t mfj = (int32_t)__reduce_min_sync(FULL, (uint32_t)lj_f);
+            const int32_t mtj = __reduce_max_sync(FULL, lj_f == mfj ? lj_t : -1);
+            const int32_t fi = mfi == 0xffffffffu ? INT32_MAX : (int32_t)mfi;
+            const int32_t ti = mti == 0xffffffffu ? INT32_MAX : (int32_t)mti;
+            const int32_t fj = mfj, tj = mtj;
             int side;
             int32_t delta, tl;
             if (la < 0 || lb < 0) {
