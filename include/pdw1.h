@@ -97,7 +97,9 @@ typedef struct {
                                1 = start from the potentials predicted by the context's network
                                (pd_ws_train / pd_ws_load); 2 = start from the exact potentials of a
                                cold solve of the same pair (diagnostic: the best a prediction can do);
-                               3 = start from potentials 0 (the greedy on costs alone, no network) */
+                               3 = start from the potentials +d(u) for sources, -d(v) for sinks (d: the
+                               distance to the diagonal), i.e. the greedy by the saving
+                               d(u) + d(v) - c(u, v) of pairing u with v (no network) */
 } pd_opts;
 
 void pd_opts_default(pd_opts* opts);

@@ -516,7 +516,7 @@ static pd_status warm_start(Ctx* c, const Front& f, W1Prep* w, const pd_opts& o,
         p.resize((size_t)nt);
         for (int64_t v = 0; v < nt; v++) p[(size_t)v] = (float)(pi[(size_t)v] - pi[(size_t)(nt - 1)]);
     } else if (o.warm_start == 3) {
-        p.assign((size_t)w->nt, 0.f);  // all potentials 0: the greedy ranks arcs by cost alone
+        PD_TRY(ws_diag_potentials(c, f.nodes, *w, &p, st));  // the greedy ranks arcs by their saving
     } else {
         return fail(c, PD_EINVAL, "warm_start must be 0, 1, 2 or 3");
     }

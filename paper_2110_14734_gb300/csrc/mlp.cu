@@ -137,6 +137,36 @@ __global__ void k_targets(const int64_t* __restrict__ pi, const int32_t* __restr
     mask[r] = ok ? 1.f : 0.f;
 }
 
+// Potentials from the distance to the diagonal: +d(u) for a source, -d(v)
+// for a sink, 0 for the diagonal node, so that the reduced cost of an arc is
+// c(u, v) - d(u) - d(v) <= 0: minus the saving of sending u to v instead of
+// both to the diagonal.
+__global__ void k_diag_potentials(const int32_t* __restrict__ X, const int32_t* __restrict__ Y,
+                                  const int32_t* __restrict__ S, const int32_t* __restrict__ T, int64_t nS, int64_t nT,
+                                  float* __restrict__ p) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r > nS + nT) return;
+    if (r == nS + nT) {
+        p[r] = 0.f;
+        return;
+    }
+    const int32_t u = r < nS ? S[r] : T[r - nS];
+    const float d = (float)cost_diag(X[u], Y[u]);
+    p[r] = r < nS ? d : -d;
+}
+
+pd_status ws_diag_potentials(Ctx* c, const pd_nodes& nodes, const W1Prep& w, std::vector<float>* p, cudaStream_t st) {
+    const int64_t n = w.nS + w.nT;
+    float* dp = bufT<float>(c, B_WS_PS, n + 1);
+    if (!dp) return PD_ENOMEM;
+    k_diag_potentials<<<grid_for(n + 1, 256), 256, 0, st>>>(nodes.X, nodes.Y, w.S, w.T, w.nS, w.nT, dp); pd::count_launch();
+    PD_TRY_CUDA(c, cudaGetLastError());
+    p->resize((size_t)(n + 1));
+    PD_TRY_CUDA(c, cudaMemcpyAsync(p->data(), dp, sizeof(float) * (n + 1), cudaMemcpyDeviceToHost, st));
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    return PD_OK;
+}
+
 // ---------------------------------------------------------------------------
 // the network: tiles of WS_TILE nodes, thread j owns hidden unit j
 // ---------------------------------------------------------------------------

@@ -36,6 +36,8 @@ pd_status mlp_adam(Ctx* c, const float* g, float lr, cudaStream_t st);
 pd_status ws_features(Ctx* c, const pd_nodes& nodes, const W1Prep& w, __nv_bfloat16* F, long long* box,
                       cudaStream_t st);
 pd_status ws_predict(Ctx* c, const pd_nodes& nodes, const W1Prep& w, std::vector<float>* p, cudaStream_t st);
+// Potentials +d(u) / -d(v) from the distance to the diagonal (host, nS + nT + 1).
+pd_status ws_diag_potentials(Ctx* c, const pd_nodes& nodes, const W1Prep& w, std::vector<float>* p, cudaStream_t st);
 pd_status ws_collect(Ctx* c, const pd_nodes& nodes, const W1Prep& w, const NSInst* d_res, const NSInst& r,
                      int64_t cmax, cudaStream_t st);
 

@@ -95,3 +95,29 @@ def test_batch_rejects_bad_arguments(pd, ctx):
     with pytest.raises(pd.PDError):
         pd.pd_w1_approx_batch(ctx, [A], [A], 0.0)
     assert pd.pd_w1_approx_batch(ctx, [], [], 0.1) == []
+
+
+def test_batch_fallback_paths(pd, ctx):
+    """Pairs solved without the transportation form (ns_transport=0: the
+    sparse network in the worker) and pairs whose certificate fails on a
+    coarse decomposition (small s: the sparse network after the shared
+    launch) give the one-pair results and the oracle's optimum."""
+    P = _pairs()[:3]
+    o = pd.opts(ns_transport=0, batch_slots=2)
+    got = pd.pd_w1_approx_batch(ctx, [_cuda(a) for a, _, _ in P], [_cuda(b) for _, b, _ in P], 0.1, o)
+    for (A, B, dt), g in zip(P, got):
+        one = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.1, o)
+        assert g["opt_quanta"] == one["opt_quanta"] == oracle.w1_approx(A, B, dt, eps=0.1)["opt"]
+        assert g["solve_method"] == one["solve_method"] == 1
+    A, B = synth.uniform_exp(700, 61), synth.uniform_exp(650, 62)
+    fails = 0
+    for s in (1, 2, 4, 13):
+        g = pd.pd_w1_approx_batch(ctx, [_cuda(A), _cuda(B)], [_cuda(B), _cuda(A)], 0.1, pd.opts(s_override=s))
+        ref = oracle.w1_approx(A, B, "f32", eps=0.1, s_override=s)["opt"]
+        assert g[0]["opt_quanta"] == ref
+        assert g[1]["opt_quanta"] == pd.pd_w1_approx(ctx, _cuda(B), _cuda(A), 0.1, pd.opts(s_override=s))["opt_quanta"]
+        fails += sum(x["cert_failures"] > 0 for x in g)
+        for x in g:
+            if x["cert_failures"] > 0:
+                assert x["solve_method"] == 1
+    assert fails > 0  # the certificate-failure fallback of the batch ran
