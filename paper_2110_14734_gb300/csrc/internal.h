@@ -26,7 +26,7 @@ enum Buf : int {
     B_S_E, B_S_P, B_S_D, B_S_CUR, B_S_RELAB, B_S_CTL, B_S_Q,
     B_RS_COUNTS, B_RS_PART, B_SCAN_PART,
     B_M_ROWPTR, B_M_SUPPLY,
-    B_NS_PI, B_NS_PARENT, B_NS_PRED, B_NS_DEPTH, B_NS_FLOW, B_NS_UP, B_NS_ORD, B_NS_POS, B_NS_SIZE, B_NS_TMP,
+    B_NS_PI, B_NS_PARENT, B_NS_PRED, B_NS_FLOW, B_NS_UP, B_NS_ORD, B_NS_POS, B_NS_SIZE, B_NS_TMP,
     B_NS_PATH, B_NS_SEG, B_NS_INST, B_NS_ORDER, B_NS_COST, B_TR_S, B_TR_T, B_TR_SUP, B_TR_XCOST,
     B_DB_SXY, B_DB_SCNT, B_DB_SID,  // nearest-neighbour database: staging
     B_DB_XY, B_DB_CNT, B_DB_ID, B_DB_OFF, B_DB_ROFF, B_Q_XY, B_Q_CNT, B_DB_LA, B_DB_BIG,

@@ -1,23 +1,27 @@
 // Primal network simplex for the uncapacitated min-cost flow, one CTA per
 // instance (the min-cost flow of the network-simplex section: block search
-// pivoting, run to optimality).
+// pivoting, run to optimality).  The kernel is persistent: each CTA takes
+// instances from a device counter, largest first.
 //
 // GPU layout.  Pricing is the parallel part: the whole CTA evaluates a block
 // of arcs (reduced cost c - pi(tail) + pi(head)) and reduces to the most
-// negative one.  The pivot is done by one warp: lanes 0 and 1 walk the two
-// half-cycles up to the apex (found with the preorder ancestor test
-// pos(a) <= pos(b) < pos(a) + size(a), so no depths are kept), then the warp
-// finds the leaving arc, changes the flow and re-roots the cut path.  The
-// spanning tree is kept as an explicit preorder array (ord, pos, size), so
-// re-hanging the cut subtree is a handful of contiguous segment moves done by
-// all threads plus one potential shift -- no pointer chasing over the subtree.
-// Up to 9216 nodes the node arrays live in shared memory with 16-bit indices
-// (24 bytes per node); larger trees keep 32-bit arrays in global memory.
+// negative one, the next block prefetched into L2.  The two half-cycles of the
+// entering arc are found by the whole CTA with the preorder ancestor test
+// pos(a) <= pos(b) < pos(a) + size(a) (a ballot scan over preorder positions;
+// no depths are kept; trees in global memory are walked by two lanes
+// instead).  One warp then finds the leaving arc, changes the flow and
+// re-roots the cut path.  The spanning tree is kept as an explicit preorder
+// array (ord, pos, size), so re-hanging the cut subtree is a handful of
+// contiguous segment moves done by all threads plus one potential shift -- no
+// pointer chasing over the subtree.  Up to 9216 nodes the node arrays live in
+// shared memory with 16-bit indices (24 bytes per node); larger trees keep
+// 32-bit arrays in global memory.
 //
 // Big-M start: node i has an artificial arc to (supply >= 0) or from (< 0) an
 // extra root; zero-flow tree arcs point to the root (strongly feasible tree),
 // and the leaving arc is the last blocking arc met when the cycle is walked
 // from the apex in the direction of the entering arc, which rules out cycling.
+// An instance may instead carry its own strongly feasible start (warm start).
 #include <algorithm>
 #include <vector>
 
