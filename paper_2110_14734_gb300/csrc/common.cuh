@@ -28,10 +28,13 @@ enum : uint32_t {
 
 constexpr int64_t COORD_LIMIT = int64_t(1) << 29;  // |quantised coordinate| < 2^29
 
-// floor(sqrt(v)) for v < 2^63: a correctly rounded double square root is at
-// most one unit away from the integer root; the two loops correct it.
+// floor(sqrt(v)) for v < 2^63: a first guess from a floating-point square
+// root, then the two loops make it exact.  Below 2^44 the float root is within
+// 0.4 of sqrt(v) (relative error < 1.5 * 2^-24 on a value < 2^22), so the loops
+// run at most once or twice and the double-precision unit is not needed;
+// above, a correctly rounded double root is at most one unit away.
 PD_D uint64_t isqrt_u64(uint64_t v) {
-    uint64_t r = (uint64_t)sqrt((double)v);
+    uint64_t r = v < (1ull << 44) ? (uint64_t)sqrtf((float)v) : (uint64_t)sqrt((double)v);
     while (r * r > v) r--;
     while ((r + 1) * (r + 1) <= v) r++;
     return r;

@@ -272,6 +272,63 @@ __global__ void k_ws_expand(const int2* __restrict__ F, int64_t nf, const int64_
     }
 }
 
+// Count-only level of the frontier: well-separated pairs are counted, the
+// others split (same rule as k_ws_expand) into the next frontier at slots
+// taken with block-aggregated atomics -- the next frontier's order may differ
+// from run to run, the counts do not.  lv[0] += well-separated pairs, lv[1] = size
+// of the next frontier (capacity 2 nf).
+__global__ void k_ws_count_split(const int2* __restrict__ F, int64_t nf, const int32_t* __restrict__ X,
+                                 const int32_t* __restrict__ Y, const int4* __restrict__ bb,
+                                 const int32_t* __restrict__ rep, const int32_t* __restrict__ left,
+                                 const int32_t* __restrict__ right, int64_t s, int2* __restrict__ Fn,
+                                 unsigned long long* __restrict__ lv) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = i < nf;
+    bool ws = false;
+    int2 p = make_int2(0, 0);
+    TNode u{}, v{};
+    if (act) {
+        p = F[i];
+        u = load_tnode(p.x, X, Y, bb, rep, left, right);
+        v = load_tnode(p.y, X, Y, bb, rep, left, right);
+        ws = well_separated(u, v, s);
+    }
+    // block-aggregated: one pair of atomics per block (same-address atomics
+    // from every warp of a level of millions of pairs would serialise)
+    __shared__ unsigned s_ws[32], s_sp[32];
+    __shared__ unsigned long long s_base;
+    const unsigned mws = __ballot_sync(0xffffffffu, act && ws), msp = __ballot_sync(0xffffffffu, act && !ws);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) {
+        s_ws[wid] = __popc(mws);
+        s_sp[wid] = __popc(msp);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tw = 0, ts = 0;
+        for (int w = 0; w < nw; w++) {
+            tw += s_ws[w];
+            const unsigned c = s_sp[w];
+            s_sp[w] = ts;  // exclusive prefix of the splits
+            ts += c;
+        }
+        if (tw) atomicAdd(&lv[0], (unsigned long long)tw);
+        s_base = ts ? atomicAdd(&lv[1], 2ull * (unsigned long long)ts) : 0ull;
+    }
+    __syncthreads();
+    if (act && !ws) {
+        const unsigned long long slot =
+            s_base + 2ull * (unsigned long long)(s_sp[wid] + __popc(msp & ((1u << lane) - 1u)));
+        if (max_side(u) > max_side(v)) {
+            Fn[slot] = make_int2(u.l, p.y);
+            Fn[slot + 1] = make_int2(u.r, p.y);
+        } else {
+            Fn[slot] = make_int2(p.x, v.l);
+            Fn[slot + 1] = make_int2(p.x, v.r);
+        }
+    }
+}
+
 // Diagonal arcs: u -> ā if u holds A mass, b̄ -> u if u holds B mass, and
 // b̄ -> ā; absent arcs become the all-ones key, which sorts last.
 __global__ void k_diag_arcs(int64_t N, const int64_t* __restrict__ cntA, const int64_t* __restrict__ cntB, int hb,
@@ -445,6 +502,20 @@ pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* ou
     uint64_t* arcs = nullptr;
     int fb = 0;
     int64_t* h = c->h_small;
+    while (count_only && nf > 0) {
+        unsigned long long* lv = cnts + 12;
+        int2* Fn = bufT<int2>(c, fb ? B_F0 : B_F1, 2 * nf);
+        if (!Fn) return PD_ENOMEM;
+        PD_TRY_CUDA(c, cudaMemsetAsync(lv, 0, 2 * sizeof(unsigned long long), st));
+        k_ws_count_split<<<grid_for(nf, 256), 256, 0, st>>>(F, nf, nodes.X, nodes.Y, bb, rep, left, right, s, Fn, lv); pd::count_launch();
+        PD_TRY_CUDA(c, cudaGetLastError());
+        PD_TRY_CUDA(c, cudaMemcpyAsync(h, lv, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+        narcs += 2 * h[0];
+        nf = h[1];
+        F = Fn;
+        fb ^= 1;
+    }
     while (nf > 0) {
         int64_t* flag = bufT<int64_t>(c, B_WSFLAG, nf);
         int64_t* off = bufT<int64_t>(c, B_WSOFF, nf);
