@@ -624,3 +624,37 @@ def test_warm_start_network_oracle_gradient_and_bf16():
     v = rng.standard_normal(1000).astype(np.float32) * 100
     ref = torch.from_numpy(v).to(torch.bfloat16).float().numpy().astype(np.float64)
     np.testing.assert_array_equal(mlp.bf16(v), ref)
+
+
+@pytest.mark.parametrize("seed,eps,kind", [(800, 0.1, "f32"), (802, 0.05, "f32"), (804, 0.5, "f32"),
+                                           (806, 0.05, "u8"), (808, 2.0, "f32")])
+def test_nearest_neighbour_bound_is_below_the_optimum(orc, seed, eps, kind):
+    """The search's pruning bound (1 - eps_c) * RWMD of the 0-condensed
+    diagrams, RWMD with real (unrounded) distances and the diagonal option,
+    never exceeds OPT_int of the pair: delta-condensation moves the points by
+    at most eps_c * L_lo in total and OPT_int is at least the real W1 of the
+    condensed diagrams."""
+    if kind == "f32":
+        A, B = synth.uniform_exp(400, seed), synth.uniform_exp(330, seed + 1)
+    else:
+        A, B = synth.lowerstar_u8(1500, seed), synth.lowerstar_u8(1200, seed + 1)
+    r = orc.w1_approx(A, B, kind, eps=eps)
+
+    def side(P, Q):
+        px, py, pc = (np.asarray(v, np.float64) for v in P)
+        qx, qy = (np.asarray(v, np.float64) for v in Q[:2])
+        diag = np.abs(py - px) / math.sqrt(2.0)
+        if len(qx):
+            d = np.sqrt((px[:, None] - qx[None, :]) ** 2 + (py[:, None] - qy[None, :]) ** 2).min(1)
+            diag = np.minimum(diag, d)
+        return float((pc * diag).sum())
+
+    rwmd = max(side(r["Ahat"], r["Bhat"]), side(r["Bhat"], r["Ahat"]))
+    s = r["s"]
+    ec = 8.0 / (s - 4) if s >= 12 else 1.0
+    assert r["opt"] >= (1.0 - ec) * rwmd - 1e-6 * max(1.0, rwmd)
+    # and the movement of the condensation is within eps_c * L_lo
+    G, P = r["G"], r["P"]
+    moved = (r["FA"] + r["FB"]) * math.sqrt(2.0) * (G / 2 + P) if G > 1 else 0.0
+    Llo = max(r["LA"] - r["FA"], r["LB"] - r["FB"], 0)
+    assert moved <= ec * Llo * (1 + 1e-9) + 1e-9
