@@ -12,7 +12,8 @@ whole batch; per pair the optimality certificate against the WSPD.  The plain on
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle (the
-plain C restatement of the method) on a bounded sample of the same workload.
+plain C restatement of the method) on the same workload, one pair per host
+core at a time.
 """
 import argparse
 import hashlib
@@ -30,7 +31,6 @@ sys.path.insert(0, ROOT)
 METRIC = "W1 pairs/s at 100k pts, eps=0.05"
 UNIT = "pairs/s"
 WORKLOAD = "lower-star uint8 persistence diagrams, 100000 + 100000 points, eps=0.05 (s=327)"
-SAMPLE_N = 10000  # points per diagram of the CPU-oracle sample
 
 
 def parse():
@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--warm-pairs", type=int, default=2, help="pairs timed with the learned warm start (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other configurations' sub-lines")
+    ap.add_argument("--nn-db", type=int, default=512, help="database diagrams of the nearest-neighbour sub-line")
+    ap.add_argument("--mixture-n", type=int, default=10000, help="points per diagram of the continuous-mixture solve")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default pricing block (no autotuner)")
     return ap.parse_args()
 
 
@@ -56,10 +60,6 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
-
-
-def cpu_cores_used():
-    return 1  # the oracle is single-threaded C
 
 
 def host_info():
@@ -126,40 +126,65 @@ class ClockSampler:
 # CPU oracle legs
 # ---------------------------------------------------------------------------
 
-def oracle_pair_seconds(seed):
+def oracle_pair_seconds(args):
+    """One pair of the headline workload through the CPU oracle (plain C,
+    single thread): quantise .. network simplex on the sparse network."""
+    n, eps, seed = args
     import oracle
     from paper_2110_14734_gb300 import synth
-    A, B = synth.lowerstar_u8(SAMPLE_N, seed), synth.lowerstar_u8(SAMPLE_N, seed + 1)
+    A, B = synth.lowerstar_u8(n, seed), synth.lowerstar_u8(n, seed + 1)
     t = time.perf_counter()
-    oracle.w1_approx(A, B, "u8", eps=0.05)
+    oracle.w1_approx(A, B, "u8", eps=eps)
     return time.perf_counter() - t
 
 
-def cpu_baseline():
-    sec = oracle_pair_seconds(1000)
-    return {"value": 1.0 / sec, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
-            "sample": "CPU oracle (plain C, single thread: quantise .. network simplex on the sparse network) on "
-                      "one %d + %d point pair of the same generator, eps=0.05; %.1f s" % (SAMPLE_N, SAMPLE_N, sec),
-            "host": host_info()}
+def oracle_pool_run(n, eps, seeds, procs):
+    """Pairs of the workload through the oracle, one process per host core
+    (spawned before any GPU work of this process, or after it has ended).
+    Returns (wall seconds, per-pair seconds)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(procs) as pool:
+        t = time.perf_counter()
+        per = pool.map(oracle_pair_seconds, [(n, eps, sd) for sd in seeds], chunksize=1)
+        wall = time.perf_counter() - t
+    return wall, per
+
+
+def cpu_baseline(n, eps, pairs=3):
+    """pairs/s of `pairs` host cores each running the oracle on its own pair
+    of the headline workload: cores / mean seconds per pair (input generation
+    excluded)."""
+    seeds = [9000 + 2 * i for i in range(pairs)]
+    wall, per = oracle_pool_run(n, eps, seeds, pairs)
+    return {"value": pairs / statistics.mean(per), "unit": UNIT, "cores": pairs, "kind": "oracle",
+            "sample": "CPU oracle (plain C, single thread per pair: quantise .. network simplex on the sparse "
+                      "network) on %d pairs of the headline workload (%d + %d uint8 lower-star points, eps=%g), one "
+                      "process per core; oracle seconds per pair %s" %
+                      (pairs, n, n, eps, ", ".join("%.1f" % x for x in per)),
+            "median_s_per_pair": statistics.median(per), "host": host_info()}
 
 
 def run_reference(args):
+    """The oracle as it stands on the machine's host cores, on the headline
+    workload itself: every step one 100k + 100k pair, the pairs of the warm-up
+    and of the timed steps spread over the cores (one process each)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    for i in range(args.warmup):
-        oracle_pair_seconds(5000 + 2 * i)
-    times = [oracle_pair_seconds(7000 + 2 * i) for i in range(args.steps)]
-    tot = sum(times)
-    value = args.steps / tot
+    procs = max(1, min(os.cpu_count() or 1, args.steps))
+    oracle_pool_run(args.n, args.eps, [5000 + 2 * i for i in range(args.warmup)], max(1, min(procs, args.warmup)))
+    wall, per = oracle_pool_run(args.n, args.eps, [7000 + 2 * i for i in range(args.steps)], procs)
+    value = procs / statistics.mean(per)  # procs cores busy with oracle pairs (input generation excluded)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tot / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic (seeded lower-star uint8 diagrams)",
-            "config": {"workload": WORKLOAD, "sample_points_per_diagram": SAMPLE_N, "eps": 0.05},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
-                             "sample": "each step: CPU oracle on one %d + %d point pair (distinct seeds)" %
-                                       (SAMPLE_N, SAMPLE_N), "host": host_info()},
+            "config": {"workload": WORKLOAD, "n_points": args.n, "eps": args.eps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                             "sample": "each step: the CPU oracle on one %d + %d point pair of the workload "
+                                       "(distinct seeds), %d processes on the host's cores; median %.1f s per pair" %
+                                       (args.n, args.n, procs, statistics.median(per)),
+                             "host": host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -207,6 +232,119 @@ def replica_totals(local_ms, local_units, device=None):
 def _gen(args):
     from paper_2110_14734_gb300 import synth
     return synth.lowerstar_u8(*args)
+
+
+def _timed(stream, fn):
+    """Device time (ms) of fn() on `stream` by CUDA events, synchronised on both sides."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    out = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), out
+
+
+def other_configs(args, ctx, pdw1, dev, stream, flush):
+    """The workload's other configurations, each through the public entry
+    points with device-resident inputs, L2 flushed before every timed call:
+    2k uniform pairs at eps 0.1; the 100k lower-star pairs at eps 0.1 and 0.01
+    (one pair per call); a continuous mixture (few duplicates) solved at the
+    largest size of this bench's budget, with the sparse network's arcs per node
+    counted up to 1M points; and nearest-neighbour queries of 20k points
+    against a database of log-uniform sizes in [100, 50000]."""
+    import torch
+    from paper_2110_14734_gb300 import synth
+    out = {}
+
+    def plain(pairs, eps, o=None):
+        ms, rows = [], []
+        for A, B in pairs:
+            dA, dB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+            flush.zero_()
+            t, r = _timed(stream, lambda: pdw1.pd_w1_approx(ctx, dA, dB, eps, o))
+            ms.append(t)
+            rows.append(r)
+        return ms, rows
+
+    ms, rows = plain([(synth.uniform_exp(2000, 3000 + 2 * i), synth.uniform_exp(2000, 3001 + 2 * i))
+                      for i in range(10)], 0.1)
+    out["uniform_2k_eps0.1"] = {"value": 1000.0 / statistics.mean(ms), "unit": UNIT, "pairs": len(ms),
+                                "ms_per_pair": statistics.mean(ms), "form": "pd_w1_approx, one pair per call",
+                                "nodes_mean": statistics.mean(r["n_nodes"] for r in rows)}
+    ls = [(synth.lowerstar_u8(args.n, 1000), synth.lowerstar_u8(args.n, 1001)),
+          (synth.lowerstar_u8(args.n, 1002), synth.lowerstar_u8(args.n, 1003))]
+    for eps in (0.1, 0.01):
+        ms, rows = plain(ls, eps)
+        out["lowerstar_%dk_eps%g" % (args.n // 1000, eps)] = {
+            "value": 1000.0 / statistics.mean(ms), "unit": UNIT, "pairs": len(ms), "s": rows[0]["s"],
+            "ms_per_pair": statistics.mean(ms), "pivots_mean": statistics.mean(r["pivots"] for r in rows),
+            "form": "pd_w1_approx, one pair per call"}
+    # continuous mixture: one solve at the bench's size, arcs per node counted up to 1M points
+    n3 = args.mixture_n
+    ms, rows = plain([(synth.mixture_f32(n3, 1000), synth.mixture_f32(n3, 1001))], 0.1,
+                     pdw1.opts(time_limit_ms=300000))
+    r = rows[0]
+    counts = {}
+    for nc in (100000, 250000, 1000000):
+        dA = torch.from_numpy(synth.mixture_f32(nc, 1000)).to(dev)
+        dB = torch.from_numpy(synth.mixture_f32(nc, 1001)).to(dev)
+        try:
+            c3 = pdw1.pd_w1_sparsify_count(ctx, dA, dB, 0.1)
+            counts[str(nc)] = {"nodes": c3["n_nodes"], "arcs": c3["n_arcs"],
+                               "arcs_per_node": c3["n_arcs"] / max(1, c3["n_nodes"]), "ms": c3["stage_ms"][7]}
+        except pdw1.PDError as e:
+            counts[str(nc)] = {"error": str(e)}
+    out["mixture_eps0.1"] = {"value": 1000.0 / ms[0], "unit": UNIT, "n_points": n3, "ms_per_pair": ms[0],
+                             "nodes": r["n_nodes"], "arcs": r["n_arcs"], "solve_method": r["solve_method"],
+                             "pivots": r["pivots"], "sparse_network_sizes": counts,
+                             "form": "pd_w1_approx, one pair per call"}
+    # nearest neighbour: 20k-point query against a database of log-uniform sizes
+    if args.nn_db > 0:
+        sizes = synth.db_sizes(args.nn_db, 4, 100, 50000)
+        db = [torch.from_numpy(synth.uniform_exp(int(k), 20000 + i)).to(dev) for i, k in enumerate(sizes)]
+        q = torch.from_numpy(synth.uniform_exp(20000, 19999)).to(dev)
+        pdw1.pd_db_build(ctx, db)
+        flush.zero_()
+        t, r = _timed(stream, lambda: pdw1.pd_nn_search(ctx, q, 0.05))
+        out["nn_20k_query_eps0.05"] = {"value": 1000.0 / t, "unit": "queries/s", "db_diagrams": args.nn_db,
+                                       "db_points": int(sum(int(k) for k in sizes)), "ms_per_query": t,
+                                       "solved": r["solved"], "pruned": r["pruned"], "waves": r["waves"],
+                                       "bounds_ms": r["lb_ms"], "wcd_above_rwmd": r["wcd_above"],
+                                       "nn_index": r["nn_index"], "form": "pd_db_build once, then pd_nn_search"}
+        pdw1.pd_db_build(ctx, [])
+        del db
+    return out
+
+
+def gaussian_sweep(ctx, pdw1, dev, stream, flush, sizes=(10000, 20000, 40000), svals=(10, 20, 40)):
+    """Empirical complexity (appendix): synthetic Gaussian diagrams of n total
+    points (n/2 per diagram) at fixed WSPD parameters s; each pair timed once
+    through pd_w1_approx; the exponent of n is the least-squares slope of
+    log(time) against log(n) per s."""
+    import math
+    import torch
+    from paper_2110_14734_gb300 import synth
+    rows = []
+    for s_ in svals:
+        for n in sizes:
+            dA = torch.from_numpy(synth.gaussian_pd(n // 2, 500 + n)).to(dev)
+            dB = torch.from_numpy(synth.gaussian_pd(n // 2, 501 + n)).to(dev)
+            flush.zero_()
+            t, r = _timed(stream, lambda: pdw1.pd_w1_approx(ctx, dA, dB, 0.0, pdw1.opts(s_override=s_,
+                                                                                        time_limit_ms=300000)))
+            rows.append({"s": s_, "n": n, "ms": t, "nodes": r["n_nodes"], "arcs": r["n_arcs"],
+                         "method": r["solve_method"], "pivots": r["pivots"]})
+    fits = {}
+    for s_ in svals:
+        pts = [(math.log(r["n"]), math.log(r["ms"])) for r in rows if r["s"] == s_]
+        mx = sum(x for x, _ in pts) / len(pts)
+        my = sum(y for _, y in pts) / len(pts)
+        den = sum((x - mx) ** 2 for x, _ in pts)
+        fits[str(s_)] = sum((x - mx) * (y - my) for x, y in pts) / den if den > 0 else None
+    return {"rows": rows, "exponent_of_n": fits,
+            "form": "pd_w1_approx on synthetic Gaussian diagrams (gaussian_pd), s fixed by s_override"}
 
 
 def run_ours(args):
@@ -391,7 +529,7 @@ def run_ours(args):
     if rank == 0:
         line["clocks"] = clk.summary()
         if ws == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(args.n, args.eps)
         print(json.dumps(line), flush=True)
     ctx.close()
     if ws > 1:

@@ -100,6 +100,13 @@ typedef struct {
                                3 = start from the potentials +d(u) for sources, -d(v) for sinks (d: the
                                distance to the diagonal), i.e. the greedy by the saving
                                d(u) + d(v) - c(u, v) of pairing u with v (no network) */
+    int32_t ns_candidates;  /* network simplex: 1 = after a pivot, the other warps' best arcs of the last
+                               priced block are priced again and the most negative still-negative one
+                               enters before a new block is priced (a candidate list); 0 = a block is
+                               priced before every pivot (the paper's block search; default) */
+    int32_t tree;           /* hierarchical tree of the WSPD: 0 = binary radix tree over the Morton order
+                               of the nodes (a compressed quadtree; default), 1 = the paper's split tree
+                               (WSPD section: the longest side of a bounding box cut in the middle) */
 } pd_opts;
 
 void pd_opts_default(pd_opts* opts);
@@ -200,6 +207,31 @@ pd_status pd_wspd_sparsify(pd_ctx* ctx, const pd_nodes* nodes, int32_t s, pd_net
                            void* stream);
 
 /*
+ * The sparse network of pd_wspd_sparsify built on a chosen tree: tree = 0 the
+ * radix tree (exactly pd_wspd_sparsify), tree = 1 the paper's split tree (WSPD
+ * section: a set's tight bounding box is cut at the middle of its longest
+ * side, the x side on ties, a point going to the lower half when twice its
+ * coordinate is below min + max; recursion to single points).  With the split
+ * tree the network's node ids 0..N-1 are the positions of the nodes in the
+ * tree's leaf order (the recursion's order, lower half first, the input order
+ * kept within each half); ordered_out (may be NULL) receives the nodes in that
+ * order (context-owned device memory, valid until the next call).  `nodes` as
+ * for pd_wspd_sparsify.
+ */
+pd_status pd_wspd_sparsify_tree(pd_ctx* ctx, const pd_nodes* nodes, int32_t s, int32_t tree,
+                                pd_nodes* ordered_out, pd_network* out, void* stream);
+
+/*
+ * Size of the sparse network of pd_wspd_sparsify_tree without building it:
+ * the WSPD is enumerated level by level and its pairs counted, no arc is
+ * stored.  *n_arcs_out (host) = WSPD biarcs + diagonal arcs + 1, exactly
+ * pd_wspd_sparsify_tree's n_arcs.  Device memory: the pair frontier of one
+ * level at a time (8 bytes per pair not yet separated).
+ */
+pd_status pd_wspd_count(pd_ctx* ctx, const pd_nodes* nodes, int32_t s, int32_t tree, int64_t* n_arcs_out,
+                        void* stream);
+
+/*
  * Exact integer min-cost flow on an uncapacitated network (the min-cost flow
  * of the transshipment network definition).  Default solver: primal network
  * simplex with block pricing in one CTA (network-simplex section, run to
@@ -224,6 +256,17 @@ pd_status pd_mcf_solve(pd_ctx* ctx, const pd_network* net, const pd_opts* opts, 
  */
 pd_status pd_w1_approx(pd_ctx* ctx, pd_diagram A, pd_diagram B, double eps, const pd_opts* opts,
                        pd_result* out, void* stream);
+
+/*
+ * Algorithm 4 up to the sparse network, without solving: quantise,
+ * 0-condense, RWMD, delta-condense, tree and WSPD as pd_w1_approx runs them,
+ * the network's arcs counted but not stored.  Fills *out (host) as
+ * pd_w1_approx would except for the solver's fields (opt_quanta, w1, slack,
+ * pivots ... are 0): s, delta, cell_quanta, shift_quanta, n_nodes, n_arcs, the
+ * RWMD and the masses.  For sizing a problem before solving it.
+ */
+pd_status pd_w1_sparsify_count(pd_ctx* ctx, pd_diagram A, pd_diagram B, double eps, const pd_opts* opts,
+                               pd_result* out, void* stream);
 
 /*
  * Approximate W1 of `count` independent pairs (A[i], B[i]), each computed
@@ -258,7 +301,7 @@ typedef struct {
     float lb_ms;            /* device time of the query's condensation and all lower bounds */
     float solve_ms;         /* host wall time of the waves */
     float total_ms;         /* host wall time of the call */
-    int32_t reserved;
+    int32_t wcd_above;      /* diagrams whose WCD bound is above their RWMD bound */
 } pd_nn_result;
 
 /*
@@ -274,20 +317,57 @@ pd_status pd_db_build(pd_ctx* ctx, const pd_diagram* dbs, int64_t n_db, const pd
 /*
  * Nearest neighbour of `query` in the database: the index i minimising the
  * approximate W1 of (query, db[i]) as pd_w1_approx computes it (OPT_int;
- * ties -> lowest i).  Lower bounds: LB_i = floor((1 - eps_c) * RWMD_i) with
- * RWMD_i the relaxed-flow bound (Algorithm 1, diagonal included) of the
- * 0-condensed diagrams, evaluated in float32 with every distance rounded down,
- * and eps_c = 8 / (s - 4) (0 without condensation): delta-condensation moves
- * the points by at most eps_c * RWMD in total, so LB_i <= OPT_int(query, db[i]).
- * Pairs are solved in ascending LB_i (ties by index), opts->batch_slots pairs
+ * ties -> lowest i).  Two lower bounds, both scaled by (1 - eps_c) with
+ * eps_c = 8 / (s - 4) (0 without condensation), because delta-condensation
+ * moves the points by at most eps_c * W1 in total:
+ *   - RWMD_i, the relaxed-flow bound (Algorithm 1, diagonal included) of the
+ *     0-condensed diagrams, evaluated in float32 with every distance rounded
+ *     down;
+ *   - WCD_i / 2 (Appendix, WCD): the word centroid distance of
+ *     query + db[i]'s diagonal projections against db[i] + the query's
+ *     projections is at most twice W1; it equals |T_q - T_i| / sqrt(2) with
+ *     T the total persistence sum (d - b) of a diagram (exact integers; each
+ *     database diagram's T is summed once by pd_db_build).
+ * LB_i = max of the two, rounded down, <= OPT_int(query, db[i]).  Pairs are
+ * solved in ascending LB_i (ties by index), opts->batch_slots pairs
  * per batched solve (pd_w1_approx_batch); with opts->nn_prune (default) the
  * search stops at the first pair whose bound exceeds the best optimum found,
  * which leaves the answer unchanged.  opt_out (host, n_db entries, may be
  * NULL): OPT_int of every solved pair, -1 for pruned pairs; lb_out (host,
- * n_db, may be NULL): LB_i.  An empty database gives nn_index = -1.
+ * n_db, may be NULL): LB_i; wcd_out (host, n_db, may be NULL): the WCD bound
+ * alone.  An empty database gives nn_index = -1.
  */
 pd_status pd_nn_search(pd_ctx* ctx, pd_diagram query, double eps, const pd_opts* opts, pd_nn_result* out,
-                       int64_t* opt_out, int64_t* lb_out, void* stream);
+                       int64_t* opt_out, int64_t* lb_out, int64_t* wcd_out, void* stream);
+
+/* ---- autotuner of the simplex's pricing block (no counterpart in the paper) --
+ *
+ * The paper's block search prices blocks of sqrt(arcs) arcs.  pd_autotune
+ * measures instead: it prepares the transportation instance of each sample
+ * pair (A[i], B[i]) at eps/opts exactly as pd_w1_approx does, solves it once
+ * per candidate block (4096 ... 131072 arcs, and the default), each launch
+ * timed by CUDA events, and keeps the fastest block of each size class
+ * floor(log2(arcs + nodes)) in the context: later solves of that class whose
+ * opts->ns_block is 0 use it (pd_w1_approx, pd_w1_approx_batch,
+ * pd_nn_search, pd_mcf_solve).  Every candidate reaches the same optimum
+ * (checked).  cache_path (may be NULL): a text file of lines "gpu-name sms
+ * class block"; classes it already holds for this GPU are loaded instead of
+ * timed, and newly timed classes are written back (other GPUs' lines kept).
+ * Must not run concurrently with other calls on the same context. */
+typedef struct {
+    int64_t ns_block;   /* block chosen for the first sample pair's size class (0 if none) */
+    int32_t size_class; /* that class, floor(log2(arcs + nodes)); -1 if no pair had a transportation form */
+    int32_t candidates; /* candidate blocks */
+    int32_t pairs;      /* pairs timed (not taken from the cache) */
+    int32_t from_cache; /* 1: the first pair's class came from cache_path */
+    float best_ms;      /* simplex device time of the timed pairs of that class with the chosen block */
+    float default_ms;   /* ... with the default block max(8192, sqrt(arcs + nodes)) */
+} pd_tune_result;
+
+pd_status pd_autotune(pd_ctx* ctx, const pd_diagram* A, const pd_diagram* B, int64_t count, double eps,
+                      const pd_opts* opts, const char* cache_path, pd_tune_result* out, void* stream);
+/* The block the context uses for an instance of arcs + nodes = M (0: none tuned, the default applies). */
+pd_status pd_tuned_block(const pd_ctx* ctx, int64_t arcs_and_nodes, int64_t* block_out);
 
 /* ---- learned warm start (no counterpart in the paper) ----------------------
  *
@@ -357,11 +437,12 @@ pd_status pd_ws_load(pd_ctx* ctx, const char* path);
  * `net`: device memory in pd_network layout, as for pd_mcf_solve, with at
  * most PD_NOALLOC_MAX_NODES - 1 nodes and PD_NOALLOC_MAX_ARCS arcs; larger
  * networks return PD_ECAPACITY (so do total supplies >= 2^31).  *opt_out
- * (host) receives the optimum; the call synchronises `stream`.
+ * (host) receives the optimum.  The call synchronises `stream` and reads
+ * results back to the host, so it must not be called while `stream` (or the
+ * legacy default stream) is being captured into a CUDA graph.
  *
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array and it keeps the last call's
+ * device, with that device current).  All calls share the one array and it keeps the last call's
  * contents: calls whose GPU work overlaps (other streams, other host threads
  * on the same device) race with each other and must be serialised by the
  * caller.  Errors are reported by the return code only.

@@ -70,6 +70,8 @@ def lib():
                                          I32P, I32P, I64P, I64P, U64P]
         L.orc_radix_tree.restype = None
         L.orc_radix_tree.argtypes = [C.c_int64, U64P, I32P, I32P, I32P, I32P, I32P, I32P, I32P, I32P]
+        L.orc_split_tree.restype = None
+        L.orc_split_tree.argtypes = [C.c_int64, I32P, I32P, I32P, I32P, I32P, I32P, I32P]
         L.orc_mix64.restype = C.c_uint64
         L.orc_mix64.argtypes = [C.c_uint64]
         L.orc_wspd_pairs.restype = C.c_int64
@@ -234,6 +236,30 @@ def radix_tree(nodes):
     return t
 
 
+def split_tree(nodes):
+    """The paper's split tree over the nodes (longest bounding-box side cut in
+    the middle).  Returns (perm, tree): perm[p] = index in `nodes` of the leaf
+    at position p; the tree refers to positions, so it goes with
+    reorder(nodes, perm)."""
+    N = len(nodes["X"])
+    M = max(N - 1, 1)
+    perm = np.arange(N, dtype=np.int32)
+    t = dict(left=np.zeros(M, np.int32), right=np.zeros(M, np.int32), bb=np.zeros(4 * M, np.int32),
+             rep=np.zeros(M, np.int32))
+    if N >= 2:
+        lib().orc_split_tree(N, _nz(nodes["X"], np.int32), _nz(nodes["Y"], np.int32), perm, t["left"],
+                             t["right"], t["bb"], t["rep"])
+    else:
+        t = {k: v[:0] for k, v in t.items()}
+    t["bb"] = t["bb"].reshape(-1, 4)
+    return perm, t
+
+
+def reorder(nodes, perm):
+    """The nodes in the order perm gives (position p holds node perm[p])."""
+    return {k: np.ascontiguousarray(v[perm]) for k, v in nodes.items()}
+
+
 def wspd(nodes, tree, s, cap=None):
     N = len(nodes["X"])
     if N < 2:
@@ -349,7 +375,7 @@ def w1_exact(A, B, max_pivots=0) -> float:
 
 
 def w1_approx(A, B, dtype, eps=0.1, k=None, s_override=0, perturb=True, seed=0,
-              condense=True, solve=True):
+              condense=True, solve=True, tree="radix"):
     """Algorithm 4 end to end.  Returns a dict of every intermediate result.
 
     A, B: (n, 2) arrays of (birth, death), float32 (dtype "f32") or uint8 ("u8").
@@ -372,15 +398,43 @@ def w1_approx(A, B, dtype, eps=0.1, k=None, s_override=0, perturb=True, seed=0,
     if not perturb:
         P = 0
     nodes = condense_delta(Ahat, Bhat, G, P, seed)
-    tree = radix_tree(nodes)
-    tails, heads = wspd(nodes, tree, s)
+    if tree == "split":  # the paper's split tree: nodes renumbered in its leaf order
+        perm, tr = split_tree(nodes)
+        nodes = reorder(nodes, perm)
+    else:
+        tr = radix_tree(nodes)
+    tails, heads = wspd(nodes, tr, s)
     net = build_network(nodes, tails, heads)
     out = dict(k=k, Ahat=Ahat, Bhat=Bhat, FA=FA, FB=FB, LA=LA, LB=LB, rwmd=L, s=s, delta=delta, G=G,
-               P=P, nodes=nodes, tree=tree, ws_tails=tails, ws_heads=heads, net=net)
+               P=P, nodes=nodes, tree=tr, ws_tails=tails, ws_heads=heads, net=net)
     if solve:
         opt, flow, pot = mcf(net)
         out.update(opt=opt, flow=flow, pot=pot, slack=int(flow.sum()), w1=math.ldexp(opt, -k))
     return out
+
+
+def wcd(P, Q):
+    """Word centroid distance used as a W1 lower bound (Appendix, WCD): with
+    P~ the diagonal projections ((b+d)/2, (b+d)/2) of a diagram, the two
+    multisets U = P + Q~ and V = Q + P~ have the same size n, and
+    WCD = n |centroid(U) - centroid(V)| (Euclidean), which is at most the
+    optimal matching cost OT(U, V) <= 2 W1(P, Q); so W1 >= WCD / 2.  P, Q:
+    (n, 2) arrays of (birth, death) in any units, or (X, Y, count) triples of
+    condensed nodes; FP64 straight from the definition."""
+    def pts(D):
+        if isinstance(D, tuple):
+            X = np.repeat(np.asarray(D[0], np.float64), np.asarray(D[2], np.int64))
+            Y = np.repeat(np.asarray(D[1], np.float64), np.asarray(D[2], np.int64))
+            return np.stack([X, Y], axis=1) if len(X) else np.zeros((0, 2))
+        return np.asarray(D, np.float64).reshape(-1, 2)
+    p, q = pts(P), pts(Q)
+    proj = lambda a: np.repeat(((a[:, 0] + a[:, 1]) / 2.0)[:, None], 2, axis=1)
+    U = np.concatenate([p, proj(q)])
+    V = np.concatenate([q, proj(p)])
+    n = len(U)
+    if n == 0:
+        return 0.0
+    return float(n * np.hypot(*(U.mean(axis=0) - V.mean(axis=0))))
 
 
 def nn_search(query, db, dtype, eps=0.05, **kw):

@@ -420,6 +420,87 @@ void orc_radix_tree(int64_t N, const uint64_t* code, const int32_t* X, const int
 }
 
 /* ------------------------------------------------------------------------- */
+/* The paper's split tree (WSPD section): take the bounding box of a point    */
+/* set, cut its longest side in the middle, recurse until single points.      */
+/* ------------------------------------------------------------------------- */
+
+/* Split tree over the N nodes (X, Y).  A set of two or more points is cut at
+ * the middle of the longest side of its tight bounding box (the x side when
+ * the sides are equal): a point goes left when twice its coordinate on that
+ * axis is below min + max, else right, keeping the input order within each
+ * side.  Leaves are numbered by the position at which the recursion (left
+ * before right) meets them: perm[p] = input index of the leaf at position p.
+ * Internal nodes are numbered as in orc_radix_tree (root 0; a child covering
+ * positions [lo, split] is numbered split, one covering [split + 1, hi] is
+ * split + 1), children c >= 0 internal, c < 0 leaf at position ~c; bb and rep
+ * (the leftmost member: min X, then min Y) are given in positions too.  So
+ * after reordering the nodes by perm the WSPD code runs on this tree as it
+ * does on the radix tree.  Needs N >= 2 and distinct points. */
+void orc_split_tree(int64_t N, const int32_t* X, const int32_t* Y, int32_t* perm, int32_t* left,
+                    int32_t* right, int32_t* bb, int32_t* rep) {
+    if (N < 2) return;
+    int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * N);
+    int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * N);
+    int32_t* pos = (int32_t*)malloc(sizeof(int32_t) * N);
+    for (int64_t i = 0; i < N; i++) idx[i] = (int32_t)i;
+    int64_t* stk = (int64_t*)malloc(sizeof(int64_t) * 3 * (N + 1));
+    int64_t sp = 0;
+    stk[sp++] = 0;
+    stk[sp++] = N - 1;
+    stk[sp++] = 0;
+    while (sp > 0) {
+        int64_t w = stk[--sp], hi = stk[--sp], lo = stk[--sp];
+        int64_t mnx = X[idx[lo]], mxx = mnx, mny = Y[idx[lo]], mxy = mny;
+        int32_t r = idx[lo];
+        for (int64_t k = lo; k <= hi; k++) {
+            int32_t v = idx[k];
+            if (X[v] < mnx) mnx = X[v];
+            if (X[v] > mxx) mxx = X[v];
+            if (Y[v] < mny) mny = Y[v];
+            if (Y[v] > mxy) mxy = Y[v];
+            if (X[v] < X[r] || (X[v] == X[r] && Y[v] < Y[r])) r = v;
+        }
+        int by_x = (mxx - mnx) >= (mxy - mny);
+        int64_t mid2 = by_x ? mnx + mxx : mny + mxy;
+        int64_t nl = 0, nr = 0;
+        for (int64_t k = lo; k <= hi; k++) { /* stable partition */
+            int32_t v = idx[k];
+            int64_t c2 = 2 * (int64_t)(by_x ? X[v] : Y[v]);
+            if (c2 < mid2) idx[lo + nl++] = v;
+            else tmp[nr++] = v;
+        }
+        for (int64_t k = 0; k < nr; k++) idx[lo + nl + k] = tmp[k];
+        int64_t split = lo + nl - 1; /* both sides are non-empty: min goes left, max right */
+        left[w] = (split == lo) ? (int32_t)~lo : (int32_t)split;
+        right[w] = (split + 1 == hi) ? (int32_t)~hi : (int32_t)(split + 1);
+        bb[4 * w + 0] = (int32_t)mnx;
+        bb[4 * w + 1] = (int32_t)mxx;
+        bb[4 * w + 2] = (int32_t)mny;
+        bb[4 * w + 3] = (int32_t)mxy;
+        rep[w] = r; /* an input index for now; positions below */
+        if (split != lo) {
+            stk[sp++] = lo;
+            stk[sp++] = split;
+            stk[sp++] = split;
+        }
+        if (split + 1 != hi) {
+            stk[sp++] = split + 1;
+            stk[sp++] = hi;
+            stk[sp++] = split + 1;
+        }
+    }
+    for (int64_t p = 0; p < N; p++) {
+        perm[p] = idx[p];
+        pos[idx[p]] = (int32_t)p;
+    }
+    for (int64_t w = 0; w < N - 1; w++) rep[w] = pos[rep[w]];
+    free(idx);
+    free(tmp);
+    free(pos);
+    free(stk);
+}
+
+/* ------------------------------------------------------------------------- */
 /* s-WSPD (well-separated pairs) and its biarcs.                             */
 /* ------------------------------------------------------------------------- */
 

@@ -1,0 +1,164 @@
+// Autotuner of the network simplex's pricing block (no counterpart in the
+// paper, whose block search uses a block of sqrt(arcs)).  The block trades
+// pricing work per pivot against the quality of the entering arc, and the
+// best trade depends on the instance's size and on the GPU, so it is measured:
+// the transportation instances of sample pairs are solved once per candidate
+// block, each launch timed by CUDA events, and the fastest block is kept per
+// size class (floor(log2(arcs + nodes))) in the context -- every later solve
+// of that class whose pd_opts.ns_block is 0 uses it -- and in an optional
+// cache file, one line per (GPU name, SM count, class): "name sms class block".
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "netsimplex.cuh"
+
+using namespace pd;
+
+namespace {
+
+const int64_t kCandidates[] = {4096, 8192, 16384, 32768, 65536, 131072};
+
+std::string device_key(int device, int sms) {
+    cudaDeviceProp p;
+    std::string name = "gpu";
+    if (cudaGetDeviceProperties(&p, device) == cudaSuccess) name = p.name;
+    else cudaGetLastError();
+    for (char& ch : name)
+        if (ch == ' ' || ch == '\t' || ch == '\n') ch = '_';
+    return name + " " + std::to_string(sms);
+}
+
+// Lines "name sms class block" of the cache file that match this GPU.
+std::map<int, int64_t> read_cache(const char* path, const std::string& key) {
+    std::map<int, int64_t> m;
+    FILE* f = path ? fopen(path, "r") : nullptr;
+    if (!f) return m;
+    char name[256];
+    int sms = 0, cls = 0;
+    long long blk = 0;
+    while (fscanf(f, "%255s %d %d %lld", name, &sms, &cls, &blk) == 4)
+        if (std::string(name) + " " + std::to_string(sms) == key && blk > 0) m[cls] = (int64_t)blk;
+    fclose(f);
+    return m;
+}
+
+bool write_cache(const char* path, const std::string& key, const std::map<int, int64_t>& mine) {
+    // keep other GPUs' lines, replace this GPU's
+    std::vector<std::string> keep;
+    if (FILE* f = fopen(path, "r")) {
+        char name[256];
+        int sms = 0, cls = 0;
+        long long blk = 0;
+        while (fscanf(f, "%255s %d %d %lld", name, &sms, &cls, &blk) == 4) {
+            const std::string k = std::string(name) + " " + std::to_string(sms);
+            if (k != key) keep.push_back(k + " " + std::to_string(cls) + " " + std::to_string(blk));
+        }
+        fclose(f);
+    }
+    FILE* f = fopen(path, "w");
+    if (!f) return false;
+    for (auto& l : keep) fprintf(f, "%s\n", l.c_str());
+    for (auto& e : mine) fprintf(f, "%s %d %lld\n", key.c_str(), e.first, (long long)e.second);
+    return fclose(f) == 0;
+}
+
+}  // namespace
+
+namespace pd {
+
+int tune_class(int64_t M) { return M > 0 ? (int)floor(log2((double)M)) : 0; }
+
+int64_t tuned_block(const Ctx* c, int64_t M) {
+    const Ctx* o = c->parent ? c->parent : c;
+    auto it = o->tuned_block.find(tune_class(M));
+    return it == o->tuned_block.end() ? 0 : it->second;
+}
+
+}  // namespace pd
+
+extern "C" pd_status pd_autotune(pd_ctx* cx, const pd_diagram* A, const pd_diagram* B, int64_t count, double eps,
+                                 const pd_opts* opts, const char* cache_path, pd_tune_result* out, void* stream) {
+    Ctx* c = cx;
+    if (!c || !out || count < 0 || (count > 0 && (!A || !B))) return PD_EINVAL;
+    c->err.clear();
+    pd_opts o;
+    pd_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(eps > 0.0) && o.s_override <= 0) return fail(c, PD_EINVAL, "eps must be > 0 (or set s_override)");
+    if (o.solver == 1) return fail(c, PD_EINVAL, "the tuner times the network simplex");
+    o.warm_start = 0;
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    pd_tune_result r;
+    memset(&r, 0, sizeof(r));
+    r.size_class = -1;
+    const std::string key = device_key(c->device, c->sm_count);
+    const std::map<int, int64_t> cached = read_cache(cache_path, key);
+    NSInst* d = bufT<NSInst>(c, B_NS_INST, 1);
+    if (!d) return PD_ENOMEM;
+    // per size class: total device time of every candidate over the pairs timed
+    std::map<int, std::vector<double>> total;
+    std::map<int, double> dflt;
+    for (int64_t i = 0; i < count; i++) {
+        Front f;
+        PD_TRY(front_half(c, A[i], B[i], eps, o, &f, st, true));
+        W1Prep w;
+        PD_TRY(ns_prepare_w1(c, f.nodes, f.net.n_arcs, f.h.FB - f.h.FA, o, &w, st));
+        if (!w.ns.ready) continue;
+        const int64_t M = w.ns.h.m + w.ns.h.n;
+        const int cls = tune_class(M);
+        if (r.size_class < 0) r.size_class = cls;
+        if (cached.count(cls)) {
+            c->tuned_block[cls] = cached.at(cls);
+            continue;
+        }
+        std::vector<double>& t = total[cls];
+        t.resize(sizeof(kCandidates) / sizeof(kCandidates[0]), 0.0);
+        int64_t opt = -1;
+        for (size_t q = 0; q <= t.size(); q++) {  // the candidates, then the default block
+            NSInst h = w.ns.h;
+            h.block = q < t.size() ? kCandidates[q] : std::max<int64_t>(8 * NS_THREADS, (int64_t)sqrt((double)M));
+            if (q < t.size() && h.block > 4 * M) continue;
+            NSInst res{};
+            c->last_ns_ms = 0.f;
+            PD_TRY(ns_run(c, &h, 1, w.ns.smem, d, &res, st));
+            PD_TRY(ns_status(c, res));
+            if (opt >= 0 && res.opt != opt) return fail(c, PD_ECUDA, "tuner: the optimum changed with the block");
+            opt = res.opt;
+            if (q < t.size()) t[q] += c->last_ns_ms;
+            else dflt[cls] += c->last_ns_ms;
+        }
+        r.pairs++;
+    }
+    std::map<int, int64_t> mine = cached;
+    for (auto& e : total) {
+        size_t best = 0;
+        for (size_t q = 1; q < e.second.size(); q++)
+            if (e.second[q] > 0.0 && (e.second[best] <= 0.0 || e.second[q] < e.second[best])) best = q;
+        c->tuned_block[e.first] = kCandidates[best];
+        mine[e.first] = kCandidates[best];
+        if (e.first == r.size_class) {
+            r.best_ms = (float)e.second[best];
+            r.default_ms = (float)dflt[e.first];
+        }
+    }
+    r.candidates = (int32_t)(sizeof(kCandidates) / sizeof(kCandidates[0]));
+    r.from_cache = (r.size_class >= 0 && total.count(r.size_class) == 0) ? 1 : 0;
+    r.ns_block = r.size_class >= 0 && c->tuned_block.count(r.size_class) ? c->tuned_block[r.size_class] : 0;
+    if (cache_path && !total.empty() && !write_cache(cache_path, key, mine))
+        return fail(c, PD_EINVAL, std::string("cannot write the tuning cache ") + cache_path);
+    *out = r;
+    return PD_OK;
+}
+
+extern "C" pd_status pd_tuned_block(const pd_ctx* cx, int64_t arcs_and_nodes, int64_t* block_out) {
+    if (!cx || !block_out) return PD_EINVAL;
+    *block_out = tuned_block(cx, arcs_and_nodes);
+    return PD_OK;
+}

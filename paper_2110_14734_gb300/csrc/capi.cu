@@ -347,6 +347,48 @@ extern "C" pd_status pd_wspd_sparsify(pd_ctx* c, const pd_nodes* nodes, int32_t 
     return PD_OK;
 }
 
+extern "C" pd_status pd_wspd_sparsify_tree(pd_ctx* c, const pd_nodes* nodes, int32_t s, int32_t tree,
+                                           pd_nodes* ordered_out, pd_network* out, void* stream) {
+    if (!c || !nodes || !out) return PD_EINVAL;
+    c->err.clear();
+    if (tree != 0 && tree != 1) return fail(c, PD_EINVAL, "tree must be 0 (radix tree) or 1 (split tree)");
+    if (nodes->n_nodes < 0 || (nodes->n_nodes > 0 && (!nodes->X || !nodes->Y || !nodes->cntA || !nodes->cntB ||
+                                                      !nodes->morton)))
+        return fail(c, PD_EINVAL, "bad pd_nodes");
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    PD_TRY(validate_nodes(c, *nodes, st));
+    pd_nodes nd = *nodes;
+    WsTree split{};
+    if (tree == 1) PD_TRY(stage_split_tree(c, &nd, &split, nullptr, st));
+    pd_network net;
+    PD_TRY(stage_network(c, nd, s, &net, nullptr, nullptr, nullptr, st, false, nullptr, tree == 1 ? &split : nullptr));
+    c->net = net;
+    *out = net;
+    if (ordered_out) *ordered_out = nd;
+    return PD_OK;
+}
+
+extern "C" pd_status pd_wspd_count(pd_ctx* c, const pd_nodes* nodes, int32_t s, int32_t tree, int64_t* n_arcs_out,
+                                   void* stream) {
+    if (!c || !nodes || !n_arcs_out) return PD_EINVAL;
+    c->err.clear();
+    if (tree != 0 && tree != 1) return fail(c, PD_EINVAL, "tree must be 0 (radix tree) or 1 (split tree)");
+    if (nodes->n_nodes < 0 || (nodes->n_nodes > 0 && (!nodes->X || !nodes->Y || !nodes->cntA || !nodes->cntB ||
+                                                      !nodes->morton)))
+        return fail(c, PD_EINVAL, "bad pd_nodes");
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    PD_TRY(validate_nodes(c, *nodes, st));
+    pd_nodes nd = *nodes;
+    WsTree split{};
+    if (tree == 1) PD_TRY(stage_split_tree(c, &nd, &split, nullptr, st));
+    pd_network net;
+    PD_TRY(stage_network(c, nd, s, &net, nullptr, nullptr, nullptr, st, true, nullptr, tree == 1 ? &split : nullptr));
+    *n_arcs_out = net.n_arcs;
+    return PD_OK;
+}
+
 extern "C" pd_status pd_mcf_solve(pd_ctx* c, const pd_network* net, const pd_opts* opts, int64_t* opt_out,
                                   pd_result* stats, void* stream) {
     if (!c || !net || !opt_out) return PD_EINVAL;
@@ -388,25 +430,10 @@ extern "C" pd_status pd_mcf_solve(pd_ctx* c, const pd_network* net, const pd_opt
     return PD_OK;
 }
 
-// Algorithm 4 up to the network handed to the solver: quantise, 0-condense,
-// RWMD, delta-condense, sparse network, diagonal merge.
-struct Front {
-    Hats h{};
-    int64_t L[3] = {0, 0, 0};
-    int64_t s = 0, G = 1, P = 0;
-    double delta = 0.0;
-    int k = 0;
-    pd_nodes nodes{};
-    pd_network net{}, mnet{};  // count-only front half: net holds only the counts, mnet is empty
-    WsTree tree{};
-    bool counted = false;
-    float ms[6] = {};  // quantise+0-condense, RWMD, delta-condense, tree, WSPD, CSR
-};
+namespace pd {
 
-// count_only: the sparse network is enumerated and counted but not stored
-// (enough for the transportation form and its certificate).
-static pd_status front_half(Ctx* c, const pd_diagram& A, const pd_diagram& B, double eps, const pd_opts& o,
-                            Front* f, cudaStream_t st, bool count_only) {
+pd_status front_half(Ctx* c, const pd_diagram& A, const pd_diagram& B, double eps, const pd_opts& o, Front* f,
+                     cudaStream_t st, bool count_only) {
     cudaEvent_t ev[4];
     for (int q = 0; q < 4; q++) PD_TRY_CUDA(c, cudaEventCreate(&ev[q]));
     struct Guard {
@@ -431,9 +458,12 @@ static pd_status front_half(Ctx* c, const pd_diagram& A, const pd_diagram& B, do
     if (o.condense) delta_for(f->L[0], f->L[1], f->h.FA, f->h.FB, f->s, &f->delta, &f->G, &f->P);
     if (!o.perturb) f->P = 0;
     PD_TRY(stage_condense_delta(c, f->h, f->G, f->P, o.seed, &f->nodes, st));
-    c->nodes = f->nodes;
     PD_TRY_CUDA(c, cudaEventRecord(ev[3], st));
-    PD_TRY(stage_network(c, f->nodes, f->s, &f->net, &f->ms[3], &f->ms[4], &f->ms[5], st, count_only, &f->tree));
+    WsTree split{};
+    if (o.tree == 1) PD_TRY(stage_split_tree(c, &f->nodes, &split, nullptr, st));  // nodes renumbered by leaf order
+    c->nodes = f->nodes;
+    PD_TRY(stage_network(c, f->nodes, f->s, &f->net, &f->ms[3], &f->ms[4], &f->ms[5], st, count_only, &f->tree,
+                         o.tree == 1 ? &split : nullptr));
     f->counted = count_only;
     c->net = f->net;
     if (count_only) {
@@ -454,6 +484,8 @@ static pd_status front_half(Ctx* c, const pd_diagram& A, const pd_diagram& B, do
     cudaEventElapsedTime(&f->ms[2], ev[2], ev[3]);
     return PD_OK;
 }
+
+}  // namespace pd
 
 static void fill_result(const Front& f, const SolveStats& ss, pd_result* out) {
     pd_result r;
@@ -533,6 +565,7 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
     c->err.clear();
     pd_opts o = resolve_opts(opts);
     if (!(eps > 0.0) && o.s_override <= 0) return fail(c, PD_EINVAL, "eps must be > 0 (or set s_override)");
+    if (o.tree != 0 && o.tree != 1) return fail(c, PD_EINVAL, "tree must be 0 (radix tree) or 1 (split tree)");
     c->last_ns_ms = 0.f;
     if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
@@ -565,8 +598,11 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
             const SolveStats first = ss;
             pd_network mnet = f.mnet;
             if (f.counted) {
+                // on the same tree: with the split tree the nodes are in its leaf order, not Morton order
                 pd_network net;
-                PD_TRY(stage_network(c, f.nodes, f.s, &net, nullptr, nullptr, nullptr, st));
+                const WsTree given = f.tree;
+                PD_TRY(stage_network(c, f.nodes, f.s, &net, nullptr, nullptr, nullptr, st, false, nullptr,
+                                     o.tree == 1 ? &given : nullptr));
                 PD_TRY(merge_diagonal(c, net, f.nodes.n_nodes, &mnet, st));
             }
             PD_TRY(ns_solve_network(c, mnet, o, &ss, st));
@@ -583,6 +619,27 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
     out->kernel_launches = launch_count_ref() - launches0;
     out->ns_kernel_ms = c->last_ns_ms;
     out->warm_used = warm_used ? 1 : 0;
+    return PD_OK;
+}
+
+extern "C" pd_status pd_w1_sparsify_count(pd_ctx* c, pd_diagram A, pd_diagram B, double eps, const pd_opts* opts,
+                                          pd_result* out, void* stream) {
+    if (!c || !out) return PD_EINVAL;
+    c->err.clear();
+    pd_opts o = resolve_opts(opts);
+    if (!(eps > 0.0) && o.s_override <= 0) return fail(c, PD_EINVAL, "eps must be > 0 (or set s_override)");
+    if (o.tree != 0 && o.tree != 1) return fail(c, PD_EINVAL, "tree must be 0 (radix tree) or 1 (split tree)");
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long launches0 = launch_count_ref();
+    const auto t0 = std::chrono::steady_clock::now();
+    Front f;
+    PD_TRY(front_half(c, A, B, eps, o, &f, st, true));
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    fill_result(f, SolveStats{}, out);
+    out->solve_method = -1;
+    out->stage_ms[7] = elapsed_ms(t0);
+    out->kernel_launches = launch_count_ref() - launches0;
     return PD_OK;
 }
 
@@ -697,6 +754,7 @@ pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t 
     while ((int64_t)c->slots.size() < W) {
         Ctx* sl = ctx_new(c->device, c->cap);
         if (!sl) return fail(c, PD_ECUDA, "cannot create the buffers of a batch slot");
+        sl->parent = c;
         c->slots.push_back(sl);
     }
     while ((int)c->workers.size() < nthr) {
@@ -707,6 +765,7 @@ pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t 
             ctx_free(wk);
             return fail(c, PD_ECUDA, "cannot create a batch worker stream");
         }
+        wk->parent = c;
         c->workers.push_back(wk);
     }
     for (Ctx* wk : c->workers) wk->mlp_owner = c;  // predictions use this context's network

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -29,10 +30,12 @@ enum Buf : int {
     B_NS_PI, B_NS_PARENT, B_NS_PRED, B_NS_FLOW, B_NS_UP, B_NS_ORD, B_NS_POS, B_NS_SIZE, B_NS_TMP,
     B_NS_PATH, B_NS_SEG, B_NS_INST, B_NS_ORDER, B_NS_COST, B_TR_S, B_TR_T, B_TR_SUP, B_TR_XCOST,
     B_DB_SXY, B_DB_SCNT, B_DB_SID,  // nearest-neighbour database: staging
-    B_DB_XY, B_DB_CNT, B_DB_ID, B_DB_OFF, B_DB_ROFF, B_Q_XY, B_Q_CNT, B_DB_LA, B_DB_BIG,
+    B_DB_XY, B_DB_CNT, B_DB_ID, B_DB_OFF, B_DB_ROFF, B_Q_XY, B_Q_CNT, B_DB_LA, B_DB_BIG, B_DB_VAL, B_DB_PERS,
     B_MLP_P, B_MLP_M, B_MLP_V, B_MLP_WB, B_MLP_PART, B_MLP_G,  // warm-start network
     B_WS_GRID, B_WS_FEAT, B_WS_Y, B_WS_PS, B_WS_BOX, B_WS_DF, B_WS_DT, B_WS_DM, B_WS_IN, B_WS_TIN, B_WS_MIN,
     B_WS_P, B_WS_ROWK, B_WS_COLK, B_WS_ARCS, B_WS_COST, B_WS_RS, B_WS_RT, B_WS_RC, B_WS_COMP, B_WS_CSIZE, B_WS_CSUM,
+    B_SP_ORD, B_SP_ORD2, B_SP_SEG, B_SP_SEG2, B_SP_HI, B_SP_HI2, B_SP_NUM, B_SP_NUM2,  // split tree
+    B_SP_BB, B_SP_REPK, B_SP_REPN, B_SP_FLAG, B_SP_RANK, B_SP_X, B_SP_Y, B_SP_CA, B_SP_CB, B_SP_CODE, B_SP_POS,
     B_SMALL,                        // small device scalars
     B_COUNT
 };
@@ -59,12 +62,17 @@ struct Ctx {
     int64_t db_total = 0;
     int db_k = 0, db_dtype = 0;
     bool db_big = false;  // a database coordinate is not exact in float32
+    std::vector<int64_t> db_pers;  // total persistence sum cnt * (Y - X) of every database diagram (quanta)
     // warm-start network: parameters in B_MLP_* (of mlp_owner when set, as
     // for the batch workers), training rows in B_WS_DF / DT / DM
     bool mlp_ready = false;
     int64_t mlp_steps = 0;
     int64_t ws_rows = 0, ws_cap = 0;
     Ctx* mlp_owner = nullptr;
+    // pricing blocks chosen by pd_autotune, per size class (of the context that
+    // ran it: slots and workers of a batch look theirs up in `parent`)
+    std::map<int, int64_t> tuned_block;
+    Ctx* parent = nullptr;
 };
 
 Ctx* ctx_new(int device, size_t cap);  // nullptr on failure
@@ -135,11 +143,36 @@ struct WsTree {
 
 // count_only: the WSPD is enumerated and its arcs counted (out->n_arcs,
 // n_nodes), but no arc is stored and out's arrays are null.  tree (may be
-// null) receives the hierarchical tree.
+// null) receives the hierarchical tree.  given (may be null): a tree already
+// built over `nodes` (the split tree), used instead of the radix tree.
 pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* out, float* ms_tree,
                         float* ms_wspd, float* ms_csr, cudaStream_t st, bool count_only = false,
-                        WsTree* tree = nullptr);
+                        WsTree* tree = nullptr, const WsTree* given = nullptr);
+// The paper's split tree over `nodes` (splittree.cu): *nodes is replaced by
+// the nodes in the tree's leaf order (context buffers), *tree receives the
+// tree over those positions, *perm_out (may be null) position -> input index.
+pd_status stage_split_tree(Ctx* c, pd_nodes* nodes, WsTree* tree, int32_t** perm_out, cudaStream_t st);
 pd_status merge_diagonal(Ctx* c, const pd_network& net, int64_t N, pd_network* out, cudaStream_t st);
+
+// Algorithm 4 up to the network handed to the solver: quantise, 0-condense,
+// RWMD, delta-condense, (split tree,) sparse network, diagonal merge.
+struct Front {
+    Hats h{};
+    int64_t L[3] = {0, 0, 0};
+    int64_t s = 0, G = 1, P = 0;
+    double delta = 0.0;
+    int k = 0;
+    pd_nodes nodes{};
+    pd_network net{}, mnet{};  // count-only front half: net holds only the counts, mnet is empty
+    WsTree tree{};
+    bool counted = false;
+    float ms[6] = {};  // quantise+0-condense, RWMD, delta-condense, tree, WSPD, CSR
+};
+
+// count_only: the sparse network is enumerated and counted but not stored
+// (enough for the transportation form and its certificate).
+pd_status front_half(Ctx* c, const pd_diagram& A, const pd_diagram& B, double eps, const pd_opts& o, Front* f,
+                     cudaStream_t st, bool count_only);
 pd_status stage_solve(Ctx* c, const pd_network& net, const pd_opts& o, SolveStats* out, cudaStream_t st);
 
 pd_status validate_nodes(Ctx* c, const pd_nodes& nodes, cudaStream_t st);
@@ -160,6 +193,11 @@ pd_status stage_inputs(Ctx* c, const pd_diagram& A, const pd_diagram& B, DevDiag
 // pd_w1_approx_batch after argument checks (opts resolved)
 pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t count, double eps,
                       const pd_opts& o, pd_result* out, cudaStream_t st);
+
+// Size class of a simplex instance with M arcs + nodes, and the pricing block
+// pd_autotune chose for it (0 = none: the default block).
+int tune_class(int64_t M);
+int64_t tuned_block(const Ctx* c, int64_t M);
 
 // radix sort / scan with context scratch
 pd_status sort_u64(Ctx* c, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n,

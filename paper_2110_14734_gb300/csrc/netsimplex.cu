@@ -23,6 +23,7 @@
 // from the apex in the direction of the entering arc, which rules out cycling.
 // An instance may instead carry its own strongly feasible start (warm start).
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -95,6 +96,7 @@ struct Tree {
 };
 
 constexpr int NS_LMAX = 512;     // half-cycle entries kept in shared memory
+constexpr int NS_PR = 8;         // cost-matrix loads in flight per thread while pricing
 constexpr int NS_SEGSM = 65;     // re-hang segments kept in shared memory (paths shorter than 32)
 constexpr int NS_REGS = 9;       // shared-memory layout: at most 9 * 1024 nodes (re-hang buffered in registers)
 
@@ -117,6 +119,9 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
     __shared__ int64_t s_dpi;
     __shared__ int32_t s_go, s_status;
     __shared__ int32_t s_L0, s_S, s_pr, s_nseg, s_segsm;
+    __shared__ uint32_t s_cand[32];      // candidate list: other warps' winners of the last priced block
+    __shared__ int32_t s_ncand[2], s_ment;  // list size, double-buffered by pivot parity
+    __shared__ int64_t s_mrc;
     __shared__ int32_t sseg[3][NS_SEGSM];
     const int32_t SEGN = 2 * n + 3;
 
@@ -155,12 +160,14 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
         T.sz[root] = (IX)N1;
         s_status = 0;
     }
+    if (tid == 0) s_ncand[0] = s_ncand[1] = 0;
     __syncthreads();
     const uint64_t t0 = ns_now();
     int64_t pivots = 0, degen = 0, nscan = 0;
     const int64_t B = I.block < 1 ? 1 : I.block;
     int64_t next = 0;  // first arc of the next pricing block (same in every thread)
     int pb_buf = 0;
+    int cb = 0;  // parity of the pivot: the candidate count is read from s_ncand[cb], written to s_ncand[cb ^ 1]
 
     for (;;) {
         // ---- pricing: blocks of B arcs from `next`; the most negative reduced
@@ -172,7 +179,42 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
         // deterministic.
         int64_t scanned = 0, a0 = next;
         int64_t ent = -1, rc = 0;
-        while (scanned < M) {
+        if (s_ncand[cb] > 0) {
+            // minor iteration: one warp re-prices the candidate list with the
+            // current potentials; the most negative still-negative arc enters
+            // (same key and tie rule as a block), the rest stay candidates
+            if (wid == 0) {
+                const int32_t nc = s_ncand[cb];
+                uint32_t a = 0xffffffffu;
+                int64_t r = 0;
+                if (lane < nc) {
+                    a = s_cand[lane];
+                    int32_t t, h;
+                    arc_ends(I, a, &t, &h);
+                    r = arc_cost(I, a, big) - T.pi[t] + T.pi[h];
+                }
+                const int32_t key = r < 0 ? -__float_as_int((float)(-r)) : 0;
+                const int32_t wmin = __reduce_min_sync(FULL, key);
+                const uint32_t cand = (wmin < 0 && key == wmin) ? a : 0xffffffffu;
+                const uint32_t widx = __reduce_min_sync(FULL, cand);
+                if (wmin < 0 && cand == widx) s_mrc = r;
+                const bool keep = lane < nc && r < 0 && a != widx;
+                const uint32_t km = __ballot_sync(FULL, keep);
+                if (keep) s_cand[__popc(km & ((1u << lane) - 1u))] = a;
+                if (lane == 0) {
+                    s_ment = wmin < 0 ? (int32_t)widx : -1;
+                    s_ncand[cb ^ 1] = __popc(km);
+                }
+                nscan += nc;
+            }
+            __syncthreads();
+            if (s_ment >= 0) {
+                ent = s_ment;
+                rc = s_mrc;
+                scanned = M;  // no block priced
+            }
+        }
+        while (ent < 0 && scanned < M) {
             const int64_t aend = a0 + B < M ? a0 + B : M;
             const int64_t len = aend - a0;
             {
@@ -184,42 +226,40 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(I.cmat + pf));
             }
             int64_t lb = 0, li = -1;
-            for (int64_t c0 = a0 + 8 * (int64_t)tid; c0 < aend; c0 += 8 * NS_THREADS) {
-                if (c0 + 8 <= aend && c0 + 8 <= I.mst) {
-                    int4 w0 = __ldcg((const int4*)(I.cmat + c0));
-                    int4 w1 = __ldcg((const int4*)(I.cmat + c0 + 4));
-                    int32_t cv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-                    int32_t i = (int32_t)c0 / (int32_t)I.nT, j = (int32_t)c0 - i * (int32_t)I.nT;
-                    int64_t pt = T.pi[i];
+            // consecutive lanes take consecutive arcs: coalesced 4-byte loads,
+            // and the sink potentials pi(nS + j) they read are consecutive
+            // 8-byte words of shared memory (no bank conflicts)
+            const int64_t iend = aend < I.mst ? aend : I.mst;
+            const int32_t nT = (int32_t)I.nT, step_i = NS_THREADS / nT, step_j = NS_THREADS - step_i * nT;
+            for (int64_t base = a0; base < iend; base += NS_PR * NS_THREADS) {
+                int32_t cv[NS_PR];
 #pragma unroll
-                    for (int q = 0; q < 8; q++) {
-                        int64_t r = (int64_t)cv[q] - pt + T.pi[I.nS + j];
-                        take_min(r, c0 + q, lb, li);
-                        if (++j == (int32_t)I.nT) {
-                            j = 0;
-                            ++i;
-                            if (q < 7) pt = T.pi[i];
-                        }
-                    }
-                } else if (I.vec_explicit && c0 >= I.mst && c0 + 8 <= aend && c0 + 8 <= I.m &&
-                           ((c0 - I.mst) & 7) == 0) {
-                    const int64_t x = c0 - I.mst;
-                    int4 t0v = __ldcg((const int4*)(I.tail + x)), t1v = __ldcg((const int4*)(I.tail + x + 4));
-                    int4 h0 = __ldcg((const int4*)(I.head + x)), h1 = __ldcg((const int4*)(I.head + x + 4));
-                    int4 k0 = __ldcg((const int4*)(I.cost + x)), k1 = __ldcg((const int4*)(I.cost + x + 4));
-                    int32_t tv[8] = {t0v.x, t0v.y, t0v.z, t0v.w, t1v.x, t1v.y, t1v.z, t1v.w};
-                    int32_t hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
-                    int32_t cv[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+                for (int q = 0; q < NS_PR; q++) {
+                    const int64_t a = base + tid + q * NS_THREADS;
+                    cv[q] = a < iend ? __ldcg(I.cmat + a) : 0;
+                }
+                // row i and column j of arc base + tid (< 2^31), then NS_THREADS
+                // arcs further per step
+                const int32_t a1 = (int32_t)(base + tid);
+                int32_t i = a1 / nT, j = a1 - i * nT;
 #pragma unroll
-                    for (int q = 0; q < 8; q++) take_min((int64_t)cv[q] - T.pi[tv[q]] + T.pi[hv[q]], c0 + q, lb, li);
-                } else {
-                    int64_t ce = c0 + 8 < aend ? c0 + 8 : aend;
-                    for (int64_t a = c0; a < ce; a++) {
-                        int32_t t, h;
-                        arc_ends(I, a, &t, &h);
-                        take_min(arc_cost(I, a, big) - T.pi[t] + T.pi[h], a, lb, li);
+                for (int q = 0; q < NS_PR; q++) {
+                    const int64_t a = (int64_t)a1 + q * NS_THREADS;
+                    if (a < iend) take_min((int64_t)cv[q] - T.pi[i] + T.pi[I.nS + j], a, lb, li);
+                    i += step_i;
+                    j += step_j;
+                    if (j >= nT) {
+                        j -= nT;
+                        ++i;
                     }
                 }
+            }
+            // explicit arcs (the diagonal node's, or a whole arc list), then the
+            // artificial arcs of the initial tree
+            for (int64_t a = (a0 > I.mst ? a0 : I.mst) + tid; a < aend; a += NS_THREADS) {
+                int32_t t, h;
+                arc_ends(I, a, &t, &h);
+                take_min(arc_cost(I, a, big) - T.pi[t] + T.pi[h], a, lb, li);
             }
             const int32_t key = lb < 0 ? -__float_as_int((float)(-lb)) : 0;
             const int32_t wmin = __reduce_min_sync(FULL, key);
@@ -244,6 +284,12 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
                 rc = s_wval[pb_buf][wl];
                 ent = bidx;
                 next = a0;
+                if (I.minor && wid == 0) {  // the other warps' negative winners become the candidate list
+                    const bool keep = k2 < 0 && i2 != bidx;
+                    const uint32_t km = __ballot_sync(FULL, keep);
+                    if (keep) s_cand[__popc(km & ((1u << lane) - 1u))] = i2;
+                    if (lane == 0) s_ncand[cb ^ 1] = __popc(km);
+                }
                 pb_buf ^= 1;
                 break;
             }
@@ -628,6 +674,7 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
                 }
             }
         }
+        cb ^= 1;
     }
     // ---- result: node arrays back to the global record ---------------------
     __syncthreads();
@@ -731,6 +778,33 @@ bool ns_smem_fits(int64_t N1, int max_optin) {
     return fa.sharedSizeBytes + ns_smem_bytes(N1) <= (size_t)max_optin;
 }
 
+// The dynamic shared memory limit of a kernel is one attribute per device for
+// the whole process.  Several host threads launch k_netsimplex at once (the
+// batch workers, the allocation-free solve), so the limit is raised once per
+// device to the largest size any instance can ask for and never lowered: a
+// launch can then never see another thread's smaller value.
+cudaError_t ns_kernel_setup() {
+    static std::mutex mu;
+    static bool done[256] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> g(mu);
+    if (done[dev]) return cudaSuccess;
+    int max_optin = 0;
+    e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k_netsimplex);
+    if (e != cudaSuccess) return e;
+    const size_t most = std::min((size_t)max_optin - fa.sharedSizeBytes, ns_smem_bytes((int64_t)NS_REGS * NS_THREADS));
+    e = cudaFuncSetAttribute(k_netsimplex, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    if (e != cudaSuccess) return e;
+    done[dev] = true;
+    return cudaSuccess;
+}
+
 __global__ void k_i64_to_i32_cost(const int64_t* __restrict__ c, int64_t m, int32_t* __restrict__ o,
                                   unsigned long long* __restrict__ bad) {
     int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -771,7 +845,6 @@ pd_status ns_prepare_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS,
     h.head = head;
     h.cost = cost;
     h.supply = supply;
-    h.vec_explicit = ((((uintptr_t)tail) | ((uintptr_t)head) | ((uintptr_t)cost)) & 15) == 0 ? 1 : 0;
     h.pi = bufT<int64_t>(c, B_NS_PI, N1);
     h.parent = bufT<int32_t>(c, B_NS_PARENT, N1);
     h.pred = bufT<int32_t>(c, B_NS_PRED, N1);
@@ -790,9 +863,11 @@ pd_status ns_prepare_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS,
     if (M >= (int64_t(1) << 31) - 1) return fail(c, PD_ECAPACITY, "network simplex needs fewer than 2^31 arcs");
     // default block: one pass of the CTA (8 arcs per thread), more for very
     // large networks; blocks start at multiples of 8 (vector loads)
-    int64_t blk = o.ns_block > 0 ? o.ns_block : std::max<int64_t>(8 * NS_THREADS, (int64_t)sqrt((double)M));
+    int64_t blk = o.ns_block > 0 ? o.ns_block : tuned_block(c, M);
+    if (blk <= 0) blk = std::max<int64_t>(8 * NS_THREADS, (int64_t)sqrt((double)M));
     blk = (blk + 7) & ~(int64_t)7;
     h.block = blk;
+    h.minor = o.ns_candidates != 0 ? 1 : 0;
     h.max_pivots = o.max_rounds > 0 ? o.max_rounds : (int64_t(1) << 40);
     h.time_limit_ns = (o.time_limit_ms > 0 ? (uint64_t)o.time_limit_ms : 60000ull) * 1000000ull;
     // flows are int32: the total supply must stay below 2^31
@@ -819,7 +894,7 @@ pd_status ns_prepare_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS,
 
 pd_status ns_run(Ctx* c, const NSInst* h, int count, size_t smem, NSInst* d, NSInst* r, cudaStream_t st) {
     if (count <= 0) return PD_OK;
-    PD_TRY_CUDA(c, cudaFuncSetAttribute(k_netsimplex, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PD_TRY_CUDA(c, ns_kernel_setup());
     int per_sm = 0;
     PD_TRY_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_netsimplex, NS_THREADS, smem));
     if (per_sm < 1) return fail(c, PD_ECAPACITY, "network simplex kernel does not fit on an SM");

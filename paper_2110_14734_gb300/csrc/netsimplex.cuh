@@ -36,7 +36,7 @@ struct NSInst {
     int64_t block;     // pricing block (arcs)
     int64_t big;       // cost of the artificial arcs (more than any path cost)
     int32_t smem_nodes; // 1: hot node arrays live in shared memory
-    int32_t vec_explicit; // 1: tail, head and cost are 16-byte aligned (vector loads)
+    int32_t minor;     // 1: between block pricings, the other warps' winners of the last block are re-priced (candidate list)
     int32_t init_tree;  // 1: pi, pred, parent, flow, up, ord, pos, size hold a strongly feasible start
     int32_t pad1;
     int64_t scanned;   // result: arcs priced
@@ -55,6 +55,9 @@ struct NSInst {
 __global__ void k_netsimplex(NSInst* insts, const int32_t* __restrict__ order, int32_t count,
                              int32_t* __restrict__ next);
 size_t ns_smem_bytes(int64_t N1);
+// Raises the kernel's dynamic shared memory limit on the current device once,
+// to the most any instance uses (thread-safe; never lowers it).
+cudaError_t ns_kernel_setup();
 // True if the compact node arrays of N1 nodes fit in shared memory beside the
 // kernel's static shared memory (max_optin: the device's opt-in limit per CTA).
 bool ns_smem_fits(int64_t N1, int max_optin);

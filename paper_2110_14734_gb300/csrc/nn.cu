@@ -5,15 +5,20 @@
 // a lower bound on OPT_int, a wave of pairs at a time through the batched
 // solve, and a pair whose bound exceeds the best optimum found is skipped.
 //
-// The bound.  RWMD (Algorithm 1) of the 0-condensed diagrams is a lower bound
-// on the real W1 of the pair; delta-condensation (Algorithm 2) moves every
-// point by at most sqrt(2) (G/2 + P) <= delta / sqrt(2), which by the choice
-// of delta totals at most eps_c * L_lo <= eps_c * RWMD (eps_c = 8 / (s - 4)),
-// and OPT_int, with costs rounded up on a network whose paths are never
-// shorter than the direct routes, is at least the real W1 of the condensed
-// diagrams.  Hence OPT_int >= (1 - eps_c) RWMD.  The bound only has to be a
-// valid lower bound, so the RWMD here is computed in float32 over all
-// database nodes at once, every distance shrunk by 2^-20 to cover rounding.
+// The bounds.  RWMD (Algorithm 1) of the 0-condensed diagrams is a lower
+// bound on the real W1 of the pair, and so is half the word centroid distance
+// of A + B~ against B + A~ (Appendix, WCD; ~ = diagonal projections), which
+// reduces to |T_A - T_B| / (2 sqrt 2) with T the total persistence sum
+// (d - b): each point minus its projection is (b - d, d - b) / 2.
+// delta-condensation (Algorithm 2) moves every point by at most
+// sqrt(2) (G/2 + P) <= delta / sqrt(2), which by the choice of delta totals at
+// most eps_c * L_lo <= eps_c * W1 (eps_c = 8 / (s - 4)), and OPT_int, with
+// costs rounded up on a network whose paths are never shorter than the direct
+// routes, is at least the real W1 of the condensed diagrams.  Hence
+// OPT_int >= (1 - eps_c) max(RWMD, WCD / 2).  The RWMD only has to be a valid
+// lower bound, so it is computed in float32 over all database nodes at once,
+// every distance shrunk by 2^-20 to cover rounding; the WCD comes from exact
+// integer persistence sums (one per database diagram, summed at build time).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -63,6 +68,16 @@ __global__ void k_db_pack(const int32_t* __restrict__ X, const int32_t* __restri
     if (x >= LB_EXACT || x <= -LB_EXACT || y >= LB_EXACT || y <= -LB_EXACT) *big = 1;
 }
 
+// Total persistence sum cnt * (Y - X) of a diagram's 0-condensed nodes into
+// *out (two's-complement 64-bit sums: exact and order-free).
+__global__ void k_pers_sum(const int32_t* __restrict__ X, const int32_t* __restrict__ Y,
+                           const int64_t* __restrict__ cnt, int64_t n, unsigned long long* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    long long v = i < n ? (long long)cnt[i] * ((long long)Y[i] - X[i]) : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0) atomicAdd(out, (unsigned long long)v);
+}
+
 // Staging (raw offsets, id -1 in the gaps) -> compact store.
 __global__ void k_db_compact(const float2* __restrict__ sxy, const int32_t* __restrict__ sc,
                              const int32_t* __restrict__ sid, int64_t n, const int64_t* __restrict__ roff,
@@ -78,13 +93,12 @@ __global__ void k_db_compact(const float2* __restrict__ sxy, const int32_t* __re
     ids[d] = id;
 }
 
-// Database side: every database node v adds cnt(v) * min(d(v, query), d_diag(v))
-// to L_B of its diagram.
+// Database side: every database node v gets cnt(v) * min(d(v, query), d_diag(v)),
+// its term of L_B of its diagram (summed per diagram by k_lb_segsum).
 __global__ void __launch_bounds__(LB_THREADS) k_lb_db_side(const float2* __restrict__ dxy,
-                                                           const int32_t* __restrict__ dcnt,
-                                                           const int32_t* __restrict__ did, int64_t T,
+                                                           const int32_t* __restrict__ dcnt, int64_t T,
                                                            const float2* __restrict__ qxy, int64_t nq,
-                                                           float margin, double* __restrict__ LBsum) {
+                                                           float margin, double* __restrict__ val) {
     __shared__ float2 sq[LB_TILE];
     const int64_t base = (int64_t)blockIdx.x * (LB_THREADS * LB_R);
     float2 p[LB_R];
@@ -110,31 +124,41 @@ __global__ void __launch_bounds__(LB_THREADS) k_lb_db_side(const float2* __restr
             }
         }
     }
-    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int r = 0; r < LB_R; r++) {
         int64_t v = base + r * LB_THREADS + threadIdx.x;
-        int32_t id = v < T ? did[v] : -1;
-        double val = 0.0;
-        if (v < T) val = (double)dcnt[v] * (double)fminf(dist_lb(m[r], margin), diag_lb(p[r], margin));
-        // sum per diagram id within the warp, one atomic per distinct id
-        unsigned peers = __match_any_sync(0xffffffffu, id);
-        double tot = 0.0;
-        for (int l = 0; l < 32; l++) {
-            double o = __shfl_sync(0xffffffffu, val, l);
-            if ((peers >> l) & 1u) tot += o;
-        }
-        if (id >= 0 && lane == __ffs(peers) - 1) atomicAdd(&LBsum[id], tot);
+        if (v < T) val[v] = (double)dcnt[v] * (double)fminf(dist_lb(m[r], margin), diag_lb(p[r], margin));
     }
 }
 
+// Sum of the values of [off[i], off[i + 1]) for every diagram i (one block per
+// diagram, a fixed order of additions: the same bits on every run).
+__global__ void __launch_bounds__(LB_THREADS) k_lb_segsum(const double* __restrict__ val,
+                                                          const int64_t* __restrict__ off, int64_t stride,
+                                                          double* __restrict__ out) {
+    __shared__ double red[LB_THREADS];
+    const int64_t i = blockIdx.x;
+    const int64_t b0 = stride > 0 ? i * stride : off[i];
+    const int64_t b1 = stride > 0 ? b0 + stride : off[i + 1];
+    double t = 0.0;
+    for (int64_t v = b0 + threadIdx.x; v < b1; v += LB_THREADS) t += val[v];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int h = LB_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = red[0];
+}
+
 // Query side: blockIdx.y = database diagram i; every query node u adds
-// cnt(u) * min(d(u, D_i), d_diag(u)) to L_A of diagram i.
+// cnt(u) * min(d(u, D_i), d_diag(u)) to the block's partial sum of L_A of
+// diagram i, part[i * gridDim.x + blockIdx.x] (summed by k_lb_segsum).
 __global__ void __launch_bounds__(LB_THREADS) k_lb_query_side(const float2* __restrict__ qxy,
                                                               const int32_t* __restrict__ qcnt, int64_t nq,
                                                               const float2* __restrict__ dxy,
                                                               const int64_t* __restrict__ doff, float margin,
-                                                              double* __restrict__ LAsum) {
+                                                              double* __restrict__ part) {
     __shared__ float2 sd[LB_TILE];
     __shared__ double red[LB_THREADS / 32];
     const int32_t i = blockIdx.y;
@@ -175,7 +199,7 @@ __global__ void __launch_bounds__(LB_THREADS) k_lb_query_side(const float2* __re
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < LB_THREADS / 32; w++) t += red[w];
-        if (t != 0.0) atomicAdd(&LAsum[i], t);
+        part[(int64_t)i * gridDim.x + blockIdx.x] = t;
     }
 }
 
@@ -217,8 +241,10 @@ extern "C" pd_status pd_db_build(pd_ctx* cx, const pd_diagram* dbs, int64_t n_db
     int32_t* sid = bufT<int32_t>(c, B_DB_SID, R);
     if (!sxy || !sc || !sid) return PD_ENOMEM;
     int32_t* big = bufT<int32_t>(c, B_DB_BIG, 2);
-    if (!big) return PD_ENOMEM;
+    unsigned long long* pers = bufT<unsigned long long>(c, B_DB_PERS, n_db + 1);
+    if (!big || !pers) return PD_ENOMEM;
     PD_TRY_CUDA(c, cudaMemsetAsync(big, 0, sizeof(int32_t) * 2, st));
+    PD_TRY_CUDA(c, cudaMemsetAsync(pers, 0, sizeof(unsigned long long) * (n_db + 1), st));
     if (R > 0) PD_TRY_CUDA(c, cudaMemsetAsync(sid, 0xff, sizeof(int32_t) * R, st));
     const pd_diagram empty{nullptr, 0, dtype, 0};
     for (int64_t i = 0; i < n_db; i++) {
@@ -227,9 +253,11 @@ extern "C" pd_status pd_db_build(pd_ctx* cx, const pd_diagram* dbs, int64_t n_db
         Hats h;
         pd_status e = stage_condense0(c, a, b, k, &h, st);
         if (e != PD_OK) return fail(c, e, "database diagram " + std::to_string(i) + ": " + c->err);
-        if (h.nA > 0)
+        if (h.nA > 0) {
             k_db_pack<<<grid_for(h.nA, 256), 256, 0, st>>>(h.X, h.Y, h.cnt, h.nA, (int32_t)i, roff[(size_t)i], sxy, sc,
                                                              sid, big); pd::count_launch();
+            k_pers_sum<<<grid_for(h.nA, 256), 256, 0, st>>>(h.X, h.Y, h.cnt, h.nA, pers + i); pd::count_launch();
+        }
         PD_TRY_CUDA(c, cudaGetLastError());
         hats[(size_t)i] = h.nA;
     }
@@ -246,9 +274,13 @@ extern "C" pd_status pd_db_build(pd_ctx* cx, const pd_diagram* dbs, int64_t n_db
     if (R > 0) k_db_compact<<<grid_for(R, 256), 256, 0, st>>>(sxy, sc, sid, R, droff, doff, xy, cn, ids); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     int32_t hbig = 0;
+    std::vector<int64_t> hp((size_t)n_db + 1);
     PD_TRY_CUDA(c, cudaMemcpyAsync(&hbig, big, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PD_TRY_CUDA(c, cudaMemcpyAsync(hp.data(), pers, sizeof(int64_t) * (n_db + 1), cudaMemcpyDeviceToHost, st));
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     c->db_big = hbig != 0;
+    hp.resize((size_t)n_db);
+    c->db_pers = hp;
     c->db.assign(dbs, dbs + n_db);
     c->db_hats = hats;
     c->db_total = T;
@@ -258,7 +290,8 @@ extern "C" pd_status pd_db_build(pd_ctx* cx, const pd_diagram* dbs, int64_t n_db
 }
 
 extern "C" pd_status pd_nn_search(pd_ctx* cx, pd_diagram query, double eps, const pd_opts* opts,
-                                  pd_nn_result* out, int64_t* opt_out, int64_t* lb_out, void* stream) {
+                                  pd_nn_result* out, int64_t* opt_out, int64_t* lb_out, int64_t* wcd_out,
+                                  void* stream) {
     Ctx* c = cx;
     if (!c || !out) return PD_EINVAL;
     c->err.clear();
@@ -303,27 +336,45 @@ extern "C" pd_status pd_nn_search(pd_ctx* cx, pd_diagram query, double eps, cons
     if (!qxy || !qc || !LA) return PD_ENOMEM;
     double* LB = LA + n_db;
     int32_t* big = bufT<int32_t>(c, B_DB_BIG, 2);
-    if (!big) return PD_ENOMEM;
+    unsigned long long* pers = bufT<unsigned long long>(c, B_DB_PERS, n_db + 1);
+    if (!big || !pers) return PD_ENOMEM;
     PD_TRY_CUDA(c, cudaMemsetAsync(big + 1, 0, sizeof(int32_t), st));
-    if (nq > 0) k_db_pack<<<grid_for(nq, 256), 256, 0, st>>>(h.X, h.Y, h.cnt, nq, 0, 0, qxy, qc, nullptr, big + 1); pd::count_launch();
+    PD_TRY_CUDA(c, cudaMemsetAsync(pers + n_db, 0, sizeof(unsigned long long), st));
+    if (nq > 0) {
+        k_db_pack<<<grid_for(nq, 256), 256, 0, st>>>(h.X, h.Y, h.cnt, nq, 0, 0, qxy, qc, nullptr, big + 1); pd::count_launch();
+        k_pers_sum<<<grid_for(nq, 256), 256, 0, st>>>(h.X, h.Y, h.cnt, nq, pers + n_db); pd::count_launch();
+    }
     int32_t qbig = 0;
+    int64_t qpers = 0;
     PD_TRY_CUDA(c, cudaMemcpyAsync(&qbig, big + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PD_TRY_CUDA(c, cudaMemcpyAsync(&qpers, pers + n_db, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     const float margin = (qbig || c->db_big) ? LB_MARGIN : 0.f;
-    PD_TRY_CUDA(c, cudaMemsetAsync(LA, 0, sizeof(double) * 2 * n_db, st));
     const int64_t T = c->db_total;
     const int64_t per = (int64_t)LB_THREADS * LB_R;
-    if (T > 0)
+    const int64_t gq = (nq + per - 1) / per;  // query tiles: partial sums per diagram
+    double* val = bufT<double>(c, B_DB_VAL, std::max<int64_t>(T, gq * n_db));
+    if (!val) return PD_ENOMEM;
+    // sums in a fixed order (no floating-point atomics): the bounds are the same bits on every run
+    if (T > 0) {
         k_lb_db_side<<<(unsigned)((T + per - 1) / per), LB_THREADS, 0, st>>>(
-            (const float2*)c->ptr[B_DB_XY], (const int32_t*)c->ptr[B_DB_CNT], (const int32_t*)c->ptr[B_DB_ID], T,
-            qxy, nq, margin, LB); pd::count_launch();
+            (const float2*)c->ptr[B_DB_XY], (const int32_t*)c->ptr[B_DB_CNT], T, qxy, nq, margin, val);
+        pd::count_launch();
+    }
+    k_lb_segsum<<<(unsigned)n_db, LB_THREADS, 0, st>>>(val, (const int64_t*)c->ptr[B_DB_OFF], 0, LB);
+    pd::count_launch();
+    PD_TRY_CUDA(c, cudaGetLastError());
     if (nq > 0) {
         for (int64_t y0 = 0; y0 < n_db; y0 += 65535) {
             const int64_t ny = std::min<int64_t>(65535, n_db - y0);
-            k_lb_query_side<<<dim3((unsigned)((nq + per - 1) / per), (unsigned)ny), LB_THREADS, 0, st>>>(
+            k_lb_query_side<<<dim3((unsigned)gq, (unsigned)ny), LB_THREADS, 0, st>>>(
                 qxy, qc, nq, (const float2*)c->ptr[B_DB_XY], (const int64_t*)c->ptr[B_DB_OFF] + y0, margin,
-                LA + y0); pd::count_launch();
+                val + y0 * gq); pd::count_launch();
         }
+        k_lb_segsum<<<(unsigned)n_db, LB_THREADS, 0, st>>>(val, nullptr, gq, LA);
+        pd::count_launch();
+    } else {
+        PD_TRY_CUDA(c, cudaMemsetAsync(LA, 0, sizeof(double) * n_db, st));
     }
     PD_TRY_CUDA(c, cudaGetLastError());
     PD_TRY_CUDA(c, cudaEventRecord(e1, st));
@@ -333,12 +384,21 @@ extern "C" pd_status pd_nn_search(pd_ctx* cx, pd_diagram query, double eps, cons
     cudaEventElapsedTime(&r.lb_ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    // OPT_int >= (1 - eps_c) RWMD; the last factor covers double rounding
+    // OPT_int >= (1 - eps_c) max(RWMD, WCD / 2); the last factor covers double rounding
     const double ec = o.condense ? (s >= 12 ? 8.0 / (double)(s - 4) : 1.0) : 0.0;
-    std::vector<int64_t> lb((size_t)n_db);
+    std::vector<int64_t> lb((size_t)n_db), lbw((size_t)n_db);
     for (int64_t i = 0; i < n_db; i++) {
         double L = std::max(hl[(size_t)i], hl[(size_t)(n_db + i)]) * (1.0 - ec) * (1.0 - 1e-9);
         lb[(size_t)i] = L > 0.0 ? (int64_t)std::floor(L) : 0;
+        // WCD / 2 = |T_q - T_i| / (2 sqrt(2)): the persistence sums are exact
+        // integers; the double quotient is shrunk to cover its rounding
+        const double dT = std::fabs((double)(qpers - c->db_pers[(size_t)i]));
+        const double W = dT / (2.0 * std::sqrt(2.0)) * (1.0 - ec) * (1.0 - 1e-9);
+        lbw[(size_t)i] = W > 0.0 ? (int64_t)std::floor(W) : 0;
+        if (lbw[(size_t)i] > lb[(size_t)i]) {
+            r.wcd_above++;
+            lb[(size_t)i] = lbw[(size_t)i];
+        }
     }
     // ---- waves in ascending bound ------------------------------------------
     std::vector<int64_t> order((size_t)n_db), opt((size_t)n_db, -1);
@@ -383,6 +443,7 @@ extern "C" pd_status pd_nn_search(pd_ctx* cx, pd_diagram query, double eps, cons
     r.total_ms = ms_since(t_all);
     if (opt_out) std::copy(opt.begin(), opt.end(), opt_out);
     if (lb_out) std::copy(lb.begin(), lb.end(), lb_out);
+    if (wcd_out) std::copy(lbw.begin(), lbw.end(), wcd_out);
     *out = r;
     return PD_OK;
 }

@@ -136,7 +136,6 @@ extern "C" pd_status pd_mcf_solve_noalloc(const pd_network* net, int64_t* opt_ou
     h.cost = c32;
     h.supply = net->supply;
     h.big = N1 * (cmax + 1) + 1;
-    h.vec_explicit = ((((uintptr_t)tail) | ((uintptr_t)net->head) | ((uintptr_t)c32)) & 15) == 0 ? 1 : 0;
     h.pi = (int64_t*)(base + OFF_PI);
     h.pred = (int32_t*)(base + OFF_PRED);
     h.parent = (int32_t*)(base + OFF_PARENT);
@@ -160,7 +159,7 @@ extern "C" pd_status pd_mcf_solve_noalloc(const pd_network* net, int64_t* opt_ou
     size_t smem = ns_smem_bytes(N1);
     h.smem_nodes = ns_smem_fits(N1, max_optin) ? 1 : 0;
     if (!h.smem_nodes) smem = 0;
-    NA_TRY(cudaFuncSetAttribute(k_netsimplex, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    NA_TRY(ns_kernel_setup());
     NA_TRY(cudaMemcpyAsync(dinst, &h, sizeof(NSInst), cudaMemcpyHostToDevice, st));
     int32_t* order = (int32_t*)(flags + 4);  // zeroed with the flags: order = {0}, next = 0
     k_netsimplex<<<1, NS_THREADS, smem, st>>>(dinst, order, 1, order + 1); pd::count_launch();

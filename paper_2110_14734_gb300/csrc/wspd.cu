@@ -462,7 +462,8 @@ pd_status merge_diagonal(Ctx* c, const pd_network& net, int64_t N, pd_network* o
 }
 
 pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* out, float* ms_tree,
-                        float* ms_wspd, float* ms_csr, cudaStream_t st, bool count_only, WsTree* tree) {
+                        float* ms_wspd, float* ms_csr, cudaStream_t st, bool count_only, WsTree* tree,
+                        const WsTree* given) {
     int64_t N = nodes.n_nodes;
     if (N >= (int64_t(1) << 31) - 4) return fail(c, PD_ECAPACITY, "more than 2^31 - 4 condensed nodes");
     if (s < 1) return fail(c, PD_EINVAL, "WSPD parameter s must be >= 1");
@@ -470,20 +471,36 @@ pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* ou
     for (int q = 0; q < 4; q++) PD_TRY_CUDA(c, cudaEventCreate(&ev[q]));
     PD_TRY_CUDA(c, cudaEventRecord(ev[0], st));
     int64_t M = N > 1 ? N - 1 : 1;
-    int32_t* left = bufT<int32_t>(c, B_T_LEFT, M);
-    int32_t* right = bufT<int32_t>(c, B_T_RIGHT, M);
-    int4* bb = bufT<int4>(c, B_T_BB, M);
-    int32_t* rep = bufT<int32_t>(c, B_T_REP, M);
-    int32_t* par_int = bufT<int32_t>(c, B_T_PARENT, M);
-    int32_t* par_leaf = bufT<int32_t>(c, B_T_LPARENT, N);
-    int32_t* visit = bufT<int32_t>(c, B_T_VISIT, M);
     unsigned long long* cnts = bufT<unsigned long long>(c, B_SMALL, 64);
-    if (!left || !right || !bb || !rep || !par_int || !par_leaf || !visit || !cnts) return PD_ENOMEM;
-    if (N >= 2) {
-        k_karras<<<grid_for(N - 1, 256), 256, 0, st>>>(nodes.morton, N, left, right, par_int, par_leaf); pd::count_launch();
-        PD_TRY_CUDA(c, cudaMemsetAsync(visit, 0, sizeof(int32_t) * M, st));
-        k_bbox<<<grid_for(N, 256), 256, 0, st>>>(N, nodes.X, nodes.Y, left, right, par_int, par_leaf, bb, rep, visit); pd::count_launch();
-        PD_TRY_CUDA(c, cudaGetLastError());
+    if (!cnts) return PD_ENOMEM;
+    const int32_t *left, *right, *rep;
+    const int4* bb;
+    if (given) {
+        if (given->N != N || given->X != nodes.X || given->Y != nodes.Y)
+            return fail(c, PD_EINVAL, "the given tree is not over these nodes");
+        left = given->left;
+        right = given->right;
+        bb = given->bb;
+        rep = given->rep;
+    } else {
+        int32_t* l = bufT<int32_t>(c, B_T_LEFT, M);
+        int32_t* r = bufT<int32_t>(c, B_T_RIGHT, M);
+        int4* b = bufT<int4>(c, B_T_BB, M);
+        int32_t* rp = bufT<int32_t>(c, B_T_REP, M);
+        int32_t* par_int = bufT<int32_t>(c, B_T_PARENT, M);
+        int32_t* par_leaf = bufT<int32_t>(c, B_T_LPARENT, N);
+        int32_t* visit = bufT<int32_t>(c, B_T_VISIT, M);
+        if (!l || !r || !b || !rp || !par_int || !par_leaf || !visit) return PD_ENOMEM;
+        left = l;
+        right = r;
+        bb = b;
+        rep = rp;
+        if (N >= 2) {
+            k_karras<<<grid_for(N - 1, 256), 256, 0, st>>>(nodes.morton, N, l, r, par_int, par_leaf); pd::count_launch();
+            PD_TRY_CUDA(c, cudaMemsetAsync(visit, 0, sizeof(int32_t) * M, st));
+            k_bbox<<<grid_for(N, 256), 256, 0, st>>>(N, nodes.X, nodes.Y, l, r, par_int, par_leaf, b, rp, visit); pd::count_launch();
+            PD_TRY_CUDA(c, cudaGetLastError());
+        }
     }
     PD_TRY_CUDA(c, cudaEventRecord(ev[1], st));
     if (tree) *tree = WsTree{N, nodes.X, nodes.Y, left, right, bb, rep};

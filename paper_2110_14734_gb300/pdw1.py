@@ -37,7 +37,8 @@ class pd_opts(C.Structure):
                 ("seq_threshold", C.c_int32), ("solver", C.c_int32), ("ns_block", C.c_int64),
                 ("ns_transport", C.c_int32), ("ns_smem", C.c_int32), ("batch_slots", C.c_int32),
                 ("batch_threads", C.c_int32),
-                ("nn_prune", C.c_int32), ("warm_start", C.c_int32)]
+                ("nn_prune", C.c_int32), ("warm_start", C.c_int32), ("ns_candidates", C.c_int32),
+                ("tree", C.c_int32)]
 
 
 class pd_nodes(C.Structure):
@@ -72,7 +73,7 @@ class pd_result(C.Structure):
 class pd_nn_result(C.Structure):
     _fields_ = [("nn_index", C.c_int64), ("nn_opt_quanta", C.c_int64), ("nn_w1", C.c_double),
                 ("solved", C.c_int64), ("pruned", C.c_int64), ("waves", C.c_int32), ("coord_shift", C.c_int32),
-                ("lb_ms", C.c_float), ("solve_ms", C.c_float), ("total_ms", C.c_float), ("reserved", C.c_int32)]
+                ("lb_ms", C.c_float), ("solve_ms", C.c_float), ("total_ms", C.c_float), ("wcd_above", C.c_int32)]
 
     def to_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -109,12 +110,21 @@ _lib.pd_rwmd_lower_bound.argtypes = [C.c_void_p, pd_diagram, pd_diagram, C.POINT
                                      C.POINTER(C.c_int64), C.c_void_p]
 _lib.pd_wspd_sparsify.restype = C.c_int
 _lib.pd_wspd_sparsify.argtypes = [C.c_void_p, C.POINTER(pd_nodes), C.c_int32, C.POINTER(pd_network), C.c_void_p]
+_lib.pd_wspd_count.restype = C.c_int
+_lib.pd_wspd_count.argtypes = [C.c_void_p, C.POINTER(pd_nodes), C.c_int32, C.c_int32, C.POINTER(C.c_int64),
+                               C.c_void_p]
+_lib.pd_wspd_sparsify_tree.restype = C.c_int
+_lib.pd_wspd_sparsify_tree.argtypes = [C.c_void_p, C.POINTER(pd_nodes), C.c_int32, C.c_int32, C.POINTER(pd_nodes),
+                                       C.POINTER(pd_network), C.c_void_p]
 _lib.pd_mcf_solve.restype = C.c_int
 _lib.pd_mcf_solve.argtypes = [C.c_void_p, C.POINTER(pd_network), C.POINTER(pd_opts), C.POINTER(C.c_int64),
                               C.POINTER(pd_result), C.c_void_p]
 _lib.pd_w1_approx.restype = C.c_int
 _lib.pd_w1_approx.argtypes = [C.c_void_p, pd_diagram, pd_diagram, C.c_double, C.POINTER(pd_opts),
                               C.POINTER(pd_result), C.c_void_p]
+_lib.pd_w1_sparsify_count.restype = C.c_int
+_lib.pd_w1_sparsify_count.argtypes = [C.c_void_p, pd_diagram, pd_diagram, C.c_double, C.POINTER(pd_opts),
+                                      C.POINTER(pd_result), C.c_void_p]
 _lib.pd_w1_approx_batch.restype = C.c_int
 _lib.pd_w1_approx_batch.argtypes = [C.c_void_p, C.POINTER(pd_diagram), C.POINTER(pd_diagram), C.c_int64,
                                     C.c_double, C.POINTER(pd_opts), C.POINTER(pd_result), C.c_void_p]
@@ -123,7 +133,21 @@ _lib.pd_db_build.restype = C.c_int
 _lib.pd_db_build.argtypes = [C.c_void_p, C.POINTER(pd_diagram), C.c_int64, C.POINTER(pd_opts), C.c_void_p]
 _lib.pd_nn_search.restype = C.c_int
 _lib.pd_nn_search.argtypes = [C.c_void_p, pd_diagram, C.c_double, C.POINTER(pd_opts), C.POINTER(pd_nn_result),
-                              C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_void_p]
+                              C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_void_p]
+
+class pd_tune_result(C.Structure):
+    _fields_ = [("ns_block", C.c_int64), ("size_class", C.c_int32), ("candidates", C.c_int32), ("pairs", C.c_int32),
+                ("from_cache", C.c_int32), ("best_ms", C.c_float), ("default_ms", C.c_float)]
+
+    def to_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib.pd_autotune.restype = C.c_int
+_lib.pd_autotune.argtypes = [C.c_void_p, C.POINTER(pd_diagram), C.POINTER(pd_diagram), C.c_int64, C.c_double,
+                             C.POINTER(pd_opts), C.c_char_p, C.POINTER(pd_tune_result), C.c_void_p]
+_lib.pd_tuned_block.restype = C.c_int
+_lib.pd_tuned_block.argtypes = [C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
 
 _F32P = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
 _lib.pd_ws_train.restype = C.c_int
@@ -291,6 +315,37 @@ def pd_wspd_sparsify(ctx: Context, nodes: dict, s: int, stream=None) -> dict:
                 supply=_copy_out(out.supply, n, torch.int64, dev, st))
 
 
+def pd_wspd_sparsify_tree(ctx: Context, nodes: dict, s: int, tree: int, stream=None) -> tuple:
+    """As pd_wspd_sparsify on the radix tree (tree=0) or the paper's split tree
+    (tree=1).  Returns (network dict, nodes dict in the tree's leaf order)."""
+    N = int(nodes["X"].numel())
+    keep = [nodes[k].contiguous() for k in ("X", "Y", "cntA", "cntB", "morton")]
+    nd = pd_nodes(N, *[C.c_void_p(t.data_ptr() if N else 0) for t in keep])
+    out = pd_network()
+    ordered = pd_nodes()
+    st = _stream(stream)
+    ctx.check(_lib.pd_wspd_sparsify_tree(ctx.ptr, C.byref(nd), int(s), int(tree), C.byref(ordered), C.byref(out),
+                                         C.c_void_p(st)))
+    dev = torch.device("cuda", ctx.device)
+    n, m = out.n_nodes, out.n_arcs
+    net = dict(n_nodes=n, n_arcs=m, row_ptr=_copy_out(out.row_ptr, n + 1, torch.int64, dev, st),
+               head=_copy_out(out.head, m, torch.int32, dev, st), cost=_copy_out(out.cost, m, torch.int64, dev, st),
+               supply=_copy_out(out.supply, n, torch.int64, dev, st))
+    nds = dict(X=_copy_out(ordered.X, N, torch.int32, dev, st), Y=_copy_out(ordered.Y, N, torch.int32, dev, st),
+               cntA=_copy_out(ordered.cntA, N, torch.int64, dev, st), cntB=_copy_out(ordered.cntB, N, torch.int64, dev, st))
+    return net, nds
+
+
+def pd_wspd_count(ctx: Context, nodes: dict, s: int, tree: int = 0, stream=None) -> int:
+    """Arcs of the sparse network over `nodes` (as pd_wspd_sparsify_tree), counted without building it."""
+    N = int(nodes["X"].numel())
+    keep = [nodes[k].contiguous() for k in ("X", "Y", "cntA", "cntB", "morton")]
+    nd = pd_nodes(N, *[C.c_void_p(t.data_ptr() if N else 0) for t in keep])
+    m = C.c_int64()
+    ctx.check(_lib.pd_wspd_count(ctx.ptr, C.byref(nd), int(s), int(tree), C.byref(m), C.c_void_p(_stream(stream))))
+    return int(m.value)
+
+
 def pd_mcf_solve(ctx: Context, net: dict, o: pd_opts | None = None, stream=None):
     """net: dict of cuda tensors row_ptr, head, cost, supply (int64 / int32).
     Returns (OPT, stats dict)."""
@@ -304,6 +359,16 @@ def pd_mcf_solve(ctx: Context, net: dict, o: pd_opts | None = None, stream=None)
     ctx.check(_lib.pd_mcf_solve(ctx.ptr, C.byref(nw), C.byref(o) if o else None, C.byref(opt), C.byref(res),
                                 C.c_void_p(_stream(stream))))
     return int(opt.value), res.to_dict()
+
+
+def pd_w1_sparsify_count(ctx: Context, A, B, eps: float, o: pd_opts | None = None, stream=None) -> dict:
+    """Algorithm 4 up to the sparse network (arcs counted, nothing solved): the result dict's sizes."""
+    da, ka = diagram(A)
+    db, kb = diagram(B)
+    res = pd_result()
+    ctx.check(_lib.pd_w1_sparsify_count(ctx.ptr, da, db, float(eps), C.byref(o) if o else None, C.byref(res),
+                                        C.c_void_p(_stream(stream))))
+    return res.to_dict()
 
 
 def pd_w1_approx(ctx: Context, A, B, eps: float, o: pd_opts | None = None, stream=None) -> dict:
@@ -353,18 +418,44 @@ def pd_db_build(ctx: Context, dbs, o: pd_opts | None = None, stream=None):
 
 def pd_nn_search(ctx: Context, query, eps: float, o: pd_opts | None = None, stream=None) -> dict:
     """Nearest neighbour of `query` in the database: dict of pd_nn_result plus
-    per-diagram `opt` (-1 where pruned) and `lb` lists."""
+    per-diagram `opt` (-1 where pruned), `lb` (the bound used) and `wcd` (the
+    WCD bound alone) lists."""
     dq, kq = diagram(query)
     n = len(getattr(ctx, "_db_keep", []))
     res = pd_nn_result()
     opt = (C.c_int64 * max(n, 1))()
     lb = (C.c_int64 * max(n, 1))()
-    ctx.check(_lib.pd_nn_search(ctx.ptr, dq, float(eps), C.byref(o) if o else None, C.byref(res), opt, lb,
+    wcd = (C.c_int64 * max(n, 1))()
+    ctx.check(_lib.pd_nn_search(ctx.ptr, dq, float(eps), C.byref(o) if o else None, C.byref(res), opt, lb, wcd,
                                 C.c_void_p(_stream(stream))))
     d = res.to_dict()
     d["opt"] = [int(opt[i]) for i in range(n)]
     d["lb"] = [int(lb[i]) for i in range(n)]
+    d["wcd"] = [int(wcd[i]) for i in range(n)]
     return d
+
+
+def pd_autotune(ctx: Context, As, Bs, eps: float, o: pd_opts | None = None, cache_path: str | None = None,
+                stream=None) -> dict:
+    """Time the simplex's pricing block on the sample pairs; the context keeps the best per size class."""
+    n = len(As)
+    da = (pd_diagram * max(n, 1))()
+    db = (pd_diagram * max(n, 1))()
+    keep = []
+    for i in range(n):
+        da[i], ka = diagram(As[i])
+        db[i], kb = diagram(Bs[i])
+        keep += [ka, kb]
+    res = pd_tune_result()
+    ctx.check(_lib.pd_autotune(ctx.ptr, da, db, n, float(eps), C.byref(o) if o else None,
+                               cache_path.encode() if cache_path else None, C.byref(res), C.c_void_p(_stream(stream))))
+    return res.to_dict()
+
+
+def pd_tuned_block(ctx: Context, arcs_and_nodes: int) -> int:
+    b = C.c_int64()
+    ctx.check(_lib.pd_tuned_block(ctx.ptr, int(arcs_and_nodes), C.byref(b)))
+    return int(b.value)
 
 
 def pd_ws_train(ctx: Context, As, Bs, eps: float, o: pd_opts | None = None, epochs: int = 20, lr: float = 1e-3,

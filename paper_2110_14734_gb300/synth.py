@@ -13,6 +13,8 @@ oracle and the CUDA library both draw their inputs from these functions.
   experiments stand behind this shape; the datasets themselves are not used).
 * mixture_f32(n, seed): b ~ U[0,1], persistence p ~ 0.95 Exp(mean 0.01) +
   0.05 U[0, 0.5], d = b + p, float32, few duplicates.
+* gaussian_pd(n, seed): points of a 2D Gaussian mirrored above the diagonal
+  (the synthetic Gaussian diagrams of the empirical-complexity experiment).
 * db_sizes(count, seed, lo, hi): log-uniform diagram sizes in [lo, hi].
 """
 from __future__ import annotations
@@ -63,6 +65,17 @@ def mixture_f32(n: int, seed: int) -> np.ndarray:
     pick = rng.random(n) < 0.95
     p = np.where(pick, rng.exponential(0.01, n), rng.random(n) * 0.5)
     return np.stack([b, b + p], axis=1).astype(np.float32)
+
+
+def gaussian_pd(n: int, seed: int) -> np.ndarray:
+    """Synthetic Gaussian diagram (the empirical-complexity experiment of the
+    appendix): n points of a 2D Gaussian (mean (0.4, 0.6), standard deviation
+    0.15 per axis, independent), each point mirrored above the diagonal
+    (birth <= death), float32.  Not a persistence diagram of any filtration."""
+    rng = np.random.default_rng(seed)
+    x = rng.normal(0.4, 0.15, n)
+    y = rng.normal(0.6, 0.15, n)
+    return np.stack([np.minimum(x, y), np.maximum(x, y)], axis=1).astype(np.float32)
 
 
 def _gauss_smooth(img: np.ndarray, sigma: float) -> np.ndarray:

@@ -86,3 +86,52 @@ def test_nn_empty_database_and_bad_queries(pd, ctx):
         pd.pd_nn_search(ctx, _cuda(synth.uniform_exp(100, 1)), 0.0)
     with pytest.raises(pd.PDError):
         pd.pd_db_build(ctx, [_cuda(synth.uniform_exp(50, 2)), _cuda(synth.lowerstar_u8(60, 3))])
+
+
+def test_nn_coordinates_beyond_float32_exactness(pd, ctx):
+    """Every diagram translated along (t, t) to coordinates >= 2^23 quanta,
+    where float32 stops being exact: the bound takes its absolute margin and
+    must stay below every optimum; the answer equals the oracle's, with and
+    without pruning, and the bounds are the same bits on every call (fixed
+    order of summation)."""
+    db = [(d + 100.0).astype(np.float32) for d in _db(10, 17)]
+    q = (synth.uniform_exp(600, 77) + 100.0).astype(np.float32)
+    assert (q * 2.0 ** 20).min() >= 2 ** 23
+    eps = 0.1
+    pd.pd_db_build(ctx, [_cuda(d) for d in db])
+    full = pd.pd_nn_search(ctx, _cuda(q), eps, pd.opts(nn_prune=0))
+    idx, opts = oracle.nn_search(q, db, "f32", eps=eps)
+    assert full["opt"] == opts and full["nn_index"] == idx
+    assert all(0 <= lb <= o for lb, o in zip(full["lb"], opts))
+    pr = pd.pd_nn_search(ctx, _cuda(q), eps, pd.opts(batch_slots=3))
+    assert (pr["nn_index"], pr["nn_opt_quanta"]) == (idx, opts[idx])
+    assert pr["lb"] == full["lb"]
+
+
+def _hat(D, dtype):
+    k = oracle.default_shift(dtype)
+    return oracle.condense0(*oracle.quantize(D, dtype, k))
+
+
+def test_nn_wcd_bound_matches_the_oracle_and_stays_below_the_optimum(pd, ctx):
+    """The WCD bound (Appendix, WCD) of every pair equals (1 - eps_c) WCD / 2
+    of the oracle's definition (centroids of A + B~ and B + A~) on the
+    quantised diagrams, rounded down (within one quantum of double rounding);
+    the bound used is never below it and never above the optimum."""
+    db = _db(16, 23, lo=20, hi=900)
+    db[5] = np.concatenate([db[5], db[5]])  # twice the total persistence: the WCD bound grows
+    q = synth.uniform_exp(700, 55)
+    eps = 0.1
+    s = oracle.s_from_eps(eps)
+    ec = oracle.eps_c(s)
+    pd.pd_db_build(ctx, [_cuda(d) for d in db])
+    full = pd.pd_nn_search(ctx, _cuda(q), eps, pd.opts(nn_prune=0))
+    idx, opts = oracle.nn_search(q, db, "f32", eps=eps)
+    assert full["opt"] == opts and full["nn_index"] == idx
+    qh = _hat(q, "f32")
+    for i, d in enumerate(db):
+        w = oracle.wcd(qh, _hat(d, "f32"))
+        exp = int(np.floor((1 - ec) * w / 2))
+        assert abs(full["wcd"][i] - exp) <= 1
+        assert full["wcd"][i] <= full["lb"][i] <= opts[i]
+    assert 0 <= full["wcd_above"] <= sum(1 for i in range(len(db)) if full["wcd"][i] == full["lb"][i])

@@ -137,6 +137,48 @@ def test_wspd_network_matches_oracle(pd, ctx, s):
     _assert_network(got, exp)
 
 
+@pytest.mark.parametrize("s", [1, 3, 13, 40, 167])
+def test_split_tree_network_matches_oracle(pd, ctx, s):
+    """The paper's split tree: the nodes in its leaf order and the whole CSR
+    network over them, bit-exact with the oracle's sequential recursion."""
+    A, B = synth.uniform_exp(1500, 33), synth.uniform_exp(1400, 34)
+    Ah, Bh = _oracle_hats(A, B, "f32", 20)
+    nodes = oracle.condense_delta(Ah, Bh, 600, 2, 9)
+    perm, tree = oracle.split_tree(nodes)
+    ordered = oracle.reorder(nodes, perm)
+    exp = oracle.build_network(ordered, *oracle.wspd(ordered, tree, s))
+    got, gn = pd.pd_wspd_sparsify_tree(ctx, _upload_nodes(nodes), s, 1)
+    for k in ("X", "Y", "cntA", "cntB"):
+        np.testing.assert_array_equal(_np(gn[k]), ordered[k])
+    _assert_network(got, exp)
+    assert pd.pd_wspd_count(ctx, _upload_nodes(nodes), s, 1) == int(exp["row_ptr"][-1])
+    # tree = 0 is the radix tree of pd_wspd_sparsify
+    got0, gn0 = pd.pd_wspd_sparsify_tree(ctx, _upload_nodes(nodes), s, 0)
+    exp0 = oracle.build_network(nodes, *oracle.wspd(nodes, oracle.radix_tree(nodes), s))
+    _assert_network(got0, exp0)
+    assert pd.pd_wspd_count(ctx, _upload_nodes(nodes), s, 0) == int(exp0["row_ptr"][-1])
+
+
+def test_split_tree_clustered_and_tiny(pd, ctx):
+    rng = np.random.default_rng(15)
+    ctr = rng.integers(0, 2**24, (10, 2))
+    pts = np.unique(np.concatenate([c + rng.integers(0, 3000, (200, 2)) for c in ctr]), axis=0)
+    Xs, Ys = pts[:, 0].astype(np.int32), pts[:, 1].astype(np.int32)
+    cnt = rng.integers(1, 4, len(Xs)).astype(np.int64)
+    half = len(Xs) // 2
+    empty = (np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int64))
+    for nodes in [oracle.condense_delta((Xs[:half], Ys[:half], cnt[:half]), (Xs[half:], Ys[half:], cnt[half:]),
+                                        1, 0, 0),
+                  oracle.condense_delta((Xs[:1], Ys[:1], cnt[:1]), empty, 1, 0, 0),
+                  oracle.condense_delta((Xs[:2], Ys[:2], cnt[:2]), (Xs[2:3], Ys[2:3], cnt[2:3]), 1, 0, 0)]:
+        perm, tree = oracle.split_tree(nodes)
+        ordered = oracle.reorder(nodes, perm)
+        for s in (3, 20):
+            got, gn = pd.pd_wspd_sparsify_tree(ctx, _upload_nodes(nodes), s, 1)
+            np.testing.assert_array_equal(_np(gn["X"]), ordered["X"])
+            _assert_network(got, oracle.build_network(ordered, *oracle.wspd(ordered, tree, s)))
+
+
 def test_wspd_network_clustered_and_tiny(pd, ctx):
     rng = np.random.default_rng(5)
     ctr = rng.integers(0, 2**24, (10, 2))
@@ -213,17 +255,18 @@ def test_mcf_on_w1_networks(pd, ctx, name):
 
 
 def _check_w1(pd, ctx, A, B, dt, eps, **kw):
-    r = oracle.w1_approx(A, B, dt, eps=eps, **{k: v for k, v in kw.items() if k in ("k", "s_override", "perturb",
-                                                                                     "seed", "condense")})
+    tree = kw.get("tree", "radix")
+    r = oracle.w1_approx(A, B, dt, eps=eps, tree=tree,
+                         **{k: v for k, v in kw.items() if k in ("k", "s_override", "perturb", "seed", "condense")})
     o = pd.opts(verify=1, s_override=kw.get("s_override", 0), perturb=int(kw.get("perturb", True)),
                 seed=kw.get("seed", 0), condense=int(kw.get("condense", True)),
-                coord_shift=kw.get("k", -1) if kw.get("k") is not None else -1)
+                coord_shift=kw.get("k", -1) if kw.get("k") is not None else -1, tree=int(tree == "split"))
     g = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), eps, o)
     assert (g["rwmd_A"], g["rwmd_B"]) == (r["LA"], r["LB"])
     # the simplex straight on the sparse network must agree as well
     g2 = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), eps, pd.opts(
         s_override=o.s_override, perturb=o.perturb, seed=o.seed, condense=o.condense, coord_shift=o.coord_shift,
-        ns_transport=0))
+        ns_transport=0, tree=o.tree))
     assert g2["opt_quanta"] == r["opt"] and g2["solve_method"] == 1
     assert g["s"] == r["s"] and g["cell_quanta"] == r["G"] and g["shift_quanta"] == r["P"]
     assert g["delta"] == r["delta"]
@@ -245,10 +288,19 @@ def test_w1_approx_uniform2k(pd, ctx, eps):
     assert (1 - eps) * w - slack <= g["w1"] <= (1 + eps) * w + slack
 
 
-@pytest.mark.parametrize("eps", [0.1, 0.05])
+@pytest.mark.parametrize("eps", [0.1, 0.05, 0.01])
 def test_w1_approx_lowerstar_u8(pd, ctx, eps):
     A, B = synth.lowerstar_u8(20000, 1000), synth.lowerstar_u8(20000, 1001)
     _check_w1(pd, ctx, A, B, "u8", eps)
+
+
+@pytest.mark.parametrize("name,eps", [("uniform2k", 0.1), ("lowerstar20k", 0.05), ("mixture5k", 0.1)])
+def test_w1_approx_on_the_split_tree(pd, ctx, name, eps):
+    """Algorithm 4 on the paper's split tree (pd_opts.tree = 1): every integer
+    result bit-exact with the oracle on the same tree, both solve paths."""
+    A, B, dt = PAIRS[name]()
+    g, r = _check_w1(pd, ctx, A, B, dt, eps, tree="split")
+    assert g["n_arcs"] == int(r["net"]["row_ptr"][-1])
 
 
 def test_w1_approx_edge_cases(pd, ctx):
@@ -271,6 +323,26 @@ def test_w1_approx_edge_cases(pd, ctx):
     assert g["opt_quanta"] == 0 and g["n_nodes"] == 0
 
 
+def test_cost_scaling_round_cap_and_time_limit_return_timeout(pd, ctx):
+    """The watchdogs of both solvers end a solve early with PD_ETIMEOUT and
+    leave the context usable: the cost-scaling kernel's round cap (every
+    block leaves through its bounded grid barriers) and the simplex's device
+    wall-clock limit (checked every 128 pivots)."""
+    A, B, dt = PAIRS["uniform2k"]()
+    r = oracle.w1_approx(A, B, dt, eps=0.5, solve=False)
+    net = {k: _cuda(r["net"][k]) for k in ("row_ptr", "head", "cost", "supply")}
+    for rounds in (1, 2, 5):
+        with pytest.raises(pd.PDError) as e:
+            pd.pd_mcf_solve(ctx, net, pd.opts(solver=1, max_rounds=rounds))
+        assert e.value.status == pd.PD_ETIMEOUT
+    L = synth.lowerstar_u8(20000, 1000), synth.lowerstar_u8(20000, 1001)
+    with pytest.raises(pd.PDError) as e:
+        pd.pd_w1_approx(ctx, _cuda(L[0]), _cuda(L[1]), 0.05, pd.opts(time_limit_ms=1))
+    assert e.value.status == pd.PD_ETIMEOUT
+    got, _ = pd.pd_mcf_solve(ctx, net, pd.opts(solver=1))
+    assert got == oracle.mcf(r["net"])[0]
+
+
 def test_solver_round_cap_returns_timeout(pd, ctx):
     A, B, dt = PAIRS["uniform2k"]()
     with pytest.raises(pd.PDError) as e:
@@ -280,11 +352,41 @@ def test_solver_round_cap_returns_timeout(pd, ctx):
     assert pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.5)["opt_quanta"] > 0
 
 
-def test_w1_approx_full_size_lowerstar_100k(pd, ctx):
-    """The benchmark workload (100k + 100k uint8 points, eps = 0.05), exact
-    parity of every integer result with the oracle."""
+@pytest.mark.parametrize("eps", [0.05, 0.1, 0.01])
+def test_w1_approx_full_size_lowerstar_100k(pd, ctx, eps):
+    """The benchmark workload (100k + 100k uint8 points) at every eps of the
+    lower-star configuration (s = 327, 167, 1607): exact parity of every
+    integer result with the oracle."""
     A, B = synth.lowerstar_u8(100000, 1000), synth.lowerstar_u8(100000, 1001)
-    _check_w1(pd, ctx, A, B, "u8", 0.05)
+    _check_w1(pd, ctx, A, B, "u8", eps)
+
+
+@pytest.mark.parametrize("n", [5000, 10000])
+def test_w1_approx_continuous_mixture(pd, ctx, n):
+    """Continuous float32 coordinates with few duplicates (birth U[0,1],
+    persistence 0.95 Exp(0.01) + 0.05 U[0, 0.5]) at eps = 0.1: about 2n
+    condensed nodes, more than the shared-memory tree holds, so the simplex
+    keeps its tree in global memory; 10k points per diagram is the largest
+    size of this shape the CPU oracle solves within a test's time.  At 5k
+    the result is also checked against the exact FP64 W1 (the (1 +- eps) band
+    of the approximation bound)."""
+    A, B = synth.mixture_f32(n, 1000), synth.mixture_f32(n, 1001)
+    g, r = _check_w1(pd, ctx, A, B, "f32", 0.1)
+    assert g["n_nodes"] > 9216
+    if n == 5000:
+        w = oracle.w1_exact(A.astype(np.float64), B.astype(np.float64))
+        q = 2.0 ** -20
+        slack = g["slack_quanta"] * q + (r["FA"] + r["FB"]) * q
+        assert 0.9 * w - slack <= g["w1"] <= 1.1 * w + slack
+
+
+def test_w1_approx_coordinates_beyond_float32_exactness(pd, ctx):
+    """Diagrams translated along (t, t) to coordinates of 2^26-2^27 quanta,
+    where float32 no longer holds them exactly: the integer path must still
+    be bit-exact with the oracle."""
+    A, B = synth.uniform_exp(1500, 81) + 100.0, synth.uniform_exp(1400, 82) + 100.0
+    assert (A * 2.0 ** 20).min() >= 2 ** 23
+    _check_w1(pd, ctx, A.astype(np.float32), B.astype(np.float32), "f32", 0.1)
 
 
 def test_w1_certificate_on_coarse_decompositions(pd, ctx):

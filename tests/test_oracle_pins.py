@@ -277,6 +277,107 @@ def test_radix_tree_structure(orc, clustered):
     assert sorted(internal_seen) == list(range(1, N - 1)) and max(internal_seen.values()) == 1
 
 
+def _tree_ranges(t, N):
+    """Leaf-position range [lo, hi] of every internal node (root 0 covers all;
+    the left child of a node ends at its split, which is the left child's
+    number, or its position when it is a leaf)."""
+    lo = np.zeros(max(N - 1, 1), np.int64)
+    hi = np.zeros(max(N - 1, 1), np.int64)
+    stack = [(0, 0, N - 1)]
+    while stack:
+        w, a, b = stack.pop()
+        lo[w], hi[w] = a, b
+        L, R = int(t["left"][w]), int(t["right"][w])
+        sp = L if L >= 0 else ~L
+        if L >= 0:
+            stack.append((L, a, sp))
+        if R >= 0:
+            stack.append((R, sp + 1, b))
+    return lo, hi
+
+
+@pytest.mark.parametrize("clustered", [False, True])
+def test_split_tree_structure(orc, clustered):
+    """The paper's split tree: every internal node's members are cut at the
+    middle of the longest side of their tight bounding box (x on ties), the
+    lower half going left; leaves are a permutation; internal numbers are a
+    bijection onto 0..N-2; boxes are tight and reps are the leftmost members."""
+    rng = np.random.default_rng(70 + clustered)
+    if clustered:
+        ctr = rng.integers(0, 10**6, (8, 2))
+        pts = np.concatenate([c + rng.integers(0, 50, (60, 2)) for c in ctr])
+    else:
+        pts = rng.integers(0, 5000, (500, 2))
+    nodes = _nodes_from_points(orc, pts[:, 0], pts[:, 1])
+    N = len(nodes["X"])
+    perm, t = orc.split_tree(nodes)
+    assert sorted(perm.tolist()) == list(range(N))
+    X, Y = nodes["X"][perm].astype(np.int64), nodes["Y"][perm].astype(np.int64)
+    lo, hi = _tree_ranges(t, N)
+    seen = Counter()
+    for w in range(N - 1):
+        a, b = int(lo[w]), int(hi[w])
+        L, R = int(t["left"][w]), int(t["right"][w])
+        sp = L if L >= 0 else ~L
+        assert a <= sp < b
+        for ch in (L, R):
+            if ch >= 0:
+                seen[ch] += 1
+        mnx, mxx, mny, mxy = X[a:b + 1].min(), X[a:b + 1].max(), Y[a:b + 1].min(), Y[a:b + 1].max()
+        assert list(t["bb"][w]) == [mnx, mxx, mny, mxy]
+        by_x = mxx - mnx >= mxy - mny
+        C = X if by_x else Y
+        mid2 = (mnx + mxx) if by_x else (mny + mxy)
+        assert all(2 * C[i] < mid2 for i in range(a, sp + 1))
+        assert all(2 * C[i] >= mid2 for i in range(sp + 1, b + 1))
+        r = min(range(a, b + 1), key=lambda i: (int(X[i]), int(Y[i])))
+        assert int(t["rep"][w]) == r
+    assert sorted(seen) == list(range(1, N - 1)) and max(seen.values()) == 1
+
+
+@pytest.mark.parametrize("s,clustered", [(2, False), (5, True), (13, False), (40, True)])
+def test_split_tree_wspd_is_a_well_separated_pair_decomposition(orc, s, clustered):
+    rng = np.random.default_rng(91 + s)
+    if clustered:
+        ctr = rng.integers(0, 20000, (6, 2))
+        pts = np.concatenate([c + rng.integers(0, 300, (40, 2)) for c in ctr])
+    else:
+        pts = rng.integers(0, 3000, (220, 2))
+    nodes = _nodes_from_points(orc, pts[:, 0], pts[:, 1])
+    perm, t = orc.split_tree(nodes)
+    nodes = orc.reorder(nodes, perm)
+    X, Y = nodes["X"], nodes["Y"]
+    N = len(X)
+    lo, hi = _tree_ranges(t, N)
+    t = dict(t, lo=lo, hi=hi)
+    pu, pv = orc.wspd_pairs(nodes, t, s)
+    cover = Counter()
+    for u, v in zip(pu.tolist(), pv.tolist()):
+        U, V = _members(t, u), _members(t, v)
+        assert _ws_exact(X, Y, U, V, s)
+        for p in U:
+            for q in V:
+                cover[(min(p, q), max(p, q))] += 1
+    assert len(cover) == N * (N - 1) // 2 and set(cover.values()) == {1}
+
+
+@pytest.mark.parametrize("s", [8, 13, 20])
+def test_split_tree_spanner_stretch(orc, s):
+    rng = np.random.default_rng(120 + s)
+    pts = rng.integers(0, 10**5, (600, 2))
+    nodes = _nodes_from_points(orc, pts[:, 0], pts[:, 1])
+    perm, t = orc.split_tree(nodes)
+    nodes = orc.reorder(nodes, perm)
+    X, Y = nodes["X"].astype(float), nodes["Y"].astype(float)
+    N = len(X)
+    tails, heads = orc.wspd(nodes, t, s)
+    w = np.hypot(X[tails] - X[heads], Y[tails] - Y[heads])
+    D = shortest_path(csr_matrix((w, (tails, heads)), shape=(N, N)), method="D")
+    E = np.hypot(X[:, None] - X[None, :], Y[:, None] - Y[None, :])
+    iu = np.triu_indices(N, 1)
+    assert (D[iu] / E[iu]).max() <= 1 + 4 / s + 4 / (s - 2) + 1e-9
+
+
 # --------------------------------------------------------------------------
 # s-WSPD: definition checked by brute force
 # --------------------------------------------------------------------------
@@ -502,10 +603,11 @@ def _small_pair(n, seed):
     return synth.uniform_exp(n, seed), synth.uniform_exp(n, seed + 1)
 
 
-@pytest.mark.parametrize("eps,seed", [(0.1, 100), (0.5, 102), (1.0, 104)])
-def test_pipeline_bound_chain(orc, eps, seed):
+@pytest.mark.parametrize("eps,seed,tree", [(0.1, 100, "radix"), (0.5, 102, "radix"), (1.0, 104, "radix"),
+                                           (0.1, 106, "split"), (0.5, 108, "split")])
+def test_pipeline_bound_chain(orc, eps, seed, tree):
     A, B = _small_pair(400, seed)
-    r = orc.w1_approx(A, B, "f32", eps=eps, k=16)
+    r = orc.w1_approx(A, B, "f32", eps=eps, k=16, tree=tree)
     # RWMD_0 <= OPT(G_0)
     opt0 = orc.dense_opt_int(r["Ahat"], r["Bhat"])
     assert r["rwmd"] <= opt0
@@ -658,3 +760,29 @@ def test_nearest_neighbour_bound_is_below_the_optimum(orc, seed, eps, kind):
     moved = (r["FA"] + r["FB"]) * math.sqrt(2.0) * (G / 2 + P) if G > 1 else 0.0
     Llo = max(r["LA"] - r["FA"], r["LB"] - r["FB"], 0)
     assert moved <= ec * Llo * (1 + 1e-9) + 1e-9
+
+
+def test_wcd_bound_definition_closed_form_and_below_w1(orc):
+    """WCD of A + B~ against B + A~ (Appendix, WCD): equals the closed form
+    |sum_A (d - b) - sum_B (d - b)| / sqrt(2) (every point minus its own
+    projection is ((b - d)/2, (d - b)/2)), and half of it never exceeds the
+    exact W1 (Hungarian reference) -- including one-sided and empty pairs."""
+    rng = np.random.default_rng(900)
+    for trial in range(12):
+        nA, nB = int(rng.integers(0, 25)), int(rng.integers(0, 25))
+        A = rng.random((nA, 2)) * 3.0
+        B = rng.random((nB, 2)) * 3.0
+        A[:, 1] = A[:, 0] + np.abs(A[:, 1] - A[:, 0])
+        B[:, 1] = B[:, 0] + np.abs(B[:, 1] - B[:, 0])
+        w = orc.wcd(A, B)
+        closed = abs((A[:, 1] - A[:, 0]).sum() - (B[:, 1] - B[:, 0]).sum()) / math.sqrt(2.0)
+        assert abs(w - closed) <= 1e-9 * max(1.0, closed)
+        if nA + nB:
+            w1 = _augmented(A, B, lambda a, b: math.hypot(a[0] - b[0], a[1] - b[1]),
+                            lambda a: abs(a[1] - a[0]) / SQ2)
+            assert w / 2 <= w1 + 1e-9
+    assert orc.wcd(np.zeros((0, 2)), np.zeros((0, 2))) == 0.0
+    # condensed nodes (X, Y, count) give the same value as the expanded points
+    X, Y, c = np.array([1, 4]), np.array([5, 9]), np.array([3, 2])
+    pts = np.array([[1, 5]] * 3 + [[4, 9]] * 2, float)
+    assert orc.wcd((X, Y, c), (X[:1], Y[:1] + 1, c[:1])) == pytest.approx(orc.wcd(pts, np.array([[1, 6]] * 3, float)))
