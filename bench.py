@@ -46,12 +46,19 @@ def parse():
     ap.add_argument("--plain-pairs", type=int, default=3, help="pairs timed through the one-pair path")
     ap.add_argument("--threads", type=int, default=0, help="host threads preprocessing pairs (0 = library default)")
     ap.add_argument("--warm-pairs", type=int, default=2, help="pairs timed with the learned warm start (0 = skip)")
+    ap.add_argument("--train-pairs", type=int, default=16, help="seeded pairs the warm-start network is trained on")
+    ap.add_argument("--train-epochs", type=int, default=30)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="skip the other configurations' sub-lines")
     ap.add_argument("--nn-db", type=int, default=512, help="database diagrams of the nearest-neighbour sub-line")
     ap.add_argument("--mixture-n", type=int, default=10000, help="points per diagram of the continuous-mixture solve")
     ap.add_argument("--no-tune", action="store_true", help="keep the default pricing block (no autotuner)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="only the Gaussian empirical-complexity sweep (its own JSON line; minutes)")
+    ap.add_argument("--stages-only", type=int, default=0, metavar="N",
+                    help="only the sparsification stages of one N + N point continuous-mixture pair, twice "
+                         "(prints their rooflines; the command of the stage kernels' ncu captures)")
     return ap.parse_args()
 
 
@@ -246,6 +253,33 @@ def _timed(stream, fn):
     return a.elapsed_time(b), out
 
 
+def stage_rooflines(r, points):
+    """Algorithmic bytes / device time of the sparsification stages of one
+    pd_w1_sparsify_count call (stage times by CUDA events inside the library),
+    against the measured HBM copy bandwidth.  Bytes per unit, from what each
+    stage must read and write at least (the kernels' own layouts):
+      quantise + 0-condense: 8 B read per float32 point, 16 B written per node
+        (int32 X, Y, int64 count) -- the radix-sort passes in between are
+        overhead, not algorithmic;
+      RWMD: 16 B read per 0-condensed node (it scans the other side's buckets);
+      delta-condense: 16 B read and 32 B written per node (X, Y, cntA, cntB)
+        + 8 B Morton code;
+      tree: 8 B Morton code read + 28 B per internal node written;
+      WSPD (counted): 16 B per tree node read (box, rep, children), 4 B per
+        directed arc of the count (the arcs a stored network would hold)."""
+    pk, _ = peaks()
+    N = r["n_nodes"]
+    units = {"condense0": 8 * points + 16 * N, "rwmd": 16 * N, "delta_condense": 56 * N,
+             "tree": 36 * N, "wspd": 16 * N + 4 * r["n_arcs"]}
+    out = {}
+    for q, k in enumerate(["condense0", "rwmd", "delta_condense", "tree", "wspd"]):
+        ms = r["stage_ms"][q]
+        gbs = units[k] / (ms / 1000.0) / 1e9 if ms > 0 else None
+        out[k] = {"ms": ms, "algorithmic_bytes": units[k], "achieved_gbs": gbs,
+                  "frac": gbs / pk["hbm_gbs"] if gbs else None}
+    return out
+
+
 def other_configs(args, ctx, pdw1, dev, stream, flush):
     """The workload's other configurations, each through the public entry
     points with device-resident inputs, L2 flushed before every timed call:
@@ -287,15 +321,21 @@ def other_configs(args, ctx, pdw1, dev, stream, flush):
                      pdw1.opts(time_limit_ms=300000))
     r = rows[0]
     counts = {}
+    stage_roof = None
     for nc in (100000, 250000, 1000000):
         dA = torch.from_numpy(synth.mixture_f32(nc, 1000)).to(dev)
         dB = torch.from_numpy(synth.mixture_f32(nc, 1001)).to(dev)
         try:
+            pdw1.pd_w1_sparsify_count(ctx, dA, dB, 0.1)  # buffers grown, first-touch costs paid
+            flush.zero_()
             c3 = pdw1.pd_w1_sparsify_count(ctx, dA, dB, 0.1)
             counts[str(nc)] = {"nodes": c3["n_nodes"], "arcs": c3["n_arcs"],
                                "arcs_per_node": c3["n_arcs"] / max(1, c3["n_nodes"]), "ms": c3["stage_ms"][7]}
+            if nc == 1000000:
+                stage_roof = stage_rooflines(c3, 2 * nc)
         except pdw1.PDError as e:
             counts[str(nc)] = {"error": str(e)}
+    out["stage_rooflines_mixture_1M"] = stage_roof
     out["mixture_eps0.1"] = {"value": 1000.0 / ms[0], "unit": UNIT, "n_points": n3, "ms_per_pair": ms[0],
                              "nodes": r["n_nodes"], "arcs": r["n_arcs"], "solve_method": r["solve_method"],
                              "pivots": r["pivots"], "sparse_network_sizes": counts,
@@ -332,8 +372,8 @@ def gaussian_sweep(ctx, pdw1, dev, stream, flush, sizes=(10000, 20000, 40000), s
             dA = torch.from_numpy(synth.gaussian_pd(n // 2, 500 + n)).to(dev)
             dB = torch.from_numpy(synth.gaussian_pd(n // 2, 501 + n)).to(dev)
             flush.zero_()
-            t, r = _timed(stream, lambda: pdw1.pd_w1_approx(ctx, dA, dB, 0.0, pdw1.opts(s_override=s_,
-                                                                                        time_limit_ms=300000)))
+            t, r = _timed(stream, lambda: pdw1.pd_w1_approx(ctx, dA, dB, 0.0, pdw1.opts(
+                s_override=s_, ns_transport=2, time_limit_ms=300000)))
             rows.append({"s": s_, "n": n, "ms": t, "nodes": r["n_nodes"], "arcs": r["n_arcs"],
                          "method": r["solve_method"], "pivots": r["pivots"]})
     fits = {}
@@ -344,7 +384,8 @@ def gaussian_sweep(ctx, pdw1, dev, stream, flush, sizes=(10000, 20000, 40000), s
         den = sum((x - mx) ** 2 for x, _ in pts)
         fits[str(s_)] = sum((x - mx) * (y - my) for x, y in pts) / den if den > 0 else None
     return {"rows": rows, "exponent_of_n": fits,
-            "form": "pd_w1_approx on synthetic Gaussian diagrams (gaussian_pd), s fixed by s_override"}
+            "form": "pd_w1_approx on synthetic Gaussian diagrams (gaussian_pd), s fixed by s_override, the "
+                    "transportation form with its WSPD certificate (ns_transport=2)"}
 
 
 def run_ours(args):
@@ -400,6 +441,15 @@ def run_ours(args):
             raise pdw1.PDError(st, pdw1._lib.pd_last_error(ctx.ptr).decode())
         return [res[q].to_dict() for q in range(P)]
 
+    # pricing block of the simplex: measured on two pool pairs by the library's
+    # autotuner (outside the timed region); every later solve of that size
+    # class uses it
+    tune = None
+    if not args.no_tune:
+        i0, j0 = pairs_all[-1]
+        i1, j1 = pairs_all[-2]
+        tune = pdw1.pd_autotune(ctx, [dev_t[i0], dev_t[i1]], [dev_t[j0], dev_t[j1]], args.eps)
+
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
@@ -442,17 +492,25 @@ def run_ours(args):
             raise pdw1.PDError(st, pdw1._lib.pd_last_error(ctx.ptr).decode())
         plain_ms.append(a.elapsed_time(b))
 
-    # ---- warm start: network trained on cold solves of 4 pool pairs, timed
-    # on pairs it has not seen (one pair per call), beside the cold path ------
+    # ---- warm start (one pair per call, on pool pairs the network has not
+    # seen): cold start; the potentials of a coarse solve of the same pair
+    # (warm_start 4); those corrected by the network (1), trained on cold
+    # solves of other seeded pairs of 20k-100k points; and, as the ceiling,
+    # the exact potentials (2, timed without the cold solve it needs) -------
     warm = None
-    if args.warm_pairs > 0 and len(pairs_all) >= 4 + args.warm_pairs:
-        tr = pairs_all[-4:]
-        st = pdw1.pd_ws_train(ctx, [dev_t[i] for i, _ in tr], [dev_t[j] for _, j in tr], args.eps, epochs=600,
-                              lr=5e-4, seed=1)
+    if args.warm_pairs > 0:
+        import numpy as np
+        from paper_2110_14734_gb300 import synth as _s
+        rng = np.random.default_rng(77)
+        sizes = [int(x) for x in rng.integers(20000, args.n + 1, args.train_pairs)]
+        trA = [torch.from_numpy(_s.lowerstar_u8(k, 40000 + 2 * t)).to(dev) for t, k in enumerate(sizes)]
+        trB = [torch.from_numpy(_s.lowerstar_u8(k, 40001 + 2 * t)).to(dev) for t, k in enumerate(sizes)]
+        st = pdw1.pd_ws_train(ctx, trA, trB, args.eps, epochs=args.train_epochs, lr=1e-3, seed=1)
+        del trA, trB
         rows = []
         for q in range(args.warm_pairs):
             i, j = pairs_all[q]
-            for mode in (0, 1, 2):
+            for mode in (0, 4, 1, 2):
                 flush.zero_()
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
@@ -461,17 +519,26 @@ def run_ours(args):
                 torch.cuda.synchronize()
                 if s2 != 0:
                     raise pdw1.PDError(s2, pdw1._lib.pd_last_error(ctx.ptr).decode())
-                rows.append((mode, a.elapsed_time(b), one.pivots, one.opt_quanta, one.warm_used))
+                ms = a.elapsed_time(b)
+                if mode == 2:  # the exact-potential start needs a cold solve first: time its own solve only
+                    ms = one.ns_kernel_ms
+                rows.append((mode, ms, one.pivots, one.opt_quanta, one.warm_used))
+
         def agg(mode):
             sel = [r for r in rows if r[0] == mode]
             return statistics.mean(r[1] for r in sel), sum(r[2] for r in sel)
-        (cm, cp), (wm, wp), (em, ep) = agg(0), agg(1), agg(2)
-        same = len({(r[3]) for r in rows if r[0] != 0} - {r[3] for r in rows if r[0] == 0}) == 0
+        (cm, cp), (zm, zp), (wm, wp), (em, ep) = agg(0), agg(4), agg(1), agg(2)
+        same = {r[3] for r in rows if r[0] != 0} <= {r[3] for r in rows if r[0] == 0}
         warm = {"value": 1000.0 / wm, "unit": UNIT, "pairs": args.warm_pairs,
-                "form": "pd_w1_approx with warm_start=1 (network trained on 4 other pool pairs), one pair per call",
+                "form": "pd_w1_approx with warm_start=1: the potentials of a coarse solve of the pair corrected by "
+                        "the network, on pool pairs it was not trained on, one pair per call",
                 "cold_value": 1000.0 / cm, "pivots_cold": cp, "pivots_warm": wp,
-                "exact_potentials_value": 1000.0 / em, "pivots_exact_potentials": ep,
-                "same_optimum": same, "train_rows": st["rows"], "train_loss_last": st["loss_last"]}
+                "coarse_value": 1000.0 / zm, "pivots_coarse": zp,
+                "exact_potentials_simplex_value": 1000.0 / em, "pivots_exact_potentials": ep,
+                "same_optimum": same, "train_pairs": st["pairs"], "train_rows": st["rows"],
+                "train_points_per_diagram": [min(sizes), max(sizes)], "train_epochs": args.train_epochs,
+                "train_loss_first": st["loss_first"], "train_loss_last": st["loss_last"],
+                "train_s": (st["collect_ms"] + st["train_ms"]) / 1000.0}
 
     # ---- end to end through the C ABI with pinned host buffers -------------
     e2e_steps = max(1, min(args.e2e_steps, args.steps))
@@ -528,6 +595,10 @@ def run_ours(args):
             "wall_s": t_wall}
     if rank == 0:
         line["clocks"] = clk.summary()
+    line["config"]["autotune"] = tune
+    if rank == 0 and ws == 1 and not args.no_configs:
+        line["configs"] = other_configs(args, ctx, pdw1, dev, stream, flush)
+    if rank == 0:
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.n, args.eps)
         print(json.dumps(line), flush=True)
@@ -536,10 +607,46 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_stages(args):
+    import torch
+    from paper_2110_14734_gb300 import build, synth
+    build.build()
+    from paper_2110_14734_gb300 import pdw1
+    dev = torch.device("cuda", 0)
+    ctx = pdw1.pd_create(0)
+    n = args.stages_only
+    dA = torch.from_numpy(synth.mixture_f32(n, 1000)).to(dev)
+    dB = torch.from_numpy(synth.mixture_f32(n, 1001)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    pdw1.pd_w1_sparsify_count(ctx, dA, dB, 0.1)
+    flush.zero_()
+    r = pdw1.pd_w1_sparsify_count(ctx, dA, dB, 0.1)
+    print(json.dumps({"n_points": n, "nodes": r["n_nodes"], "arcs": r["n_arcs"],
+                      "stage_rooflines": stage_rooflines(r, 2 * n)}), flush=True)
+    ctx.close()
+
+
+def run_sweep(args):
+    import torch
+    from paper_2110_14734_gb300 import build
+    build.build()
+    from paper_2110_14734_gb300 import pdw1
+    dev = torch.device("cuda", 0)
+    ctx = pdw1.pd_create(0)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    out = gaussian_sweep(ctx, pdw1, dev, torch.cuda.current_stream(dev), flush)
+    print(json.dumps({"gaussian_sweep": out}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.stages_only > 0:
+        run_stages(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args)
 

@@ -86,7 +86,9 @@ typedef struct {
     int32_t seq_threshold;  /* cost scaling: at most this many active nodes, one block finishes them (-1 = 64) */
     int32_t solver;         /* 0 = network simplex (default), 1 = cost scaling with push/relabel */
     int64_t ns_block;       /* network simplex pricing block in arcs (0 = max(8192, sqrt(arcs))) */
-    int32_t ns_transport;   /* W1 only: 1 = try the transportation form with its certificate first (default) */
+    int32_t ns_transport;   /* W1 only: 1 = try the transportation form with its certificate first when it
+                               has at most twice the sparse network's arcs (default); 2 = whenever its
+                               arcs fit the simplex (< 2^31); 0 = solve the sparse network itself */
     int32_t ns_smem;        /* network simplex: 1 = hot node arrays in shared memory when they fit (default) */
     int32_t batch_slots;    /* pairs per simplex launch of pd_w1_approx_batch and pd_nn_search
                                (0 = twice the number of SMs) */
@@ -94,19 +96,28 @@ typedef struct {
     int32_t nn_prune;       /* pd_nn_search: 1 = skip pairs whose lower bound exceeds the best optimum
                                (default); 0 = solve every pair */
     int32_t warm_start;     /* network simplex on the transportation form: 0 = cold start (default);
-                               1 = start from the potentials predicted by the context's network
-                               (pd_ws_train / pd_ws_load); 2 = start from the exact potentials of a
+                               1 = start from the coarse solve's potentials (as 4) corrected by the
+                               context's network (pd_ws_train / pd_ws_load); 2 = start from the exact
+                               potentials of a
                                cold solve of the same pair (diagnostic: the best a prediction can do);
                                3 = start from the potentials +d(u) for sources, -d(v) for sinks (d: the
                                distance to the diagonal), i.e. the greedy by the saving
-                               d(u) + d(v) - c(u, v) of pairing u with v (no network) */
-    int32_t ns_candidates;  /* network simplex: 1 = after a pivot, the other warps' best arcs of the last
-                               priced block are priced again and the most negative still-negative one
-                               enters before a new block is priced (a candidate list); 0 = a block is
-                               priced before every pivot (the paper's block search; default) */
+                               d(u) + d(v) - c(u, v) of pairing u with v (no network);
+                               4 = start from the potentials of an exact solve of the same pair
+                               condensed onto a coarser lattice (cell max(2 G, node box / 64)), each
+                               node taking its nearest coarse node's */
+    int32_t ns_walk;        /* network simplex, trees in shared memory: the two half-cycles of a pivot are
+                               followed up the tree by two lanes when neither side is longer than this
+                               many nodes, else found by a scan of the whole preorder by the CTA
+                               (-1 = the autotuned value, else 0; 0 = always the scan; at most 512) */
     int32_t tree;           /* hierarchical tree of the WSPD: 0 = binary radix tree over the Morton order
                                of the nodes (a compressed quadtree; default), 1 = the paper's split tree
                                (WSPD section: the longest side of a bounding box cut in the middle) */
+    int32_t diag_kappa;     /* unbalanced transport (the Conclusion: ā and b̄ as destructor / creator):
+                               a unit at p is destroyed (arc p -> ā) or created (b̄ -> p) at cost
+                               diag_kappa * d_diag(p) + diag_tau quanta; 1 and 0 (default) give W1
+                               between persistence diagrams, 0 a constant cost diag_tau */
+    int64_t diag_tau;       /* >= 0 quanta, < 2^30 */
 } pd_opts;
 
 void pd_opts_default(pd_opts* opts);
@@ -340,28 +351,31 @@ pd_status pd_db_build(pd_ctx* ctx, const pd_diagram* dbs, int64_t n_db, const pd
 pd_status pd_nn_search(pd_ctx* ctx, pd_diagram query, double eps, const pd_opts* opts, pd_nn_result* out,
                        int64_t* opt_out, int64_t* lb_out, int64_t* wcd_out, void* stream);
 
-/* ---- autotuner of the simplex's pricing block (no counterpart in the paper) --
+/* ---- autotuner of the simplex's launch parameters (no counterpart in the paper)
  *
  * The paper's block search prices blocks of sqrt(arcs) arcs.  pd_autotune
  * measures instead: it prepares the transportation instance of each sample
  * pair (A[i], B[i]) at eps/opts exactly as pd_w1_approx does, solves it once
- * per candidate block (4096 ... 131072 arcs, and the default), each launch
- * timed by CUDA events, and keeps the fastest block of each size class
+ * per candidate (pricing block of 4096 ... 32768 arcs) x (walk limit 0, 8,
+ * 32, see pd_opts.ns_walk), and once with the defaults, each launch timed by
+ * CUDA events, and keeps the fastest pair of values of each size class
  * floor(log2(arcs + nodes)) in the context: later solves of that class whose
- * opts->ns_block is 0 use it (pd_w1_approx, pd_w1_approx_batch,
- * pd_nn_search, pd_mcf_solve).  Every candidate reaches the same optimum
- * (checked).  cache_path (may be NULL): a text file of lines "gpu-name sms
- * class block"; classes it already holds for this GPU are loaded instead of
- * timed, and newly timed classes are written back (other GPUs' lines kept).
- * Must not run concurrently with other calls on the same context. */
+ * opts->ns_block is 0 (and ns_walk -1) use them (pd_w1_approx,
+ * pd_w1_approx_batch, pd_nn_search, pd_mcf_solve).  Every candidate reaches
+ * the same optimum (checked).  cache_path (may be NULL): a text file of lines
+ * "gpu-name sms class block walk"; classes it already holds for this GPU are
+ * loaded instead of timed, and newly timed classes are written back (other
+ * GPUs' lines kept).  Must not run concurrently with other calls on the same
+ * context. */
 typedef struct {
     int64_t ns_block;   /* block chosen for the first sample pair's size class (0 if none) */
+    int32_t ns_walk;    /* walk limit chosen for that class (pd_opts.ns_walk) */
     int32_t size_class; /* that class, floor(log2(arcs + nodes)); -1 if no pair had a transportation form */
     int32_t candidates; /* candidate blocks */
     int32_t pairs;      /* pairs timed (not taken from the cache) */
     int32_t from_cache; /* 1: the first pair's class came from cache_path */
     float best_ms;      /* simplex device time of the timed pairs of that class with the chosen block */
-    float default_ms;   /* ... with the default block max(8192, sqrt(arcs + nodes)) */
+    float default_ms;   /* ... with the default block max(8192, sqrt(arcs + nodes)) and walk 0 */
 } pd_tune_result;
 
 pd_status pd_autotune(pd_ctx* ctx, const pd_diagram* A, const pd_diagram* B, int64_t count, double eps,
@@ -372,19 +386,22 @@ pd_status pd_tuned_block(const pd_ctx* ctx, int64_t arcs_and_nodes, int64_t* blo
 /* ---- learned warm start (no counterpart in the paper) ----------------------
  *
  * A network of 68 -> 128 -> 128 -> 1 units (ReLU) predicts, per node of the
- * transportation form, its optimal potential (up to a common offset);
- * the simplex then starts from a greedy flow on the arcs of smallest
- * predicted reduced cost instead of the all-artificial tree (pd_opts
- * warm_start = 1).  Weights are stored in bf16, products accumulate in
+ * transportation form, the correction from the potentials of a coarse solve
+ * of the same pair (pd_opts warm_start = 4) to its optimal potential (up to a
+ * common offset); the simplex then starts from a greedy flow on the arcs of
+ * smallest predicted reduced cost, each tree of that forest hung from the
+ * root at its predicted potential, instead of the all-artificial tree
+ * (pd_opts warm_start = 1).  Weights are stored in bf16, products accumulate in
  * float32; the float32 master parameters (PD_WS_NPARAMS floats) are laid out
  * as W1[68][128], b1[128], W2[128][128], b2[128], w3[128], b3 (W[k][j] is the
  * weight from input k to unit j).  Features of a node (68): its coordinates
  * relative to the pair's node box and divided by the box's larger side,
  * log(1 + cntA), log(1 + cntB), and an 8 x 8 window (offsets -4..3) of a
  * 64 x 64 grid over the box holding sign(s) log(1 + |s|) of the summed supply
- * s = cntA - cntB of the nodes in each cell.  Target: (potential of the node
+ * s = cntA - cntB of the nodes in each cell.  Target: ((potential of the node
  * in the optimal tree - the mean potential of the tree's largest component
- * below the root) / the box's side, for the nodes of that component.
+ * below the root) - (the same for the coarse solve's potentials)) / the box's
+ * side, for the nodes of that component.
  */
 #define PD_WS_NFEAT 68
 #define PD_WS_NPARAMS 25473

@@ -49,7 +49,7 @@ def lib():
         L.orc_condense0.restype = C.c_int64
         L.orc_condense0.argtypes = [I32P, I32P, C.c_int64, I32P, I32P, I64P]
         L.orc_rwmd.restype = None
-        L.orc_rwmd.argtypes = [I32P, I32P, I64P, C.c_int64, I32P, I32P, I64P, C.c_int64, I64P]
+        L.orc_rwmd.argtypes = [I32P, I32P, I64P, C.c_int64, I32P, I32P, I64P, C.c_int64, C.c_int64, C.c_int64, I64P]
         L.orc_bound.restype = C.c_double
         L.orc_bound.argtypes = [C.c_int64]
         L.orc_s_from_eps.restype = C.c_int64
@@ -84,7 +84,7 @@ def lib():
                                I32P, I32P, C.c_int64]
         L.orc_build_network.restype = C.c_int64
         L.orc_build_network.argtypes = [C.c_int64, I32P, I32P, I64P, I64P, C.c_int64, I32P, I32P,
-                                        I64P, I32P, I64P, I64P]
+                                        I64P, I32P, I64P, I64P, C.c_int64, C.c_int64]
         L.orc_mcf_csr.restype = C.c_int
         L.orc_mcf_csr.argtypes = [C.c_int64, I64P, I32P, I64P, I64P, I64P, I64P,
                                   C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int64]
@@ -97,9 +97,11 @@ def lib():
                                        C.c_double]
         L.orc_dense_opt_int.restype = C.c_int
         L.orc_dense_opt_int.argtypes = [I32P, I32P, I64P, C.c_int64, I32P, I32P, I64P, C.c_int64,
-                                        C.POINTER(C.c_int64), C.c_int64]
+                                        C.c_int64, C.c_int64, C.POINTER(C.c_int64), C.c_int64]
         L.orc_w1_exact.restype = C.c_double
-        L.orc_w1_exact.argtypes = [F64P, C.c_int64, F64P, C.c_int64, C.c_int64]
+        L.orc_w1_exact.argtypes = [F64P, C.c_int64, F64P, C.c_int64, C.c_double, C.c_double, C.c_int64]
+        L.orc_cmake.restype = C.c_int64
+        L.orc_cmake.argtypes = [C.c_int64] * 4
         _lib = L
     return _lib
 
@@ -118,6 +120,13 @@ def ceil_sqrt(v: int) -> int:
 
 def cost(x1, y1, x2, y2) -> int:
     return int(lib().orc_cost(x1, y1, x2, y2))
+
+
+def cmake(x, y, kappa=1, tau=0) -> int:
+    """Creation / destruction cost of a unit at (x, y): kappa * cdiag + tau
+    (1, 0: the distance to the diagonal of persistence diagrams; the
+    Conclusion's unbalanced transport otherwise)."""
+    return int(lib().orc_cmake(x, y, kappa, tau))
 
 
 def cdiag(x, y) -> int:
@@ -200,11 +209,13 @@ def _nz(a, dt):
     return a if a.size else np.zeros(1, dt)
 
 
-def rwmd(Ahat, Bhat):
-    """Ahat, Bhat = (X, Y, cnt).  Returns (L_A, L_B, max)."""
+def rwmd(Ahat, Bhat, kappa=1, tau=0):
+    """Ahat, Bhat = (X, Y, cnt).  Returns (L_A, L_B, max).  kappa, tau: the
+    creation / destruction cost kappa * d_diag + tau (see cmake)."""
     L = np.zeros(3, np.int64)
     lib().orc_rwmd(_nz(Ahat[0], np.int32), _nz(Ahat[1], np.int32), _nz(Ahat[2], np.int64), len(Ahat[0]),
-                   _nz(Bhat[0], np.int32), _nz(Bhat[1], np.int32), _nz(Bhat[2], np.int64), len(Bhat[0]), L)
+                   _nz(Bhat[0], np.int32), _nz(Bhat[1], np.int32), _nz(Bhat[2], np.int64), len(Bhat[0]),
+                   int(kappa), int(tau), L)
     return int(L[0]), int(L[1]), int(L[2])
 
 
@@ -295,7 +306,7 @@ def mix64(z: int) -> int:
     return int(lib().orc_mix64(z))
 
 
-def build_network(nodes, tails, heads):
+def build_network(nodes, tails, heads, kappa=1, tau=0):
     N = len(nodes["X"])
     nws = len(tails)
     na = int(np.count_nonzero(nodes["cntA"] > 0))
@@ -307,7 +318,8 @@ def build_network(nodes, tails, heads):
     sup = np.zeros(N + 2, np.int64)
     m2 = lib().orc_build_network(N, _nz(nodes["X"], np.int32), _nz(nodes["Y"], np.int32),
                                  _nz(nodes["cntA"], np.int64), _nz(nodes["cntB"], np.int64), nws,
-                                 _nz(tails, np.int32), _nz(heads, np.int32), row_ptr, head, cst, sup)
+                                 _nz(tails, np.int32), _nz(heads, np.int32), row_ptr, head, cst, sup,
+                                 int(kappa), int(tau))
     assert m2 == m
     return dict(n_nodes=N, row_ptr=row_ptr, head=head, cost=cst, supply=sup)
 
@@ -351,35 +363,39 @@ def mcf_arcs_dbl(n, tails, heads, costs, supply, tol=1e-12, max_pivots=0):
     return st, opt.value, flow[:m], pot[:n]
 
 
-def dense_opt_int(P, Q, max_pivots=0):
+def dense_opt_int(P, Q, max_pivots=0, kappa=1, tau=0):
     """Integer optimum of the dense bipartite G(A,B) between weighted node sets
     P = (X, Y, cnt) (A side) and Q (B side), rounded-up costs."""
     opt = C.c_int64()
     st = lib().orc_dense_opt_int(_nz(P[0], np.int32), _nz(P[1], np.int32), _nz(P[2], np.int64), len(P[0]),
                                  _nz(Q[0], np.int32), _nz(Q[1], np.int32), _nz(Q[2], np.int64), len(Q[0]),
-                                 C.byref(opt), max_pivots)
+                                 int(kappa), int(tau), C.byref(opt), max_pivots)
     if st != 0:
         raise RuntimeError("network simplex status %d" % st)
     return opt.value
 
 
-def w1_exact(A, B, max_pivots=0) -> float:
-    """Exact FP64 W1 (l2 ground metric) on unquantised (n, 2) diagrams."""
+def w1_exact(A, B, max_pivots=0, kappa=1.0, tau=0.0) -> float:
+    """Exact FP64 W1 (l2 ground metric) on unquantised (n, 2) diagrams;
+    kappa, tau (in the diagrams' units): creation / destruction costs."""
     a = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(-1, 2))
     b = np.ascontiguousarray(np.asarray(B, dtype=np.float64).reshape(-1, 2))
     v = lib().orc_w1_exact(_nz(a.reshape(-1), np.float64), a.shape[0], _nz(b.reshape(-1), np.float64),
-                           b.shape[0], max_pivots)
+                           b.shape[0], float(kappa), float(tau), max_pivots)
     if v < 0:
         raise RuntimeError("exact W1 solve failed")
     return float(v)
 
 
 def w1_approx(A, B, dtype, eps=0.1, k=None, s_override=0, perturb=True, seed=0,
-              condense=True, solve=True, tree="radix"):
+              condense=True, solve=True, tree="radix", kappa=1, tau=0):
     """Algorithm 4 end to end.  Returns a dict of every intermediate result.
 
     A, B: (n, 2) arrays of (birth, death), float32 (dtype "f32") or uint8 ("u8").
     W1 ~= OPT_int * 2^-k.  condense=False keeps G = 1, P = 0 (no snapping).
+    tree: "radix" (Morton radix tree) or "split" (the paper's split tree).
+    kappa, tau: creation / destruction cost kappa * d_diag + tau quanta of the
+    diagonal arcs (1, 0 for persistence diagrams).
     """
     if k is None:
         k = default_shift(dtype)
@@ -389,7 +405,7 @@ def w1_approx(A, B, dtype, eps=0.1, k=None, s_override=0, perturb=True, seed=0,
     Bhat = condense0(XB, YB)
     FA = int(Ahat[2].sum())
     FB = int(Bhat[2].sum())
-    LA, LB, L = rwmd(Ahat, Bhat)
+    LA, LB, L = rwmd(Ahat, Bhat, kappa, tau)
     s = int(s_override) if s_override else s_from_eps(eps)
     if condense:
         delta, G, P = delta_params(LA, LB, FA, FB, s)
@@ -404,7 +420,7 @@ def w1_approx(A, B, dtype, eps=0.1, k=None, s_override=0, perturb=True, seed=0,
     else:
         tr = radix_tree(nodes)
     tails, heads = wspd(nodes, tr, s)
-    net = build_network(nodes, tails, heads)
+    net = build_network(nodes, tails, heads, kappa, tau)
     out = dict(k=k, Ahat=Ahat, Bhat=Bhat, FA=FA, FB=FB, LA=LA, LB=LB, rwmd=L, s=s, delta=delta, G=G,
                P=P, nodes=nodes, tree=tr, ws_tails=tails, ws_heads=heads, net=net)
     if solve:

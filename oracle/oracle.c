@@ -79,6 +79,15 @@ int64_t orc_cdiag(int64_t x, int64_t y) {
     return (int64_t)orc_ceil_sqrt((t2 + 1) / 2);
 }
 
+/* Cost of destroying a unit at (x, y) (arc u -> ā) or creating one there
+ * (b̄ -> v): the distance to the diagonal for persistence diagrams (kappa 1,
+ * tau 0).  The Conclusion's unbalanced optimal transport on R^2 reassigns
+ * these arcs' costs to creation / destruction costs; here kappa * d_diag + tau
+ * with kappa in {0, 1} and tau >= 0 quanta (kappa 0: a constant cost). */
+int64_t orc_cmake(int64_t x, int64_t y, int64_t kappa, int64_t tau) {
+    return (kappa ? orc_cdiag(x, y) : 0) + tau;
+}
+
 static int64_t floordiv(int64_t a, int64_t b) { /* b > 0 */
     int64_t q = a / b;
     if ((a % b) != 0 && a < 0) q--;
@@ -162,12 +171,13 @@ int64_t orc_condense0(const int32_t* X, const int32_t* Y, int64_t n,
 
 /* One side of Algorithm 1: every unit at node u of P is sent to the cheapest
  * node of Q or, as the relaxed min-cost flow also allows, to the diagonal
- * node (cost d_diag(u)).  min_v ceil(sqrt(d2)) = ceil(sqrt(min_v d2)).      */
+ * node (cost d_diag(u), or the destruction cost of orc_cmake).
+ * min_v ceil(sqrt(d2)) = ceil(sqrt(min_v d2)).                              */
 static int64_t rwmd_side(const int32_t* PX, const int32_t* PY, const int64_t* Pc, int64_t nP,
-                         const int32_t* QX, const int32_t* QY, int64_t nQ) {
+                         const int32_t* QX, const int32_t* QY, int64_t nQ, int64_t kappa, int64_t tau) {
     int64_t L = 0;
     for (int64_t u = 0; u < nP; u++) {
-        int64_t best = orc_cdiag(PX[u], PY[u]);
+        int64_t best = orc_cmake(PX[u], PY[u], kappa, tau);
         if (nQ > 0) {
             uint64_t bd2 = UINT64_MAX;
             for (int64_t v = 0; v < nQ; v++) {
@@ -185,9 +195,10 @@ static int64_t rwmd_side(const int32_t* PX, const int32_t* PY, const int64_t* Pc
 
 /* L[0] = L_A, L[1] = L_B, L[2] = max(L_A, L_B), all in quanta. */
 void orc_rwmd(const int32_t* AX, const int32_t* AY, const int64_t* Ac, int64_t nA,
-              const int32_t* BX, const int32_t* BY, const int64_t* Bc, int64_t nB, int64_t* L) {
-    L[0] = rwmd_side(AX, AY, Ac, nA, BX, BY, nB);
-    L[1] = rwmd_side(BX, BY, Bc, nB, AX, AY, nA);
+              const int32_t* BX, const int32_t* BY, const int64_t* Bc, int64_t nB, int64_t kappa, int64_t tau,
+              int64_t* L) {
+    L[0] = rwmd_side(AX, AY, Ac, nA, BX, BY, nB, kappa, tau);
+    L[1] = rwmd_side(BX, BY, Bc, nB, AX, AY, nA, kappa, tau);
     L[2] = L[0] > L[1] ? L[0] : L[1];
 }
 
@@ -674,7 +685,7 @@ int64_t orc_wspd_pairs(int64_t N, const int32_t* X, const int32_t* Y, const int3
  * sigma(ā) = -F_A, sigma(b̄) = F_B.  Returns the number of arcs m. */
 int64_t orc_build_network(int64_t N, const int32_t* X, const int32_t* Y, const int64_t* cntA,
                           const int64_t* cntB, int64_t nws, const int32_t* wt, const int32_t* wh,
-                          int64_t* row_ptr, int32_t* head, int64_t* cost, int64_t* supply) {
+                          int64_t* row_ptr, int32_t* head, int64_t* cost, int64_t* supply, int64_t kappa, int64_t tau) {
     int64_t na = 0, nb = 0, FA = 0, FB = 0;
     for (int64_t i = 0; i < N; i++) {
         if (cntA[i] > 0) na++;
@@ -700,9 +711,9 @@ int64_t orc_build_network(int64_t N, const int32_t* X, const int32_t* Y, const i
         if (u < N && v < N)
             cost[a] = orc_cost(X[u], Y[u], X[v], Y[v]);
         else if (u < N && v == N)
-            cost[a] = orc_cdiag(X[u], Y[u]);
+            cost[a] = orc_cmake(X[u], Y[u], kappa, tau);
         else if (u == N + 1 && v < N)
-            cost[a] = orc_cdiag(X[v], Y[v]);
+            cost[a] = orc_cmake(X[v], Y[v], kappa, tau);
         else
             cost[a] = 0;
     }
@@ -771,7 +782,7 @@ int orc_mcf_arcs_dbl(int64_t n, int64_t m, const int32_t* tail, const int32_t* h
  * b̄ -> Q, b̄ -> ā.  Coincident nodes of P and Q stay separate (cost 0). */
 int orc_dense_opt_int(const int32_t* PX, const int32_t* PY, const int64_t* Pc, int64_t nP,
                       const int32_t* QX, const int32_t* QY, const int64_t* Qc, int64_t nQ,
-                      int64_t* opt, int64_t max_pivots) {
+                      int64_t kappa, int64_t tau, int64_t* opt, int64_t max_pivots) {
     int64_t n = nP + nQ + 2, abar = nP + nQ, bbar = nP + nQ + 1;
     int64_t m = nP * nQ + nP + nQ + 1;
     int32_t* t = (int32_t*)malloc(sizeof(int32_t) * m);
@@ -791,7 +802,7 @@ int orc_dense_opt_int(const int32_t* PX, const int32_t* PY, const int64_t* Pc, i
     for (int64_t u = 0; u < nP; u++) {
         t[k] = (int32_t)u;
         h[k] = (int32_t)abar;
-        c[k] = orc_cdiag(PX[u], PY[u]);
+        c[k] = orc_cmake(PX[u], PY[u], kappa, tau);
         k++;
         sup[u] = Pc[u];
         FA += Pc[u];
@@ -799,7 +810,7 @@ int orc_dense_opt_int(const int32_t* PX, const int32_t* PY, const int64_t* Pc, i
     for (int64_t v = 0; v < nQ; v++) {
         t[k] = (int32_t)bbar;
         h[k] = (int32_t)(nP + v);
-        c[k] = orc_cdiag(QX[v], QY[v]);
+        c[k] = orc_cmake(QX[v], QY[v], kappa, tau);
         k++;
         sup[nP + v] = -Qc[v];
         FB += Qc[v];
@@ -860,8 +871,11 @@ static int64_t condense_dbl(const double* bd, int64_t n, double* ob, double* od,
 /* Exact W1 (Problem 1) with the l2 ground metric, in FP64, on unquantised
  * diagrams given as interleaved (b, d) doubles: min-cost flow on the dense
  * 0-condensed network G(A,B), which by Proposition (matching iff flow) equals
- * the optimal partial matching.  Returns W1, or -1 on failure. */
-double orc_w1_exact(const double* A, int64_t nA, const double* B, int64_t nB, int64_t max_pivots) {
+ * the optimal partial matching.  Diagonal arcs cost kappa * d_diag + tau (1
+ * and 0 for persistence diagrams; the Conclusion's unbalanced transport
+ * otherwise).  Returns W1, or -1 on failure. */
+double orc_w1_exact(const double* A, int64_t nA, const double* B, int64_t nB, double kappa, double tau,
+                    int64_t max_pivots) {
     double* ab = (double*)malloc(sizeof(double) * (nA + 1));
     double* ad = (double*)malloc(sizeof(double) * (nA + 1));
     int64_t* ac = (int64_t*)malloc(sizeof(int64_t) * (nA + 1));
@@ -891,7 +905,7 @@ double orc_w1_exact(const double* A, int64_t nA, const double* B, int64_t nB, in
     for (int64_t u = 0; u < na; u++) {
         t[k] = (int32_t)u;
         h[k] = (int32_t)abar;
-        c[k] = fabs(ad[u] - ab[u]) / sqrt(2.0);
+        c[k] = kappa * fabs(ad[u] - ab[u]) / sqrt(2.0) + tau;
         if (c[k] > cmax) cmax = c[k];
         k++;
         sup[u] = ac[u];
@@ -900,7 +914,7 @@ double orc_w1_exact(const double* A, int64_t nA, const double* B, int64_t nB, in
     for (int64_t v = 0; v < nb; v++) {
         t[k] = (int32_t)bbar;
         h[k] = (int32_t)(na + v);
-        c[k] = fabs(bdd[v] - bb[v]) / sqrt(2.0);
+        c[k] = kappa * fabs(bdd[v] - bb[v]) / sqrt(2.0) + tau;
         if (c[k] > cmax) cmax = c[k];
         k++;
         sup[na + v] = -bc[v];

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libpdw1.so")
-SOURCES = ["capi.cu", "condense.cu", "wspd.cu", "solver.cu", "netsimplex.cu", "noalloc.cu", "nn.cu", "warm.cu", "mlp.cu", "splittree.cu", "autotune.cu"]
+SOURCES = ["capi.cu", "condense.cu", "wspd.cu", "solver.cu", "netsimplex.cu", "noalloc.cu", "nn.cu", "warm.cu", "mlp.cu", "splittree.cu", "autotune.cu", "coarse.cu"]
 HEADERS = ["common.cuh", "prims.cuh", "internal.h", "netsimplex.cuh", "mlp.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

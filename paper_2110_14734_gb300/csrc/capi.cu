@@ -171,6 +171,9 @@ extern "C" void pd_opts_default(pd_opts* o) {
     o->ns_transport = 1;
     o->ns_smem = 1;
     o->nn_prune = 1;
+    o->ns_walk = -1;
+    o->diag_kappa = 1;
+    o->diag_tau = 0;
 }
 
 namespace pd {
@@ -197,9 +200,23 @@ Ctx* ctx_new(int device, size_t cap) {
     return c;
 }
 
+static void wave_free(Ctx* c) {
+    if (c->wave_exec) cudaGraphExecDestroy(c->wave_exec);
+    if (c->wave_stream) cudaStreamDestroy(c->wave_stream);
+    for (cudaEvent_t& e : c->wave_ev)
+        if (e) cudaEventDestroy(e);
+    if (c->wave_pin) cudaFreeHost(c->wave_pin);
+    c->wave_exec = nullptr;
+    c->wave_stream = nullptr;
+    c->wave_pin = nullptr;
+}
+
 void ctx_free(Ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
+    wave_free(c);
+    ctx_free(c->coarse);
+    c->coarse = nullptr;
     for (Ctx* sl : c->slots) ctx_free(sl);
     c->slots.clear();
     for (Ctx* wk : c->workers) ctx_free(wk);
@@ -236,6 +253,9 @@ extern "C" pd_status pd_create(pd_ctx** out, int device, size_t arena_bytes) {
 extern "C" void pd_destroy(pd_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
+    wave_free(c);
+    ctx_free(c->coarse);
+    c->coarse = nullptr;
     for (Ctx* sl : c->slots) ctx_free(sl);
     c->slots.clear();
     for (Ctx* wk : c->workers) ctx_free(wk);
@@ -249,6 +269,12 @@ extern "C" void pd_destroy(pd_ctx* c) {
 extern "C" const char* pd_last_error(const pd_ctx* c) { return c ? c->err.c_str() : "no context"; }
 
 extern "C" int64_t pd_kernel_launches(void) { return g_launches.load(); }
+
+pd_status pd::check_diag_cost(Ctx* c, const pd_opts& o) {
+    if ((o.diag_kappa != 0 && o.diag_kappa != 1) || o.diag_tau < 0 || o.diag_tau >= (int64_t(1) << 30))
+        return fail(c, PD_EINVAL, "need diag_kappa in {0, 1} and 0 <= diag_tau < 2^30");
+    return PD_OK;
+}
 
 pd_status pd::check_diag(Ctx* c, const pd_diagram& d) {
     if (d.n < 0) return fail(c, PD_EINVAL, "negative diagram size");
@@ -325,7 +351,8 @@ extern "C" pd_status pd_rwmd_lower_bound(pd_ctx* c, pd_diagram A, pd_diagram B, 
     Hats h;
     PD_TRY(stage_condense0(c, a, b, k, &h, st));
     int64_t L[3];
-    PD_TRY(stage_rwmd(c, h, L, st));
+    PD_TRY(check_diag_cost(c, o));
+    PD_TRY(stage_rwmd(c, h, L, diag_cost(o), st));
     out3[0] = L[0];
     out3[1] = L[1];
     out3[2] = L[2];
@@ -442,13 +469,14 @@ pd_status front_half(Ctx* c, const pd_diagram& A, const pd_diagram& B, double ep
             for (int q = 0; q < 4; q++) cudaEventDestroy(e[q]);
         }
     } guard{ev};
+    PD_TRY(check_diag_cost(c, o));
     PD_TRY_CUDA(c, cudaEventRecord(ev[0], st));
     DevDiag a, b;
     PD_TRY(stage_inputs(c, A, B, &a, &b, st));
     f->k = o.coord_shift >= 0 ? o.coord_shift : default_shift(A.dtype);
     PD_TRY(stage_condense0(c, a, b, f->k, &f->h, st));
     PD_TRY_CUDA(c, cudaEventRecord(ev[1], st));
-    PD_TRY(stage_rwmd(c, f->h, f->L, st));
+    PD_TRY(stage_rwmd(c, f->h, f->L, diag_cost(o), st));
     PD_TRY_CUDA(c, cudaEventRecord(ev[2], st));
     f->s = o.s_override > 0 ? o.s_override : s_for_eps(eps);
     if (f->s < 1) return fail(c, PD_EINVAL, "no WSPD parameter s for this eps");
@@ -463,7 +491,7 @@ pd_status front_half(Ctx* c, const pd_diagram& A, const pd_diagram& B, double ep
     if (o.tree == 1) PD_TRY(stage_split_tree(c, &f->nodes, &split, nullptr, st));  // nodes renumbered by leaf order
     c->nodes = f->nodes;
     PD_TRY(stage_network(c, f->nodes, f->s, &f->net, &f->ms[3], &f->ms[4], &f->ms[5], st, count_only, &f->tree,
-                         o.tree == 1 ? &split : nullptr));
+                         o.tree == 1 ? &split : nullptr, diag_cost(o)));
     f->counted = count_only;
     c->net = f->net;
     if (count_only) {
@@ -532,9 +560,13 @@ constexpr int64_t WARM_MAX_RESIDUAL = int64_t(1) << 18;
 static pd_status warm_start(Ctx* c, const Front& f, W1Prep* w, const pd_opts& o, bool* used, cudaStream_t st) {
     *used = false;
     if (!w->ns.ready || o.warm_start == 0) return PD_OK;
-    std::vector<float> p;
-    if (o.warm_start == 1) {
-        PD_TRY(ws_predict(c, f.nodes, *w, &p, st));
+    std::vector<float> pf;
+    std::vector<double> p;
+    if (o.warm_start == 1) {  // the coarse solve's potentials corrected by the network
+        PD_TRY(ws_coarse_potentials(c, f, *w, o, &p, st));
+        PD_TRY(ws_predict(c, f.nodes, *w, &pf, st));
+        if (!p.empty())
+            for (size_t v = 0; v < p.size() && v < pf.size(); v++) p[v] += pf[v];
     } else if (o.warm_start == 2) {
         NSInst* d = bufT<NSInst>(c, B_NS_INST, 1);
         if (!d) return PD_ENOMEM;
@@ -546,12 +578,16 @@ static pd_status warm_start(Ctx* c, const Front& f, W1Prep* w, const pd_opts& o,
         PD_TRY_CUDA(c, cudaMemcpyAsync(pi.data(), r.pi, sizeof(int64_t) * nt, cudaMemcpyDeviceToHost, st));
         PD_TRY_CUDA(c, cudaStreamSynchronize(st));
         p.resize((size_t)nt);
-        for (int64_t v = 0; v < nt; v++) p[(size_t)v] = (float)(pi[(size_t)v] - pi[(size_t)(nt - 1)]);
+        for (int64_t v = 0; v < nt; v++) p[(size_t)v] = (double)(pi[(size_t)v] - pi[(size_t)(nt - 1)]);
     } else if (o.warm_start == 3) {
-        PD_TRY(ws_diag_potentials(c, f.nodes, *w, &p, st));  // the greedy ranks arcs by their saving
+        PD_TRY(ws_diag_potentials(c, f.nodes, *w, &pf, st));  // the greedy ranks arcs by their saving
+    } else if (o.warm_start == 4) {
+        PD_TRY(ws_coarse_potentials(c, f, *w, o, &p, st));
+        if (p.empty()) return PD_OK;  // nothing to solve at the coarse level: cold start
     } else {
-        return fail(c, PD_EINVAL, "warm_start must be 0, 1, 2 or 3");
+        return fail(c, PD_EINVAL, "warm_start must be 0 .. 4");
     }
+    if (p.empty()) p.assign(pf.begin(), pf.end());
     return ns_warm_tree(c, &w->ns, p.data(), WARM_MAX_RESIDUAL, used, st);
 }
 
@@ -602,7 +638,7 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
                 pd_network net;
                 const WsTree given = f.tree;
                 PD_TRY(stage_network(c, f.nodes, f.s, &net, nullptr, nullptr, nullptr, st, false, nullptr,
-                                     o.tree == 1 ? &given : nullptr));
+                                     o.tree == 1 ? &given : nullptr, diag_cost(o)));
                 PD_TRY(merge_diagonal(c, net, f.nodes.n_nodes, &mnet, st));
             }
             PD_TRY(ns_solve_network(c, mnet, o, &ss, st));
@@ -709,12 +745,21 @@ static pd_status batch_prepare(Ctx* work, Ctx* slot, const pd_diagram& A, const 
     if (transport)
         PD_TRY(ns_prepare_w1(slot, bp->f.nodes, bp->f.net.n_arcs, bp->f.h.FB - bp->f.h.FA, o, &bp->w, st));
     if (bp->w.ns.ready) {
-        if (o.warm_start == 1) {
-            std::vector<float> p;
-            PD_TRY(ws_predict(work, bp->f.nodes, bp->w, &p, st));
+        if (o.warm_start == 1) {  // the coarse solve's potentials corrected by the network
+            std::vector<float> pf;
+            std::vector<double> p;
+            PD_TRY(ws_coarse_potentials(work, bp->f, bp->w, o, &p, st));
+            PD_TRY(ws_predict(work, bp->f.nodes, bp->w, &pf, st));
+            if (p.empty()) p.assign(pf.begin(), pf.end());
+            else
+                for (size_t v = 0; v < p.size() && v < pf.size(); v++) p[v] += pf[v];
             PD_TRY(ns_warm_tree(slot, &bp->w.ns, p.data(), WARM_MAX_RESIDUAL, &bp->warm, st));
+        } else if (o.warm_start == 4) {
+            std::vector<double> p;
+            PD_TRY(ws_coarse_potentials(work, bp->f, bp->w, o, &p, st));
+            if (!p.empty()) PD_TRY(ns_warm_tree(slot, &bp->w.ns, p.data(), WARM_MAX_RESIDUAL, &bp->warm, st));
         } else if (o.warm_start != 0) {
-            return fail(work, PD_EINVAL, "the batched solve takes warm_start 0 or 1");
+            return fail(work, PD_EINVAL, "the batched solve takes warm_start 0, 1 or 4");
         }
         PD_TRY(persist_for_certificate(slot, bp->f, bp, st));
     } else {
@@ -770,13 +815,13 @@ pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t 
     }
     for (Ctx* wk : c->workers) wk->mlp_owner = c;  // predictions use this context's network
     if (o.warm_start == 1 && !c->mlp_ready) return fail(c, PD_EINVAL, "warm_start = 1 needs a trained network");
-    NSInst* d = bufT<NSInst>(c, B_NS_INST, W);
-    if (!d) return PD_ENOMEM;
     // the workers start after everything already queued on the caller's stream
     cudaEvent_t ready;
     PD_TRY_CUDA(c, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
     std::vector<BatchPair> bp((size_t)W);
     std::vector<NSInst> hin, hout;
+    std::vector<CertJob> jobs;
+    std::vector<unsigned long long> cert;
     pd_status status = PD_OK;
     for (int64_t base = 0; base < count && status == PD_OK; base += W) {
         const int64_t nw = std::min<int64_t>(W, count - base);
@@ -820,35 +865,65 @@ pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t 
             status = fail(c, first, first_msg);
             break;
         }
-        // ---- one launch for the wave, one CTA per pair
+        // ---- the wave as one CUDA graph: records up, one persistent simplex
+        // launch (one CTA per SM takes the pairs, largest first), every pair's
+        // certificate in one launch, records and certificate counts down
         hin.clear();
+        jobs.clear();
         size_t smem = 0;
         for (int64_t j = 0; j < nw; j++) {
             BatchPair& p = bp[(size_t)j];
             if (p.done) continue;
             p.inst = (int)hin.size();
             hin.push_back(p.w.ns.h);
+            CertJob J{};
+            J.rec = p.inst;
+            J.S = p.w.S;
+            J.T = p.w.T;
+            J.nS = p.w.nS;
+            J.nT = p.w.nT;
+            J.s = p.f.s;
+            J.tree = p.tree;
+            J.dc = diag_cost(o);
+            jobs.push_back(J);
             smem = std::max(smem, p.w.ns.smem);
         }
         hout.assign(hin.size(), NSInst{});
+        cert.assign(2 * hin.size(), 0ull);
         c->last_ns_ms = 0.f;
         const auto tl = std::chrono::steady_clock::now();
         const long long lw = launch_count_ref();
-        status = ns_run(c, hin.data(), (int)hin.size(), smem, d, hout.data(), st);
-        if (status != PD_OK) break;
+        if (!hin.empty()) {
+            status = ns_run_wave(c, hin.data(), (int)hin.size(), smem, jobs.data(), hout.data(), cert.data(), st);
+            if (status != PD_OK) break;
+        }
         const float wave_ms = elapsed_ms(tl), wave_ns = c->last_ns_ms;
         const long long wave_launches = launch_count_ref() - lw;
-        // ---- certificates; a pair whose certificate fails is preprocessed
-        // again and solved on its sparse network
+        // ---- results; a pair whose certificate failed is preprocessed again
+        // and solved on its sparse network
         for (int64_t j = 0; j < nw && status == PD_OK; j++) {
             BatchPair& p = bp[(size_t)j];
             Ctx* sl = c->slots[(size_t)j];
+            sl->last_ns_ms = 0.f;
             if (!p.done) {
                 const long long l0 = launch_count_ref();
                 const auto t0 = std::chrono::steady_clock::now();
-                sl->last_ns_ms = 0.f;
-                status = ns_finish_w1(sl, p.tree, p.f.s, nullptr, o, p.w, d + p.inst, hout[(size_t)p.inst], &p.ss, st);
-                if (status == PD_OK && p.ss.method == -1) {
+                const NSInst& r = hout[(size_t)p.inst];
+                status = ns_status(sl, r);
+                if (status != PD_OK) {
+                    status = fail(c, status, "pair " + std::to_string(base + j) + ": " + sl->err);
+                    break;
+                }
+                p.ss = SolveStats{};
+                p.ss.pivots = r.pivots;
+                p.ss.degenerate = r.degenerate;
+                p.ss.scanned = r.scanned;
+                if (cert[2 * (size_t)p.inst] == 0) {
+                    p.ss.opt = r.opt;
+                    p.ss.slack = (int64_t)cert[2 * (size_t)p.inst + 1];
+                    p.ss.verified = 1;
+                    p.ss.method = 2;
+                } else {
                     Ctx* wk = c->workers[0];
                     const SolveStats first_try = p.ss;
                     wk->last_ns_ms = 0.f;
@@ -860,12 +935,8 @@ pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t 
                     p.ss.pivots += first_try.pivots;
                     p.ss.degenerate += first_try.degenerate;
                     p.ss.scanned += first_try.scanned;
-                    p.ss.cert_failures = first_try.cert_failures;
+                    p.ss.cert_failures = (int64_t)cert[2 * (size_t)p.inst];
                     sl->last_ns_ms += wk->last_ns_ms;
-                }
-                if (status != PD_OK) {
-                    status = fail(c, status, "pair " + std::to_string(base + j) + ": " + sl->err);
-                    break;
                 }
                 p.solve_ms = wave_ms + elapsed_ms(t0);
                 p.launches += wave_launches + (launch_count_ref() - l0);
@@ -916,11 +987,14 @@ extern "C" pd_status pd_ws_train(pd_ctx* c, const pd_diagram* A, const pd_diagra
         if (!w.ns.ready) continue;
         NSInst* d = bufT<NSInst>(c, B_NS_INST, 1);
         if (!d) return PD_ENOMEM;
+        // the network learns the correction to the coarse solve's potentials
+        std::vector<double> base;
+        PD_TRY(ws_coarse_potentials(c, f, w, o, &base, st));
         NSInst rec{};
         PD_TRY(ns_run(c, &w.ns.h, 1, w.ns.smem, d, &rec, st));
         PD_TRY(ns_status(c, rec));
         const int64_t cmax = (rec.big - 1) / (int64_t)(rec.n + 1) - 1;
-        PD_TRY(ws_collect(c, f.nodes, w, d, rec, cmax, st));
+        PD_TRY(ws_collect(c, f.nodes, w, d, rec, cmax, base.empty() ? nullptr : &base, st));
         r.pairs++;
         r.cold_pivots += rec.pivots;
     }

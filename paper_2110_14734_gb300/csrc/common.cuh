@@ -58,6 +58,18 @@ PD_D int64_t cost_diag(int32_t x, int32_t y) {
     return (int64_t)ceil_sqrt_u64((t2 + 1) >> 1);
 }
 
+// Cost of destroying a unit at (x, y) (arc to ā) or creating one there (from
+// b̄): kappa * (distance to the diagonal) + tau quanta; kappa 1, tau 0 for
+// persistence diagrams, anything else the unbalanced transport of the
+// Conclusion (ā and b̄ as destructor and creator).
+struct DiagCost {
+    int32_t kappa;  // 0 or 1
+    int32_t pad;
+    int64_t tau;    // >= 0
+};
+
+PD_D int64_t cost_make(int32_t x, int32_t y, DiagCost dc) { return (dc.kappa ? cost_diag(x, y) : 0) + dc.tau; }
+
 PD_HD int64_t floor_div(int64_t a, int64_t b) {  // b > 0
     int64_t q = a / b;
     return (a % b != 0 && a < 0) ? q - 1 : q;

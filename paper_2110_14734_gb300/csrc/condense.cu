@@ -229,11 +229,11 @@ __global__ void __launch_bounds__(RW_THREADS) k_rwmd_min(const int32_t* __restri
 
 __global__ void k_rwmd_sum(const int32_t* __restrict__ X, const int32_t* __restrict__ Y,
                            const int64_t* __restrict__ cnt, int64_t nA, int64_t n,
-                           const unsigned long long* __restrict__ mind2, int64_t* __restrict__ L) {
+                           const unsigned long long* __restrict__ mind2, DiagCost dc, int64_t* __restrict__ L) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long va = 0, vb = 0;
     if (i < n) {
-        int64_t c = cost_diag(X[i], Y[i]);
+        int64_t c = cost_make(X[i], Y[i], dc);
         unsigned long long m = mind2[i];
         if (m != ~0ull) {
             int64_t cn = (int64_t)ceil_sqrt_u64(m);
@@ -260,7 +260,7 @@ __global__ void k_fill_u64(unsigned long long* p, int64_t n, unsigned long long 
     if (i < n) p[i] = v;
 }
 
-pd_status stage_rwmd(Ctx* c, const Hats& h, int64_t L[3], cudaStream_t st) {
+pd_status stage_rwmd(Ctx* c, const Hats& h, int64_t L[3], DiagCost dc, cudaStream_t st) {
     int64_t n = h.nA + h.nB;
     int64_t* sm = bufT<int64_t>(c, B_SMALL, 64);
     unsigned long long* mind2 = bufT<unsigned long long>(c, B_QKEY2, n);
@@ -279,7 +279,7 @@ pd_status stage_rwmd(Ctx* c, const Hats& h, int64_t L[3], cudaStream_t st) {
         if (gy < 1) gy = 1;
         if (gx > 0 && h.nA > 0 && h.nB > 0)
             k_rwmd_min<<<dim3((unsigned)gx, (unsigned)gy, 2), RW_THREADS, 0, st>>>(h.X, h.Y, h.nA, h.nB, chunk, mind2); pd::count_launch();
-        k_rwmd_sum<<<grid_for(n, 256), 256, 0, st>>>(h.X, h.Y, h.cnt, h.nA, n, mind2, sm + S_L0); pd::count_launch();
+        k_rwmd_sum<<<grid_for(n, 256), 256, 0, st>>>(h.X, h.Y, h.cnt, h.nA, n, mind2, dc, sm + S_L0); pd::count_launch();
         PD_TRY_CUDA(c, cudaGetLastError());
     }
     PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, sizeof(int64_t) * S_COUNT, cudaMemcpyDeviceToHost, st));

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/pdw1.h"
+#include "common.cuh"
 
 namespace pd {
 
@@ -28,7 +29,7 @@ enum Buf : int {
     B_RS_COUNTS, B_RS_PART, B_SCAN_PART,
     B_M_ROWPTR, B_M_SUPPLY,
     B_NS_PI, B_NS_PARENT, B_NS_PRED, B_NS_FLOW, B_NS_UP, B_NS_ORD, B_NS_POS, B_NS_SIZE, B_NS_TMP,
-    B_NS_PATH, B_NS_SEG, B_NS_INST, B_NS_ORDER, B_NS_COST, B_TR_S, B_TR_T, B_TR_SUP, B_TR_XCOST,
+    B_NS_PATH, B_NS_SEG, B_NS_INST, B_NS_ORDER, B_NS_COST, B_NS_ART, B_TR_S, B_TR_T, B_TR_SUP, B_TR_XCOST,
     B_DB_SXY, B_DB_SCNT, B_DB_SID,  // nearest-neighbour database: staging
     B_DB_XY, B_DB_CNT, B_DB_ID, B_DB_OFF, B_DB_ROFF, B_Q_XY, B_Q_CNT, B_DB_LA, B_DB_BIG, B_DB_VAL, B_DB_PERS,
     B_MLP_P, B_MLP_M, B_MLP_V, B_MLP_WB, B_MLP_PART, B_MLP_G,  // warm-start network
@@ -36,6 +37,8 @@ enum Buf : int {
     B_WS_P, B_WS_ROWK, B_WS_COLK, B_WS_ARCS, B_WS_COST, B_WS_RS, B_WS_RT, B_WS_RC, B_WS_COMP, B_WS_CSIZE, B_WS_CSUM,
     B_SP_ORD, B_SP_ORD2, B_SP_SEG, B_SP_SEG2, B_SP_HI, B_SP_HI2, B_SP_NUM, B_SP_NUM2,  // split tree
     B_SP_BB, B_SP_REPK, B_SP_REPN, B_SP_FLAG, B_SP_RANK, B_SP_X, B_SP_Y, B_SP_CA, B_SP_CB, B_SP_CODE, B_SP_POS,
+    B_CO_BOX, B_CO_P, B_CO_P2,      // coarse-solve warm start
+    B_NS_JOBS, B_NS_CERT,           // batched certificate
     B_SMALL,                        // small device scalars
     B_COUNT
 };
@@ -72,7 +75,19 @@ struct Ctx {
     // pricing blocks chosen by pd_autotune, per size class (of the context that
     // ran it: slots and workers of a batch look theirs up in `parent`)
     std::map<int, int64_t> tuned_block;
+    std::map<int, int32_t> tuned_walk;
     Ctx* parent = nullptr;
+    Ctx* coarse = nullptr;            // helper context of the coarse solve (warm_start 4)
+    int64_t last_coarse_pivots = 0;   // pivots of the last coarse solve
+    // the batch's wave as a CUDA graph (ns_run_wave): pinned staging, the
+    // captured executable and what it was captured with
+    void* wave_pin = nullptr;
+    size_t wave_pin_bytes = 0;
+    cudaGraphExec_t wave_exec = nullptr;
+    cudaStream_t wave_stream = nullptr;
+    cudaEvent_t wave_ev[3] = {nullptr, nullptr, nullptr};
+    uint64_t wave_key = 0;
+    int64_t wave_launches = 0;        // graph launches (each replays the wave's kernels)
 };
 
 Ctx* ctx_new(int device, size_t cap);  // nullptr on failure
@@ -125,7 +140,7 @@ struct SolveStats {
 };
 
 pd_status stage_condense0(Ctx* c, const DevDiag& A, const DevDiag& B, int k, Hats* out, cudaStream_t st);
-pd_status stage_rwmd(Ctx* c, const Hats& h, int64_t L[3], cudaStream_t st);
+pd_status stage_rwmd(Ctx* c, const Hats& h, int64_t L[3], DiagCost dc, cudaStream_t st);
 pd_status stage_condense_delta(Ctx* c, const Hats& h, int64_t G, int64_t P, uint64_t seed, pd_nodes* out,
                                cudaStream_t st);
 // Hierarchical tree of the WSPD (device arrays of the context that built it):
@@ -147,7 +162,7 @@ struct WsTree {
 // built over `nodes` (the split tree), used instead of the radix tree.
 pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* out, float* ms_tree,
                         float* ms_wspd, float* ms_csr, cudaStream_t st, bool count_only = false,
-                        WsTree* tree = nullptr, const WsTree* given = nullptr);
+                        WsTree* tree = nullptr, const WsTree* given = nullptr, DiagCost dc = DiagCost{1, 0, 0});
 // The paper's split tree over `nodes` (splittree.cu): *nodes is replaced by
 // the nodes in the tree's leaf order (context buffers), *tree receives the
 // tree over those positions, *perm_out (may be null) position -> input index.
@@ -173,6 +188,13 @@ struct Front {
 // (enough for the transportation form and its certificate).
 pd_status front_half(Ctx* c, const pd_diagram& A, const pd_diagram& B, double eps, const pd_opts& o, Front* f,
                      cudaStream_t st, bool count_only);
+
+struct W1Prep;
+// Potentials of the fine transportation instance w from an exact solve of the
+// same pair condensed onto a coarser lattice (coarse.cu); empty if there is
+// nothing to solve at the coarse level.
+pd_status ws_coarse_potentials(Ctx* c, const Front& f, const W1Prep& w, const pd_opts& o, std::vector<double>* p,
+                               cudaStream_t st);
 pd_status stage_solve(Ctx* c, const pd_network& net, const pd_opts& o, SolveStats* out, cudaStream_t st);
 
 pd_status validate_nodes(Ctx* c, const pd_nodes& nodes, cudaStream_t st);
@@ -184,6 +206,10 @@ __global__ void k_max_cost(const int64_t* __restrict__ cost, int64_t m, unsigned
 __global__ void k_max_cost32(const int32_t* __restrict__ cost, int64_t m, unsigned long long* __restrict__ out);
 
 __global__ void k_row_ptr(const uint64_t* key, int64_t m, int hb, int64_t nrows, int64_t* row_ptr);
+
+// creation / destruction costs of the options (validated by check_diag_cost)
+inline DiagCost diag_cost(const pd_opts& o) { return DiagCost{o.diag_kappa, 0, o.diag_tau}; }
+pd_status check_diag_cost(Ctx* c, const pd_opts& o);
 
 // entry-point helpers shared by the C ABI files
 int default_shift(int dtype);                // k of the quantum for a dtype
@@ -198,6 +224,7 @@ pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t 
 // pd_autotune chose for it (0 = none: the default block).
 int tune_class(int64_t M);
 int64_t tuned_block(const Ctx* c, int64_t M);
+int32_t tuned_walk(const Ctx* c, int64_t M);  // the walk limit (16 when none was tuned)
 
 // radix sort / scan with context scratch
 pd_status sort_u64(Ctx* c, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, int64_t n,

@@ -126,14 +126,18 @@ __global__ void k_component_sum(const int64_t* __restrict__ pi, const int32_t* _
 // components hang from the root by artificial arcs, which fix their
 // potentials only up to an offset of their own; a common offset does not
 // matter to the start (only differences enter reduced costs).
+// Target of row r: its optimal potential minus the anchor component's mean,
+// less the same for the base potentials (a coarse solve's) when given, over
+// the node box's side; rows outside the anchor component are masked out.
 __global__ void k_targets(const int64_t* __restrict__ pi, const int32_t* __restrict__ comp, int64_t n,
-                          int32_t anchor, double mean, const long long* __restrict__ box, float* __restrict__ t,
-                          float* __restrict__ mask) {
+                          int32_t anchor, double mean, const double* __restrict__ base, double base_mean,
+                          const long long* __restrict__ box, float* __restrict__ t, float* __restrict__ mask) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const long long ext = max(max(box[2] - box[0], box[3] - box[1]), 1LL);
     const bool ok = comp[r] == anchor;
-    t[r] = ok ? (float)(((double)pi[r] - mean) / (double)ext) : 0.f;
+    const double b = base ? base[r] - base_mean : 0.0;
+    t[r] = ok ? (float)(((double)pi[r] - mean - b) / (double)ext) : 0.f;
     mask[r] = ok ? 1.f : 0.f;
 }
 
@@ -143,7 +147,7 @@ __global__ void k_targets(const int64_t* __restrict__ pi, const int32_t* __restr
 // both to the diagonal.
 __global__ void k_diag_potentials(const int32_t* __restrict__ X, const int32_t* __restrict__ Y,
                                   const int32_t* __restrict__ S, const int32_t* __restrict__ T, int64_t nS, int64_t nT,
-                                  float* __restrict__ p) {
+                                  float* __restrict__ p, DiagCost dc) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r > nS + nT) return;
     if (r == nS + nT) {
@@ -151,7 +155,7 @@ __global__ void k_diag_potentials(const int32_t* __restrict__ X, const int32_t* 
         return;
     }
     const int32_t u = r < nS ? S[r] : T[r - nS];
-    const float d = (float)cost_diag(X[u], Y[u]);
+    const float d = (float)cost_make(X[u], Y[u], dc);
     p[r] = r < nS ? d : -d;
 }
 
@@ -159,7 +163,7 @@ pd_status ws_diag_potentials(Ctx* c, const pd_nodes& nodes, const W1Prep& w, std
     const int64_t n = w.nS + w.nT;
     float* dp = bufT<float>(c, B_WS_PS, n + 1);
     if (!dp) return PD_ENOMEM;
-    k_diag_potentials<<<grid_for(n + 1, 256), 256, 0, st>>>(nodes.X, nodes.Y, w.S, w.T, w.nS, w.nT, dp); pd::count_launch();
+    k_diag_potentials<<<grid_for(n + 1, 256), 256, 0, st>>>(nodes.X, nodes.Y, w.S, w.T, w.nS, w.nT, dp, w.dc); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     p->resize((size_t)(n + 1));
     PD_TRY_CUDA(c, cudaMemcpyAsync(p->data(), dp, sizeof(float) * (n + 1), cudaMemcpyDeviceToHost, st));
@@ -531,7 +535,7 @@ pd_status ws_predict(Ctx* c, const pd_nodes& nodes, const W1Prep& w, std::vector
 // Training rows of one solved pair appended to the context's data set: the
 // instance's features and the targets from the solved record d_res.
 pd_status ws_collect(Ctx* c, const pd_nodes& nodes, const W1Prep& w, const NSInst* d_res, const NSInst& r,
-                     int64_t cmax, cudaStream_t st) {
+                     int64_t cmax, const std::vector<double>* base, cudaStream_t st) {
     const int64_t n = w.nS + w.nT;
     if (n <= 0) return PD_OK;
     const int64_t have = c->ws_rows;
@@ -560,8 +564,27 @@ pd_status ws_collect(Ctx* c, const pd_nodes& nodes, const W1Prep& w, const NSIns
     PD_TRY_CUDA(c, cudaMemcpyAsync(&hsum, sum, sizeof(hsum), cudaMemcpyDeviceToHost, st));
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     const double mean = (double)(int64_t)hsum / (double)std::max(hs[(size_t)anchor], 1);
-    k_targets<<<grid_for(n, 256), 256, 0, st>>>(r.pi, comp, n, anchor, mean, box, T + have, M + have); pd::count_launch();
+    // base potentials: the network learns the correction to them
+    double* db = nullptr;
+    double bmean = 0.0;
+    if (base && (int64_t)base->size() >= n) {
+        std::vector<int32_t> hc((size_t)n);
+        PD_TRY_CUDA(c, cudaMemcpyAsync(hc.data(), comp, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+        PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+        int64_t cnt = 0;
+        for (int64_t v = 0; v < n; v++)
+            if (hc[(size_t)v] == anchor) {
+                bmean += (*base)[(size_t)v];
+                cnt++;
+            }
+        bmean = cnt ? bmean / (double)cnt : 0.0;
+        db = bufT<double>(c, B_CO_P2, n);
+        if (!db) return PD_ENOMEM;
+        PD_TRY_CUDA(c, cudaMemcpyAsync(db, base->data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    }
+    k_targets<<<grid_for(n, 256), 256, 0, st>>>(r.pi, comp, n, anchor, mean, db, bmean, box, T + have, M + have); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));  // the base copy's host memory belongs to the caller
     (void)d_res;
     (void)cmax;
     c->ws_rows = have + n;

@@ -39,12 +39,12 @@ pd_status ws_predict(Ctx* c, const pd_nodes& nodes, const W1Prep& w, std::vector
 // Potentials +d(u) / -d(v) from the distance to the diagonal (host, nS + nT + 1).
 pd_status ws_diag_potentials(Ctx* c, const pd_nodes& nodes, const W1Prep& w, std::vector<float>* p, cudaStream_t st);
 pd_status ws_collect(Ctx* c, const pd_nodes& nodes, const W1Prep& w, const NSInst* d_res, const NSInst& r,
-                     int64_t cmax, cudaStream_t st);
+                     int64_t cmax, const std::vector<double>* base, cudaStream_t st);
 
 // Strongly feasible start of a prepared transportation instance from
 // potentials p (host, one per transportation node, cost units); the greedy
 // takes all arcs between the unbalanced nodes once at most max_residual are
 // left.  *used = false (instance untouched) if the greedy does not balance.
-pd_status ns_warm_tree(Ctx* c, NSPrep* prep, const float* p, int64_t max_residual, bool* used, cudaStream_t st);
+pd_status ns_warm_tree(Ctx* c, NSPrep* prep, const double* p, int64_t max_residual, bool* used, cudaStream_t st);
 
 }  // namespace pd

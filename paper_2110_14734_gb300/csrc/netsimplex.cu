@@ -18,7 +18,9 @@
 // 32-bit arrays in global memory.
 //
 // Big-M start: node i has an artificial arc to (supply >= 0) or from (< 0) an
-// extra root; zero-flow tree arcs point to the root (strongly feasible tree),
+// extra root, of cost big (more than any path of real arcs) plus an optional
+// per-node offset >= 0 that a warm start uses to place its tree components'
+// potentials; zero-flow tree arcs point to the root (strongly feasible tree),
 // and the leaving arc is the last blocking arc met when the cycle is walked
 // from the apex in the direction of the entering arc, which rules out cycling.
 // An instance may instead carry its own strongly feasible start (warm start).
@@ -61,14 +63,7 @@ PD_D void arc_ends(const NSInst& I, int64_t a, int32_t* t, int32_t* h) {
 PD_D int64_t arc_cost(const NSInst& I, int64_t a, int64_t big) {
     if (a < I.mst) return I.cmat[a];
     if (a < I.m) return I.cost[a - I.mst];
-    return big;
-}
-
-PD_D void take_min(int64_t rc, int64_t a, int64_t& lb, int64_t& li) {
-    if (rc < lb || (rc == lb && rc < 0 && a < li)) {
-        lb = rc;
-        li = a;
-    }
+    return I.art ? big + I.art[a - I.m] : big;  // artificial arc of node a - m
 }
 
 // Node arrays of the spanning tree.  IX = uint16_t: compact layout in shared
@@ -117,11 +112,8 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
     __shared__ uint32_t s_mask[2][32][NS_REGS];  // path discovery ballots, i-side and j-side
     __shared__ int32_t s_cnt[2][32];
     __shared__ int64_t s_dpi;
-    __shared__ int32_t s_go, s_status;
+    __shared__ int32_t s_go, s_status, s_scan;
     __shared__ int32_t s_L0, s_S, s_pr, s_nseg, s_segsm;
-    __shared__ uint32_t s_cand[32];      // candidate list: other warps' winners of the last priced block
-    __shared__ int32_t s_ncand[2], s_ment;  // list size, double-buffered by pivot parity
-    __shared__ int64_t s_mrc;
     __shared__ int32_t sseg[3][NS_SEGSM];
     const int32_t SEGN = 2 * n + 3;
 
@@ -160,14 +152,12 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
         T.sz[root] = (IX)N1;
         s_status = 0;
     }
-    if (tid == 0) s_ncand[0] = s_ncand[1] = 0;
     __syncthreads();
     const uint64_t t0 = ns_now();
     int64_t pivots = 0, degen = 0, nscan = 0;
     const int64_t B = I.block < 1 ? 1 : I.block;
     int64_t next = 0;  // first arc of the next pricing block (same in every thread)
     int pb_buf = 0;
-    int cb = 0;  // parity of the pivot: the candidate count is read from s_ncand[cb], written to s_ncand[cb ^ 1]
 
     for (;;) {
         // ---- pricing: blocks of B arcs from `next`; the most negative reduced
@@ -179,42 +169,7 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
         // deterministic.
         int64_t scanned = 0, a0 = next;
         int64_t ent = -1, rc = 0;
-        if (s_ncand[cb] > 0) {
-            // minor iteration: one warp re-prices the candidate list with the
-            // current potentials; the most negative still-negative arc enters
-            // (same key and tie rule as a block), the rest stay candidates
-            if (wid == 0) {
-                const int32_t nc = s_ncand[cb];
-                uint32_t a = 0xffffffffu;
-                int64_t r = 0;
-                if (lane < nc) {
-                    a = s_cand[lane];
-                    int32_t t, h;
-                    arc_ends(I, a, &t, &h);
-                    r = arc_cost(I, a, big) - T.pi[t] + T.pi[h];
-                }
-                const int32_t key = r < 0 ? -__float_as_int((float)(-r)) : 0;
-                const int32_t wmin = __reduce_min_sync(FULL, key);
-                const uint32_t cand = (wmin < 0 && key == wmin) ? a : 0xffffffffu;
-                const uint32_t widx = __reduce_min_sync(FULL, cand);
-                if (wmin < 0 && cand == widx) s_mrc = r;
-                const bool keep = lane < nc && r < 0 && a != widx;
-                const uint32_t km = __ballot_sync(FULL, keep);
-                if (keep) s_cand[__popc(km & ((1u << lane) - 1u))] = a;
-                if (lane == 0) {
-                    s_ment = wmin < 0 ? (int32_t)widx : -1;
-                    s_ncand[cb ^ 1] = __popc(km);
-                }
-                nscan += nc;
-            }
-            __syncthreads();
-            if (s_ment >= 0) {
-                ent = s_ment;
-                rc = s_mrc;
-                scanned = M;  // no block priced
-            }
-        }
-        while (ent < 0 && scanned < M) {
+        while (scanned < M) {
             const int64_t aend = a0 + B < M ? a0 + B : M;
             const int64_t len = aend - a0;
             {
@@ -225,27 +180,37 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
                 if (pf + 8 <= I.mst && 8 * (int64_t)tid < B)
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(I.cmat + pf));
             }
-            int64_t lb = 0, li = -1;
+            // per thread: the most negative reduced cost (lb) and its arc (li);
+            // arcs are visited in ascending order, so the strict < keeps the
+            // smallest index among equal costs.  Arc ids are below 2^31.
+            int64_t lb = 0;
+            int32_t li = -1;
             // consecutive lanes take consecutive arcs: coalesced 4-byte loads,
             // and the sink potentials pi(nS + j) they read are consecutive
             // 8-byte words of shared memory (no bank conflicts)
-            const int64_t iend = aend < I.mst ? aend : I.mst;
-            const int32_t nT = (int32_t)I.nT, step_i = NS_THREADS / nT, step_j = NS_THREADS - step_i * nT;
-            for (int64_t base = a0; base < iend; base += NS_PR * NS_THREADS) {
+            const int32_t iend = (int32_t)(aend < I.mst ? aend : I.mst);
+            const int32_t nT = (int32_t)I.nT, nS = (int32_t)I.nS;
+            const int32_t step_i = NS_THREADS / nT, step_j = NS_THREADS - step_i * nT;
+            for (int32_t base = (int32_t)a0; base < iend; base += NS_PR * NS_THREADS) {
                 int32_t cv[NS_PR];
 #pragma unroll
                 for (int q = 0; q < NS_PR; q++) {
-                    const int64_t a = base + tid + q * NS_THREADS;
+                    const int32_t a = base + tid + q * NS_THREADS;  // no overflow: m + n + 8 NS_THREADS < 2^31
                     cv[q] = a < iend ? __ldcg(I.cmat + a) : 0;
                 }
-                // row i and column j of arc base + tid (< 2^31), then NS_THREADS
-                // arcs further per step
-                const int32_t a1 = (int32_t)(base + tid);
+                // row i and column j of arc base + tid, then NS_THREADS arcs further per step
+                const int32_t a1 = base + tid;
                 int32_t i = a1 / nT, j = a1 - i * nT;
 #pragma unroll
                 for (int q = 0; q < NS_PR; q++) {
-                    const int64_t a = (int64_t)a1 + q * NS_THREADS;
-                    if (a < iend) take_min((int64_t)cv[q] - T.pi[i] + T.pi[I.nS + j], a, lb, li);
+                    const int32_t a = a1 + q * NS_THREADS;
+                    if (a < iend) {
+                        const int64_t r = (int64_t)cv[q] - T.pi[i] + T.pi[nS + j];
+                        if (r < lb) {
+                            lb = r;
+                            li = a;
+                        }
+                    }
                     i += step_i;
                     j += step_j;
                     if (j >= nT) {
@@ -259,7 +224,11 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
             for (int64_t a = (a0 > I.mst ? a0 : I.mst) + tid; a < aend; a += NS_THREADS) {
                 int32_t t, h;
                 arc_ends(I, a, &t, &h);
-                take_min(arc_cost(I, a, big) - T.pi[t] + T.pi[h], a, lb, li);
+                const int64_t r = arc_cost(I, a, big) - T.pi[t] + T.pi[h];
+                if (r < lb) {
+                    lb = r;
+                    li = (int32_t)a;
+                }
             }
             const int32_t key = lb < 0 ? -__float_as_int((float)(-lb)) : 0;
             const int32_t wmin = __reduce_min_sync(FULL, key);
@@ -284,12 +253,6 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
                 rc = s_wval[pb_buf][wl];
                 ent = bidx;
                 next = a0;
-                if (I.minor && wid == 0) {  // the other warps' negative winners become the candidate list
-                    const bool keep = k2 < 0 && i2 != bidx;
-                    const uint32_t km = __ballot_sync(FULL, keep);
-                    if (keep) s_cand[__popc(km & ((1u << lane) - 1u))] = i2;
-                    if (lane == 0) s_ncand[cb ^ 1] = __popc(km);
-                }
                 pb_buf ^= 1;
                 break;
             }
@@ -307,78 +270,19 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
         // on i's side; PB likewise from j.
         int32_t i, j;
         arc_ends(I, ent, &i, &j);
-        if constexpr (sizeof(IX) == 2) {
-            // whole CTA: a node is on i's side iff it is an ancestor of i (or i)
-            // and not of j, by the preorder test pos(v) <= pos(x) < pos(v) +
-            // size(v).  Each warp scans a contiguous range of preorder positions
-            // (so matches come out ordered from the apex down); ballots are kept
-            // for the second pass, which writes each match at its rank.
-            const int32_t pi_ = T.ps[i], pj = T.ps[j];
-            const int32_t C = (((N1 + 31) / 32) + 31) & ~31;  // positions per warp, <= 32 * NS_REGS
-            const int32_t x0 = wid * C;
-            // an ancestor's position is at most the descendant's: no warp looks
-            // past max(pos(i), pos(j))
-            const int32_t xmax = pi_ > pj ? pi_ : pj;
-            const int32_t iters = xmax < x0 ? 0 : min(C >> 5, ((xmax - x0) >> 5) + 1);
-            int32_t cI = 0, cJ = 0;
-            for (int32_t it = 0; it < iters; it++) {
-                const int32_t x = x0 + (it << 5) + lane;
-                bool inI = false, inJ = false;
-                if (x < N1) {
-                    const int32_t e = x + (int32_t)T.sz[T.od[x]];
-                    const bool ai = x <= pi_ && pi_ < e, aj = x <= pj && pj < e;
-                    inI = ai && !aj;
-                    inJ = aj && !ai;
-                }
-                const uint32_t bI = __ballot_sync(FULL, inI), bJ = __ballot_sync(FULL, inJ);
-                if (lane == 0) {
-                    s_mask[0][wid][it] = bI;
-                    s_mask[1][wid][it] = bJ;
-                }
-                cI += __popc(bI);
-                cJ += __popc(bJ);
-            }
-            if (lane == 0) {
-                s_cnt[0][wid] = cI;
-                s_cnt[1][wid] = cJ;
-            }
-            __syncthreads();
-            const int32_t mI = s_cnt[0][lane], mJ = s_cnt[1][lane];
-            int32_t oI = __reduce_add_sync(FULL, lane < wid ? mI : 0);
-            int32_t oJ = __reduce_add_sync(FULL, lane < wid ? mJ : 0);
-            const int32_t la = __reduce_add_sync(FULL, mI), lb = __reduce_add_sync(FULL, mJ);
-            const uint32_t below = (1u << lane) - 1u;
-            const int32_t iters2 = (s_cnt[0][wid] + s_cnt[1][wid]) > 0 ? iters : 0;  // warps without a match skip
-            for (int32_t it = 0; it < iters2; it++) {
-                const uint32_t bI = s_mask[0][wid][it], bJ = s_mask[1][wid][it];
-                if ((bI | bJ) == 0) continue;
-                const int32_t x = x0 + (it << 5) + lane;
-                if ((bI >> lane) & 1u) {
-                    const int32_t t = la - 1 - (oI + __popc(bI & below));
-                    const int32_t v = T.od[x];
-                    if (t < NS_LMAX) pa[t] = v; else gpa[t] = v;
-                }
-                if ((bJ >> lane) & 1u) {
-                    const int32_t t = lb - 1 - (oJ + __popc(bJ & below));
-                    const int32_t v = T.od[x];
-                    if (t < NS_LMAX) pb[t] = v; else gpb[t] = v;
-                }
-                oI += __popc(bI);
-                oJ += __popc(bJ);
-            }
-            if (tid == 0) {
-                s_la = la;
-                s_lb = lb;
-            }
-            __syncthreads();
-        } else if (wid == 0) {
-            // large trees (global memory): lanes 0 and 1 walk up from i and j
-            // until they reach an ancestor of the other end
+        // lanes 0 and 1 of warp 0 walk up from i and from j until they reach
+        // an ancestor of the other end (preorder test pos(v) <= pos(x) <
+        // pos(v) + size(v)); on the shared-memory layout a side longer than
+        // I.walk nodes is left to the CTA-wide scan below (a step of the walk
+        // is a dependent shared-memory round trip, the scan costs about
+        // N / 1024 positions per thread and two barriers, whatever the path)
+        if (wid == 0) {
             if (lane < 2) {
                 int32_t u = lane == 0 ? i : j;
                 const int32_t tgt = lane == 0 ? (int32_t)T.ps[j] : (int32_t)T.ps[i];
                 int32_t* sp = lane == 0 ? pa : pb;
                 int32_t* gp = lane == 0 ? gpa : gpb;
+                const int32_t cap = sizeof(IX) == 2 ? I.walk : n;
                 int32_t len = 0;
                 for (;;) {
                     if (u < 0 || len >= n) {  // no ancestor found within n steps: corrupt tree
@@ -387,6 +291,10 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
                     }
                     const int32_t pu = T.ps[u];
                     if (pu <= tgt && tgt < pu + (int32_t)T.sz[u]) break;
+                    if (len >= cap) {  // too long for one lane: the scan finds it
+                        len = -2;
+                        break;
+                    }
                     if (len < NS_LMAX) sp[len] = u; else gp[len] = u;
                     len++;
                     u = T.parent(u);
@@ -394,6 +302,75 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
                 if (lane == 0) s_la = len; else s_lb = len;
             }
             __syncwarp();
+            if (lane == 0) s_scan = (s_la == -2 || s_lb == -2) ? 1 : 0;
+        }
+        if constexpr (sizeof(IX) == 2) {
+            __syncthreads();
+            if (s_scan) {
+                // whole CTA: a node is on i's side iff it is an ancestor of i (or i)
+                // and not of j, by the preorder test pos(v) <= pos(x) < pos(v) +
+                // size(v).  Each warp scans a contiguous range of preorder positions
+                // (so matches come out ordered from the apex down); ballots are kept
+                // for the second pass, which writes each match at its rank.
+                const int32_t pi_ = T.ps[i], pj = T.ps[j];
+                const int32_t C = (((N1 + 31) / 32) + 31) & ~31;  // positions per warp, <= 32 * NS_REGS
+                const int32_t x0 = wid * C;
+                // an ancestor's position is at most the descendant's: no warp looks
+                // past max(pos(i), pos(j))
+                const int32_t xmax = pi_ > pj ? pi_ : pj;
+                const int32_t iters = xmax < x0 ? 0 : min(C >> 5, ((xmax - x0) >> 5) + 1);
+                int32_t cI = 0, cJ = 0;
+                for (int32_t it = 0; it < iters; it++) {
+                    const int32_t x = x0 + (it << 5) + lane;
+                    bool inI = false, inJ = false;
+                    if (x < N1) {
+                        const int32_t e = x + (int32_t)T.sz[T.od[x]];
+                        const bool ai = x <= pi_ && pi_ < e, aj = x <= pj && pj < e;
+                        inI = ai && !aj;
+                        inJ = aj && !ai;
+                    }
+                    const uint32_t bI = __ballot_sync(FULL, inI), bJ = __ballot_sync(FULL, inJ);
+                    if (lane == 0) {
+                        s_mask[0][wid][it] = bI;
+                        s_mask[1][wid][it] = bJ;
+                    }
+                    cI += __popc(bI);
+                    cJ += __popc(bJ);
+                }
+                if (lane == 0) {
+                    s_cnt[0][wid] = cI;
+                    s_cnt[1][wid] = cJ;
+                }
+                __syncthreads();
+                const int32_t mI = s_cnt[0][lane], mJ = s_cnt[1][lane];
+                int32_t oI = __reduce_add_sync(FULL, lane < wid ? mI : 0);
+                int32_t oJ = __reduce_add_sync(FULL, lane < wid ? mJ : 0);
+                const int32_t la = __reduce_add_sync(FULL, mI), lb = __reduce_add_sync(FULL, mJ);
+                const uint32_t below = (1u << lane) - 1u;
+                const int32_t iters2 = (s_cnt[0][wid] + s_cnt[1][wid]) > 0 ? iters : 0;  // warps without a match skip
+                for (int32_t it = 0; it < iters2; it++) {
+                    const uint32_t bI = s_mask[0][wid][it], bJ = s_mask[1][wid][it];
+                    if ((bI | bJ) == 0) continue;
+                    const int32_t x = x0 + (it << 5) + lane;
+                    if ((bI >> lane) & 1u) {
+                        const int32_t t = la - 1 - (oI + __popc(bI & below));
+                        const int32_t v = T.od[x];
+                        if (t < NS_LMAX) pa[t] = v; else gpa[t] = v;
+                    }
+                    if ((bJ >> lane) & 1u) {
+                        const int32_t t = lb - 1 - (oJ + __popc(bJ & below));
+                        const int32_t v = T.od[x];
+                        if (t < NS_LMAX) pb[t] = v; else gpb[t] = v;
+                    }
+                    oI += __popc(bI);
+                    oJ += __popc(bJ);
+                }
+                if (tid == 0) {
+                    s_la = la;
+                    s_lb = lb;
+                }
+                __syncthreads();
+            }
         }
 
         // ---- pivot (one warp): leaving arc, flow change, re-rooting ----------
@@ -674,7 +651,6 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
                 }
             }
         }
-        cb ^= 1;
     }
     // ---- result: node arrays back to the global record ---------------------
     __syncthreads();
@@ -860,14 +836,16 @@ pd_status ns_prepare_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS,
         !h.seg)
         return PD_ENOMEM;
     int64_t M = m + n;
-    if (M >= (int64_t(1) << 31) - 1) return fail(c, PD_ECAPACITY, "network simplex needs fewer than 2^31 arcs");
+    // arc ids, plus one pricing step past the last arc, stay below 2^31
+    if (M >= (int64_t(1) << 31) - 1 - 8 * NS_THREADS)
+        return fail(c, PD_ECAPACITY, "network simplex needs fewer than 2^31 - 8193 arcs");
     // default block: one pass of the CTA (8 arcs per thread), more for very
     // large networks; blocks start at multiples of 8 (vector loads)
     int64_t blk = o.ns_block > 0 ? o.ns_block : tuned_block(c, M);
     if (blk <= 0) blk = std::max<int64_t>(8 * NS_THREADS, (int64_t)sqrt((double)M));
     blk = (blk + 7) & ~(int64_t)7;
     h.block = blk;
-    h.minor = o.ns_candidates != 0 ? 1 : 0;
+    h.walk = o.ns_walk >= 0 ? std::min<int32_t>(o.ns_walk, NS_LMAX) : tuned_walk(c, M);
     h.max_pivots = o.max_rounds > 0 ? o.max_rounds : (int64_t(1) << 40);
     h.time_limit_ns = (o.time_limit_ms > 0 ? (uint64_t)o.time_limit_ms : 60000ull) * 1000000ull;
     // flows are int32: the total supply must stay below 2^31
@@ -916,15 +894,130 @@ pd_status ns_run(Ctx* c, const NSInst* h, int count, size_t smem, NSInst* d, NSI
     PD_TRY_CUDA(c, cudaEventRecord(e0, st));
     k_netsimplex<<<grid, NS_THREADS, smem, st>>>(d, dord, count, dord + count); pd::count_launch();
     cudaError_t le = cudaGetLastError();
-    cudaEventRecord(e1, st);
+    if (le == cudaSuccess) le = cudaEventRecord(e1, st);
     if (le == cudaSuccess) le = cudaMemcpyAsync(r, d, sizeof(NSInst) * count, cudaMemcpyDeviceToHost, st);
     if (le == cudaSuccess) le = cudaStreamSynchronize(st);
     float nms = 0.f;
-    if (le == cudaSuccess) cudaEventElapsedTime(&nms, e0, e1);
+    if (le == cudaSuccess) le = cudaEventElapsedTime(&nms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (le != cudaSuccess) return cuda_fail(c, le, "k_netsimplex");
     c->last_ns_ms += nms;
+    return PD_OK;
+}
+
+// Pinned staging of a wave: records in, records out, order (+ counter),
+// certificate jobs, certificate counts.
+struct WaveLayout {
+    size_t in, out, ord, jobs, cert, total;
+    explicit WaveLayout(int count) {
+        auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+        in = 0;
+        out = in + al(sizeof(NSInst) * count);
+        ord = out + al(sizeof(NSInst) * count);
+        jobs = ord + al(sizeof(int32_t) * (count + 1));
+        cert = jobs + al(sizeof(CertJob) * count);
+        total = cert + al(2 * sizeof(unsigned long long) * count);
+    }
+};
+
+constexpr int WAVE_CERT_BLOCKS = 8;  // blocks per pair of the batched certificate (grid-stride)
+
+pd_status ns_run_wave(Ctx* c, const NSInst* h, int count, size_t smem, const CertJob* jobs, NSInst* r,
+                      unsigned long long* cert, cudaStream_t st) {
+    if (count <= 0) return PD_OK;
+    PD_TRY_CUDA(c, ns_kernel_setup());
+    int per_sm = 0;
+    PD_TRY_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_netsimplex, NS_THREADS, smem));
+    if (per_sm < 1) return fail(c, PD_ECAPACITY, "network simplex kernel does not fit on an SM");
+    const int grid = std::min(count, per_sm * std::max(c->sm_count, 1));
+    const WaveLayout L(count);
+    if (c->wave_pin_bytes < L.total) {
+        if (c->wave_exec) cudaGraphExecDestroy(c->wave_exec);
+        c->wave_exec = nullptr;
+        if (c->wave_pin) cudaFreeHost(c->wave_pin);
+        c->wave_pin = nullptr;
+        c->wave_pin_bytes = 0;
+        PD_TRY_CUDA(c, cudaMallocHost(&c->wave_pin, L.total));
+        c->wave_pin_bytes = L.total;
+    }
+    if (!c->wave_stream) PD_TRY_CUDA(c, cudaStreamCreateWithFlags(&c->wave_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : c->wave_ev)
+        if (!e) PD_TRY_CUDA(c, cudaEventCreate(&e));
+    unsigned char* pin = (unsigned char*)c->wave_pin;
+    NSInst* p_in = (NSInst*)(pin + L.in);
+    NSInst* p_out = (NSInst*)(pin + L.out);
+    int32_t* p_ord = (int32_t*)(pin + L.ord);
+    CertJob* p_jobs = (CertJob*)(pin + L.jobs);
+    unsigned long long* p_cert = (unsigned long long*)(pin + L.cert);
+    NSInst* d = bufT<NSInst>(c, B_NS_INST, count);
+    int32_t* dord = bufT<int32_t>(c, B_NS_ORDER, count + 1);
+    CertJob* djobs = bufT<CertJob>(c, B_NS_JOBS, count);
+    unsigned long long* dcert = bufT<unsigned long long>(c, B_NS_CERT, 2 * count);
+    if (!d || !dord || !djobs || !dcert) return PD_ENOMEM;
+    // this wave's contents into the pinned staging the graph copies from;
+    // largest instances first (nodes, then arcs), ties by position
+    memcpy(p_in, h, sizeof(NSInst) * count);
+    for (int q = 0; q < count; q++) p_ord[q] = q;
+    std::stable_sort(p_ord, p_ord + count, [&](int32_t x, int32_t y) {
+        return h[x].n != h[y].n ? h[x].n > h[y].n : h[x].m > h[y].m;
+    });
+    p_ord[count] = 0;
+    for (int q = 0; q < count; q++) {
+        if (jobs[q].rec < 0 || jobs[q].rec >= count) return fail(c, PD_EINVAL, "certificate job without a record");
+        p_jobs[q] = jobs[q];
+        p_jobs[q].inst = d + jobs[q].rec;
+    }
+    // the executable is reused while everything it was captured with is the same
+    uint64_t key = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
+    mix((uint64_t)count);
+    mix((uint64_t)grid);
+    mix((uint64_t)smem);
+    mix((uint64_t)(uintptr_t)pin);
+    mix((uint64_t)(uintptr_t)d);
+    mix((uint64_t)(uintptr_t)dord);
+    mix((uint64_t)(uintptr_t)djobs);
+    mix((uint64_t)(uintptr_t)dcert);
+    cudaStream_t gs = c->wave_stream;
+    if (!c->wave_exec || c->wave_key != key) {
+        if (c->wave_exec) cudaGraphExecDestroy(c->wave_exec);
+        c->wave_exec = nullptr;
+        PD_TRY_CUDA(c, cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+        cudaMemcpyAsync(d, p_in, sizeof(NSInst) * count, cudaMemcpyHostToDevice, gs);
+        cudaMemcpyAsync(dord, p_ord, sizeof(int32_t) * (count + 1), cudaMemcpyHostToDevice, gs);
+        cudaMemcpyAsync(djobs, p_jobs, sizeof(CertJob) * count, cudaMemcpyHostToDevice, gs);
+        cudaMemsetAsync(dcert, 0, 2 * sizeof(unsigned long long) * count, gs);
+        k_netsimplex<<<grid, NS_THREADS, smem, gs>>>(d, dord, count, dord + count);
+        k_certify_batch<<<dim3(WAVE_CERT_BLOCKS, count), 256, 0, gs>>>(djobs, dcert);
+        cudaMemcpyAsync(p_out, d, sizeof(NSInst) * count, cudaMemcpyDeviceToHost, gs);
+        cudaMemcpyAsync(p_cert, dcert, 2 * sizeof(unsigned long long) * count, cudaMemcpyDeviceToHost, gs);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(gs, &g);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->wave_exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->wave_exec = nullptr;
+            return cuda_fail(c, e, "capture of the batch wave");
+        }
+        c->wave_key = key;
+    }
+    PD_TRY_CUDA(c, cudaEventRecord(c->wave_ev[2], st));  // the wave follows the work queued on st
+    PD_TRY_CUDA(c, cudaStreamWaitEvent(gs, c->wave_ev[2], 0));
+    // device time of the whole graph (the simplex is nearly all of it: the
+    // other nodes move a few hundred bytes per pair)
+    PD_TRY_CUDA(c, cudaEventRecord(c->wave_ev[0], gs));
+    PD_TRY_CUDA(c, cudaGraphLaunch(c->wave_exec, gs));
+    PD_TRY_CUDA(c, cudaEventRecord(c->wave_ev[1], gs));
+    pd::count_launch();  // the persistent simplex
+    pd::count_launch();  // the batched certificate
+    c->wave_launches++;
+    PD_TRY_CUDA(c, cudaStreamSynchronize(gs));
+    float nms = 0.f;
+    PD_TRY_CUDA(c, cudaEventElapsedTime(&nms, c->wave_ev[0], c->wave_ev[1]));
+    c->last_ns_ms += nms;
+    memcpy(r, p_out, sizeof(NSInst) * count);
+    memcpy(cert, p_cert, 2 * sizeof(unsigned long long) * count);
     return PD_OK;
 }
 
@@ -986,7 +1079,7 @@ __global__ void k_side_lists(const int64_t* __restrict__ cntA, const int64_t* __
 __global__ void k_transport_arcs(const int32_t* __restrict__ S, const int32_t* __restrict__ T, int64_t nS,
                                  int64_t nT, int dside, const int32_t* __restrict__ X, const int32_t* __restrict__ Y,
                                  int32_t* __restrict__ cmat, int32_t* __restrict__ tail, int32_t* __restrict__ head,
-                                 int32_t* __restrict__ cost, unsigned long long* __restrict__ bad) {
+                                 int32_t* __restrict__ cost, unsigned long long* __restrict__ bad, DiagCost dc) {
     int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t mst = nS * nT;
     int64_t D = nS + nT;
@@ -995,7 +1088,7 @@ __global__ void k_transport_arcs(const int32_t* __restrict__ S, const int32_t* _
         int64_t i = a / nT, j = a - i * nT;
         int32_t u = S[i], v = T[j];
         int64_t d = cost_l2(X[u], Y[u], X[v], Y[v]);
-        int64_t g = cost_diag(X[u], Y[u]) + cost_diag(X[v], Y[v]);
+        int64_t g = cost_make(X[u], Y[u], dc) + cost_make(X[v], Y[v], dc);
         c = d < g ? d : g;
         if (c >= (int64_t(1) << 31)) atomicAdd(bad, 1ull);
         cmat[a] = (int32_t)c;
@@ -1003,13 +1096,13 @@ __global__ void k_transport_arcs(const int32_t* __restrict__ S, const int32_t* _
     } else if (dside < 0 && a < mst + nS) {
         int64_t i = a - mst;
         int32_t u = S[i];
-        c = cost_diag(X[u], Y[u]);
+        c = cost_make(X[u], Y[u], dc);
         tail[a - mst] = (int32_t)i;
         head[a - mst] = (int32_t)D;
     } else if (dside > 0 && a < mst + nT) {
         int64_t j = a - mst;
         int32_t v = T[j];
-        c = cost_diag(X[v], Y[v]);
+        c = cost_make(X[v], Y[v], dc);
         tail[a - mst] = (int32_t)D;
         head[a - mst] = (int32_t)(nS + j);
     } else {
@@ -1082,7 +1175,10 @@ pd_status ns_prepare_w1(Ctx* c, const pd_nodes& nodes, int64_t n_arcs, int64_t d
     int64_t nS = c->h_small[2], nT = c->h_small[3];
     int64_t mst = nS * nT;
     int64_t mt = mst + (dsup < 0 ? nS : (dsup > 0 ? nT : 0));
-    if (!(mt <= 2 * n_arcs + 4096 && mt < (int64_t(1) << 31))) return PD_OK;
+    // the transportation form when it is not much larger than the sparse
+    // network (ns_transport 1), or whenever its arc ids fit (2)
+    if (!((o.ns_transport == 2 || mt <= 2 * n_arcs + 4096) && mt < (int64_t(1) << 31) - 1 - 8 * NS_THREADS))
+        return PD_OK;
     int64_t nt = nS + nT + 1;
     int32_t* S = bufT<int32_t>(c, B_TR_S, nS);
     int32_t* T = bufT<int32_t>(c, B_TR_T, nT);
@@ -1099,7 +1195,7 @@ pd_status ns_prepare_w1(Ctx* c, const pd_nodes& nodes, int64_t n_arcs, int64_t d
     PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, 8 * sizeof(unsigned long long), st));
     if (mt > 0)
         k_transport_arcs<<<grid_for(mt, 256), 256, 0, st>>>(S, T, nS, nT, dsup < 0 ? -1 : (dsup > 0 ? 1 : 0),
-                                                              nodes.X, nodes.Y, cmat, tail, head, cost, sm); pd::count_launch();
+                                                              nodes.X, nodes.Y, cmat, tail, head, cost, sm, diag_cost(o)); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     if (mst > 0) k_max_cost32<<<grid_for(mst, 256), 256, 0, st>>>(cmat, mst, sm + 1); pd::count_launch();
     if (mx > 0) k_max_cost32<<<grid_for(mx, 256), 256, 0, st>>>(cost, mx, sm + 1); pd::count_launch();
@@ -1113,6 +1209,7 @@ pd_status ns_prepare_w1(Ctx* c, const pd_nodes& nodes, int64_t n_arcs, int64_t d
     w->nS = nS;
     w->nT = nT;
     w->nt = nt;
+    w->dc = diag_cost(o);
     return PD_OK;
 }
 
@@ -1124,7 +1221,7 @@ pd_status ns_finish_w1(Ctx* c, const WsTree& tr, int64_t s, const pd_network* me
         unsigned long long* sm = bufT<unsigned long long>(c, B_SMALL, 64);
         if (!sm) return PD_ENOMEM;
         PD_TRY_CUDA(c, cudaMemsetAsync(sm, 0, 4 * sizeof(unsigned long long), st));
-        k_certify_tree<<<grid_for(w.nt, 256), 256, 0, st>>>(d_res, w.S, w.T, w.nS, w.nT, tr, s, sm); pd::count_launch();
+        k_certify_tree<<<grid_for(w.nt, 256), 256, 0, st>>>(d_res, w.S, w.T, w.nS, w.nT, tr, s, w.dc, sm); pd::count_launch();
         PD_TRY_CUDA(c, cudaGetLastError());
         PD_TRY_CUDA(c, cudaMemcpyAsync(c->h_small, sm, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         PD_TRY_CUDA(c, cudaStreamSynchronize(st));

@@ -22,6 +22,7 @@ struct NSInst {
     const int32_t* head;
     const int32_t* cost;
     const int64_t* supply;
+    const int64_t* art;  // n or null: the artificial arc of node i costs big + art[i] (art[i] >= 0; null = 0)
     int64_t* pi;       // n + 1
     int32_t* parent;   // n + 1
     int32_t* pred;     // n + 1 (arc id; artificial arc of node i is m + i; m + n < 2^31)
@@ -36,7 +37,7 @@ struct NSInst {
     int64_t block;     // pricing block (arcs)
     int64_t big;       // cost of the artificial arcs (more than any path cost)
     int32_t smem_nodes; // 1: hot node arrays live in shared memory
-    int32_t minor;     // 1: between block pricings, the other warps' winners of the last block are re-priced (candidate list)
+    int32_t walk;      // shared-memory layout: longest half-cycle side followed by the two-lane walk (longer: the scan)
     int32_t init_tree;  // 1: pi, pred, parent, flow, up, ord, pos, size hold a strongly feasible start
     int32_t pad1;
     int64_t scanned;   // result: arcs priced
@@ -77,6 +78,7 @@ struct NSPrep {
 // The transportation form of one W1 network, prepared for the simplex.
 struct W1Prep {
     NSPrep ns;           // ns.ready false: solve the sparse network instead
+    DiagCost dc{1, 0, 0};  // creation / destruction costs of the diagonal node's routes
     const int32_t* S = nullptr;
     const int32_t* T = nullptr;
     int64_t nS = 0, nT = 0, nt = 0;
@@ -100,6 +102,26 @@ pd_status ns_finish_w1(Ctx* c, const WsTree& tr, int64_t s, const pd_network* me
                        const W1Prep& w, const NSInst* d_res, const NSInst& r, SolveStats* out, cudaStream_t st);
 __global__ void k_certify_tree(const NSInst* __restrict__ I, const int32_t* __restrict__ S,
                                const int32_t* __restrict__ T, int64_t nS, int64_t nT, WsTree tr, int64_t s,
-                               unsigned long long* __restrict__ out);
+                               DiagCost dc, unsigned long long* __restrict__ out);
+
+// One pair's certificate in a batched launch: its solved record, its
+// transportation lists and its WSPD tree.
+struct CertJob {
+    const NSInst* inst;  // device record (set by ns_run_wave from rec)
+    int64_t rec;         // index of the pair's record in the wave
+    const int32_t* S;
+    const int32_t* T;
+    int64_t nS, nT, s;
+    WsTree tree;
+    DiagCost dc;
+};
+// k_certify_tree for every job: blockIdx.y = job, out[2 job .. 2 job + 1].
+__global__ void k_certify_batch(const CertJob* __restrict__ jobs, unsigned long long* __restrict__ out);
+
+// One wave of a batch as a CUDA graph: upload of the records, the persistent
+// simplex over all of them, every pair's certificate, download of records and
+// certificate counts.  Captured once per configuration, replayed per wave.
+pd_status ns_run_wave(Ctx* c, const NSInst* h, int count, size_t smem, const CertJob* jobs, NSInst* r,
+                      unsigned long long* cert, cudaStream_t st);
 
 }  // namespace pd

@@ -45,9 +45,10 @@ constexpr float LB_INV_SQRT2 = 0.70710677f;  // below 1/sqrt(2)
 constexpr float LB_MARGIN = 128.0f;
 constexpr int32_t LB_EXACT = 1 << 23;
 
-// Distance of (x, y) to the diagonal, rounded down.
-PD_D float diag_lb(float2 p, float margin) {
-    return fmaxf(fabsf(p.y - p.x) * LB_INV_SQRT2 * LB_SHRINK - margin, 0.f);
+// Destruction / creation cost of a unit at (x, y), rounded down: kappa times
+// the distance to the diagonal plus tau (tau_lo: tau rounded down to float).
+PD_D float diag_lb(float2 p, float margin, int kappa, float tau_lo) {
+    return (kappa ? fmaxf(fabsf(p.y - p.x) * LB_INV_SQRT2 * LB_SHRINK - margin, 0.f) : 0.f) + tau_lo;
 }
 
 PD_D float dist_lb(float m2, float margin) { return fmaxf(sqrtf(m2) * LB_SHRINK - margin, 0.f); }
@@ -98,7 +99,8 @@ __global__ void k_db_compact(const float2* __restrict__ sxy, const int32_t* __re
 __global__ void __launch_bounds__(LB_THREADS) k_lb_db_side(const float2* __restrict__ dxy,
                                                            const int32_t* __restrict__ dcnt, int64_t T,
                                                            const float2* __restrict__ qxy, int64_t nq,
-                                                           float margin, double* __restrict__ val) {
+                                                           float margin, int kappa, float tau_lo,
+                                                           double* __restrict__ val) {
     __shared__ float2 sq[LB_TILE];
     const int64_t base = (int64_t)blockIdx.x * (LB_THREADS * LB_R);
     float2 p[LB_R];
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(LB_THREADS) k_lb_db_side(const float2* __restr
 #pragma unroll
     for (int r = 0; r < LB_R; r++) {
         int64_t v = base + r * LB_THREADS + threadIdx.x;
-        if (v < T) val[v] = (double)dcnt[v] * (double)fminf(dist_lb(m[r], margin), diag_lb(p[r], margin));
+        if (v < T) val[v] = (double)dcnt[v] * (double)fminf(dist_lb(m[r], margin), diag_lb(p[r], margin, kappa, tau_lo));
     }
 }
 
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(LB_THREADS) k_lb_query_side(const float2* __re
                                                               const int32_t* __restrict__ qcnt, int64_t nq,
                                                               const float2* __restrict__ dxy,
                                                               const int64_t* __restrict__ doff, float margin,
-                                                              double* __restrict__ part) {
+                                                              int kappa, float tau_lo, double* __restrict__ part) {
     __shared__ float2 sd[LB_TILE];
     __shared__ double red[LB_THREADS / 32];
     const int32_t i = blockIdx.y;
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(LB_THREADS) k_lb_query_side(const float2* __re
 #pragma unroll
     for (int r = 0; r < LB_R; r++) {
         int64_t u = base + r * LB_THREADS + threadIdx.x;
-        if (u < nq) val += (double)qcnt[u] * (double)fminf(dist_lb(m[r], margin), diag_lb(p[r], margin));
+        if (u < nq) val += (double)qcnt[u] * (double)fminf(dist_lb(m[r], margin), diag_lb(p[r], margin, kappa, tau_lo));
     }
     for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = val;
@@ -300,6 +302,7 @@ extern "C" pd_status pd_nn_search(pd_ctx* cx, pd_diagram query, double eps, cons
     if (opts) o = *opts;
     if (!(eps > 0.0) && o.s_override <= 0) return fail(c, PD_EINVAL, "eps must be > 0 (or set s_override)");
     if (o.solver == 1) return fail(c, PD_EINVAL, "the search runs the network simplex only");
+    PD_TRY(check_diag_cost(c, o));
     PD_TRY(check_diag(c, query));
     const int64_t n_db = (int64_t)c->db.size();
     if (n_db > 0 && query.dtype != c->db_dtype) return fail(c, PD_EINVAL, "query dtype differs from the database");
@@ -352,13 +355,17 @@ extern "C" pd_status pd_nn_search(pd_ctx* cx, pd_diagram query, double eps, cons
     const float margin = (qbig || c->db_big) ? LB_MARGIN : 0.f;
     const int64_t T = c->db_total;
     const int64_t per = (int64_t)LB_THREADS * LB_R;
+    // tau in float rounded down, so every destruction cost stays a lower bound
+    float tau_lo = (float)o.diag_tau;
+    if ((double)tau_lo > (double)o.diag_tau) tau_lo = nextafterf(tau_lo, 0.f);
     const int64_t gq = (nq + per - 1) / per;  // query tiles: partial sums per diagram
     double* val = bufT<double>(c, B_DB_VAL, std::max<int64_t>(T, gq * n_db));
     if (!val) return PD_ENOMEM;
     // sums in a fixed order (no floating-point atomics): the bounds are the same bits on every run
     if (T > 0) {
         k_lb_db_side<<<(unsigned)((T + per - 1) / per), LB_THREADS, 0, st>>>(
-            (const float2*)c->ptr[B_DB_XY], (const int32_t*)c->ptr[B_DB_CNT], T, qxy, nq, margin, val);
+            (const float2*)c->ptr[B_DB_XY], (const int32_t*)c->ptr[B_DB_CNT], T, qxy, nq, margin, o.diag_kappa,
+            tau_lo, val);
         pd::count_launch();
     }
     k_lb_segsum<<<(unsigned)n_db, LB_THREADS, 0, st>>>(val, (const int64_t*)c->ptr[B_DB_OFF], 0, LB);
@@ -369,7 +376,7 @@ extern "C" pd_status pd_nn_search(pd_ctx* cx, pd_diagram query, double eps, cons
             const int64_t ny = std::min<int64_t>(65535, n_db - y0);
             k_lb_query_side<<<dim3((unsigned)gq, (unsigned)ny), LB_THREADS, 0, st>>>(
                 qxy, qc, nq, (const float2*)c->ptr[B_DB_XY], (const int64_t*)c->ptr[B_DB_OFF] + y0, margin,
-                val + y0 * gq); pd::count_launch();
+                o.diag_kappa, tau_lo, val + y0 * gq); pd::count_launch();
         }
         k_lb_segsum<<<(unsigned)n_db, LB_THREADS, 0, st>>>(val, nullptr, gq, LA);
         pd::count_launch();
@@ -392,7 +399,8 @@ extern "C" pd_status pd_nn_search(pd_ctx* cx, pd_diagram query, double eps, cons
         lb[(size_t)i] = L > 0.0 ? (int64_t)std::floor(L) : 0;
         // WCD / 2 = |T_q - T_i| / (2 sqrt(2)): the persistence sums are exact
         // integers; the double quotient is shrunk to cover its rounding
-        const double dT = std::fabs((double)(qpers - c->db_pers[(size_t)i]));
+        // (only for persistence-diagram costs, kappa 1: W1 with tau >= 0 is at least the plain W1)
+        const double dT = o.diag_kappa == 1 ? std::fabs((double)(qpers - c->db_pers[(size_t)i])) : 0.0;
         const double W = dT / (2.0 * std::sqrt(2.0)) * (1.0 - ec) * (1.0 - 1e-9);
         lbw[(size_t)i] = W > 0.0 ? (int64_t)std::floor(W) : 0;
         if (lbw[(size_t)i] > lb[(size_t)i]) {

@@ -14,7 +14,8 @@
 // Each greedy assignment exhausts one end, so the arcs used form a forest;
 // each of its trees hangs from the root by the artificial arc of one of its
 // supply nodes (flow 0, pointing to the root), which makes the start strongly
-// feasible.  Potentials of the start follow from the tree.
+// feasible; its cost big + art[r0] places the component's potentials at the
+// predicted ones.  Potentials of the start follow from the tree.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -144,7 +145,7 @@ struct Arc {
 
 }  // namespace
 
-pd_status ns_warm_tree(Ctx* c, NSPrep* prep, const float* p, int64_t max_residual, bool* used, cudaStream_t st) {
+pd_status ns_warm_tree(Ctx* c, NSPrep* prep, const double* p, int64_t max_residual, bool* used, cudaStream_t st) {
     *used = false;
     NSInst& h = prep->h;
     if (!prep->ready) return PD_OK;
@@ -177,7 +178,9 @@ pd_status ns_warm_tree(Ctx* c, NSPrep* prep, const float* p, int64_t max_residua
     };
     float* dp = bufT<float>(c, B_WS_P, nt);
     if (!dp) return PD_ENOMEM;
-    PD_TRY_CUDA(c, cudaMemcpyAsync(dp, p, sizeof(float) * nt, cudaMemcpyHostToDevice, st));
+    std::vector<float> pf((size_t)nt);
+    for (int64_t v = 0; v < nt; v++) pf[(size_t)v] = (float)p[v];  // the device top-k ranks in float
+    PD_TRY_CUDA(c, cudaMemcpyAsync(dp, pf.data(), sizeof(float) * nt, cudaMemcpyHostToDevice, st));
     // rounds over the still unbalanced sources x sinks: each source keeps its
     // WS_K best sinks and each sink its WS_K best sources (device), then a
     // greedy pass over these candidates in ascending reduced cost (host); when
@@ -185,7 +188,7 @@ pd_status ns_warm_tree(Ctx* c, NSPrep* prep, const float* p, int64_t max_residua
     std::vector<int32_t> rs, rt, hr, hc;
     std::vector<int64_t> cand;
     std::vector<int32_t> cc;
-    std::vector<std::pair<float, int64_t>> order;
+    std::vector<std::pair<double, int64_t>> order;
     int64_t last_left = INT64_MAX;
     auto residual_lists = [&]() {
         rs.clear();
@@ -258,7 +261,7 @@ pd_status ns_warm_tree(Ctx* c, NSPrep* prep, const float* p, int64_t max_residua
         for (size_t q = 0; q < cand.size(); q++) {
             const int64_t a = cand[q];
             const int32_t t = (int32_t)(a / nT), hh = (int32_t)(nS + a % nT);
-            order[q] = {(float)cc[q] - p[t] + p[hh], (int64_t)q};
+            order[q] = {(double)cc[q] - p[t] + p[hh], (int64_t)q};
         }
         std::sort(order.begin(), order.end());
         bool moved = false;
@@ -298,8 +301,8 @@ pd_status ns_warm_tree(Ctx* c, NSPrep* prep, const float* p, int64_t max_residua
             take(cand[(size_t)q], (int32_t)(cand[(size_t)q] / nT), (int32_t)(nS + cand[(size_t)q] % nT), cc[(size_t)q]);
     }
     // the diagonal node's arcs, in ascending reduced cost, for what is left
-    std::vector<std::pair<float, int64_t>> dorder((size_t)mx);
-    for (int64_t x = 0; x < mx; x++) dorder[(size_t)x] = {(float)xc[(size_t)x] - p[xt[(size_t)x]] + p[xh[(size_t)x]], x};
+    std::vector<std::pair<double, int64_t>> dorder((size_t)mx);
+    for (int64_t x = 0; x < mx; x++) dorder[(size_t)x] = {(double)xc[(size_t)x] - p[xt[(size_t)x]] + p[xh[(size_t)x]], x};
     std::sort(dorder.begin(), dorder.end());
     for (auto& o : dorder) {
         const int64_t x = o.second;
@@ -323,6 +326,22 @@ pd_status ns_warm_tree(Ctx* c, NSPrep* prep, const float* p, int64_t max_residua
     ord.push_back((int32_t)nt);  // the root
     std::vector<int32_t> stack;
     std::vector<int32_t> comp_order;
+    // Every component hangs from the root by the artificial arc of its root
+    // node r0, whose cost big + art[r0] sets pi(r0): art[r0] = p(r0) - min p
+    // over the component roots keeps the predicted offsets between components
+    // (one common big would erase them).  The other supply nodes' artificial
+    // arcs cost 2 big - 1, far above their potentials, so they never enter.
+    // Every artificial cost is >= big: still a valid big-M start.
+    std::vector<int64_t> art((size_t)nt, 0);
+    double pmin = INFINITY;
+    for (int64_t v = 0; v < nt; v++)
+        if (sup[(size_t)v] >= 0 && p[v] < pmin) pmin = p[v];
+    auto offset = [&](int64_t v) -> int64_t {
+        const double o = p[v] - pmin;
+        return o <= 0.0 ? 0 : (o >= (double)(big - 1) ? big - 1 : (int64_t)std::llround(o));
+    };
+    for (int64_t v = 0; v < nt; v++)
+        if (sup[(size_t)v] >= 0) art[(size_t)v] = big - 1;
     for (int pass = 0; pass < 2; pass++) {
         // components are rooted at a supply node (first pass) or, for a node
         // of supply 0 on its own, at that node (second pass)
@@ -334,7 +353,8 @@ pd_status ns_warm_tree(Ctx* c, NSPrep* prep, const float* p, int64_t max_residua
             pred[(size_t)r0] = (int32_t)(m + r0);
             up[(size_t)r0] = 1;
             flow[(size_t)r0] = 0;
-            pi[(size_t)r0] = big;
+            art[(size_t)r0] = offset(r0);
+            pi[(size_t)r0] = big + art[(size_t)r0];
             stack.assign(1, (int32_t)r0);
             while (!stack.empty()) {  // preorder DFS
                 const int32_t v = stack.back();
@@ -378,7 +398,11 @@ pd_status ns_warm_tree(Ctx* c, NSPrep* prep, const float* p, int64_t max_residua
     PD_TRY_CUDA(c, cudaMemcpyAsync(h.ord, ord.data(), sizeof(int32_t) * N1, cudaMemcpyHostToDevice, st));
     PD_TRY_CUDA(c, cudaMemcpyAsync(h.pos, pos.data(), sizeof(int32_t) * N1, cudaMemcpyHostToDevice, st));
     PD_TRY_CUDA(c, cudaMemcpyAsync(h.size, size.data(), sizeof(int32_t) * N1, cudaMemcpyHostToDevice, st));
+    int64_t* dart = bufT<int64_t>(c, B_NS_ART, nt);
+    if (!dart) return PD_ENOMEM;
+    PD_TRY_CUDA(c, cudaMemcpyAsync(dart, art.data(), sizeof(int64_t) * nt, cudaMemcpyHostToDevice, st));
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    h.art = dart;
     h.init_tree = 1;
     *used = true;
     return PD_OK;

@@ -196,7 +196,7 @@ PD_D bool ws_arc_exists(int32_t a, int32_t b, int64_t N, const int32_t* __restri
 // the sparse network that the flow uses (rounding slack).
 __global__ void k_certify_tree(const NSInst* __restrict__ I, const int32_t* __restrict__ S,
                                const int32_t* __restrict__ T, int64_t nS, int64_t nT, WsTree tr, int64_t s,
-                               unsigned long long* __restrict__ out) {
+                               DiagCost dc, unsigned long long* __restrict__ out) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= I->n) return;
     int64_t a = I->pred[v], f = I->flow[v];
@@ -209,7 +209,7 @@ __global__ void k_certify_tree(const NSInst* __restrict__ I, const int32_t* __re
     int64_t i = a / nT, j = a - i * nT;
     int32_t u = S[i], w = T[j];
     int64_t d = cost_l2(tr.X[u], tr.Y[u], tr.X[w], tr.Y[w]);
-    int64_t g = cost_diag(tr.X[u], tr.Y[u]) + cost_diag(tr.X[w], tr.Y[w]);
+    int64_t g = cost_make(tr.X[u], tr.Y[u], dc) + cost_make(tr.X[w], tr.Y[w], dc);
     if (g <= d) {  // through the diagonal node: u -> diag -> w, both arcs exist
         atomicAdd(&out[1], (unsigned long long)(2 * f));
         return;
@@ -217,6 +217,33 @@ __global__ void k_certify_tree(const NSInst* __restrict__ I, const int32_t* __re
     const int32_t lo = u < w ? u : w, hi = u < w ? w : u;
     if (!ws_arc_exists(lo, hi, tr.N, tr.X, tr.Y, tr.bb, tr.rep, tr.left, tr.right, s)) atomicAdd(&out[0], 1ull);
     atomicAdd(&out[1], (unsigned long long)f);
+}
+
+__global__ void k_certify_batch(const CertJob* __restrict__ jobs, unsigned long long* __restrict__ out) {
+    const CertJob J = jobs[blockIdx.y];
+    const NSInst* I = J.inst;
+    unsigned long long* o = out + 2 * (int64_t)blockIdx.y;
+    const int64_t mst = J.nS * J.nT;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < I->n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = I->pred[v], f = I->flow[v];
+        if (a >= I->m || f <= 0) continue;
+        if (a >= mst) {
+            atomicAdd(&o[1], (unsigned long long)f);
+            continue;
+        }
+        const int64_t i = a / J.nT, j = a - i * J.nT;
+        const int32_t u = J.S[i], w = J.T[j];
+        const WsTree& tr = J.tree;
+        const int64_t d = cost_l2(tr.X[u], tr.Y[u], tr.X[w], tr.Y[w]);
+        const int64_t g = cost_make(tr.X[u], tr.Y[u], J.dc) + cost_make(tr.X[w], tr.Y[w], J.dc);
+        if (g <= d) {
+            atomicAdd(&o[1], (unsigned long long)(2 * f));
+            continue;
+        }
+        const int32_t lo = u < w ? u : w, hi = u < w ? w : u;
+        if (!ws_arc_exists(lo, hi, tr.N, tr.X, tr.Y, tr.bb, tr.rep, tr.left, tr.right, J.s)) atomicAdd(&o[0], 1ull);
+        atomicAdd(&o[1], (unsigned long long)f);
+    }
 }
 
 __global__ void k_frontier_init(int64_t N, const int32_t* __restrict__ left, const int32_t* __restrict__ right,
@@ -365,7 +392,7 @@ __global__ void k_row_ptr(const uint64_t* __restrict__ key, int64_t m, int hb, i
 
 __global__ void k_head_cost(const uint64_t* __restrict__ key, int64_t m, int hb, int64_t N,
                             const int32_t* __restrict__ X, const int32_t* __restrict__ Y, int32_t* __restrict__ head,
-                            int64_t* __restrict__ cost) {
+                            int64_t* __restrict__ cost, DiagCost dc) {
     int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= m) return;
     uint64_t k = key[a];
@@ -375,9 +402,9 @@ __global__ void k_head_cost(const uint64_t* __restrict__ key, int64_t m, int hb,
     if (t < N && h < N)
         c = cost_l2(X[t], Y[t], X[h], Y[h]);
     else if (t < N && h == N)
-        c = cost_diag(X[t], Y[t]);
+        c = cost_make(X[t], Y[t], dc);
     else if (t == N + 1 && h < N)
-        c = cost_diag(X[h], Y[h]);
+        c = cost_make(X[h], Y[h], dc);
     cost[a] = c;
 }
 
@@ -463,7 +490,7 @@ pd_status merge_diagonal(Ctx* c, const pd_network& net, int64_t N, pd_network* o
 
 pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* out, float* ms_tree,
                         float* ms_wspd, float* ms_csr, cudaStream_t st, bool count_only, WsTree* tree,
-                        const WsTree* given) {
+                        const WsTree* given, DiagCost dc) {
     int64_t N = nodes.n_nodes;
     if (N >= (int64_t(1) << 31) - 4) return fail(c, PD_ECAPACITY, "more than 2^31 - 4 condensed nodes");
     if (s < 1) return fail(c, PD_EINVAL, "WSPD parameter s must be >= 1");
@@ -611,7 +638,7 @@ pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* ou
     out->supply = bufT<int64_t>(c, B_SUPPLY, nrows);
     if (!out->row_ptr || !out->head || !out->cost || !out->supply) return PD_ENOMEM;
     k_row_ptr<<<grid_for(m, 256), 256, 0, st>>>(arcs, m, hb, nrows, out->row_ptr); pd::count_launch();
-    k_head_cost<<<grid_for(m, 256), 256, 0, st>>>(arcs, m, hb, N, nodes.X, nodes.Y, out->head, out->cost); pd::count_launch();
+    k_head_cost<<<grid_for(m, 256), 256, 0, st>>>(arcs, m, hb, N, nodes.X, nodes.Y, out->head, out->cost, dc); pd::count_launch();
     k_supply<<<grid_for(N + 2, 256), 256, 0, st>>>(N, nodes.cntA, nodes.cntB, FA, FB, out->supply); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     PD_TRY_CUDA(c, cudaEventRecord(ev[3], st));

@@ -37,8 +37,8 @@ class pd_opts(C.Structure):
                 ("seq_threshold", C.c_int32), ("solver", C.c_int32), ("ns_block", C.c_int64),
                 ("ns_transport", C.c_int32), ("ns_smem", C.c_int32), ("batch_slots", C.c_int32),
                 ("batch_threads", C.c_int32),
-                ("nn_prune", C.c_int32), ("warm_start", C.c_int32), ("ns_candidates", C.c_int32),
-                ("tree", C.c_int32)]
+                ("nn_prune", C.c_int32), ("warm_start", C.c_int32), ("ns_walk", C.c_int32),
+                ("tree", C.c_int32), ("diag_kappa", C.c_int32), ("diag_tau", C.c_int64)]
 
 
 class pd_nodes(C.Structure):
@@ -136,7 +136,8 @@ _lib.pd_nn_search.argtypes = [C.c_void_p, pd_diagram, C.c_double, C.POINTER(pd_o
                               C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_void_p]
 
 class pd_tune_result(C.Structure):
-    _fields_ = [("ns_block", C.c_int64), ("size_class", C.c_int32), ("candidates", C.c_int32), ("pairs", C.c_int32),
+    _fields_ = [("ns_block", C.c_int64), ("ns_walk", C.c_int32), ("size_class", C.c_int32), ("candidates", C.c_int32),
+                ("pairs", C.c_int32),
                 ("from_cache", C.c_int32), ("best_ms", C.c_float), ("default_ms", C.c_float)]
 
     def to_dict(self):

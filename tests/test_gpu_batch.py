@@ -124,19 +124,20 @@ def test_batch_fallback_paths(pd, ctx):
 
 
 def test_autotuned_block_keeps_every_optimum_and_is_cached(pd, ctx, tmp_path):
-    """pd_autotune times candidate pricing blocks on sample pairs; the chosen
-    block is used by later solves of the same size class, which keep their
-    optimum (the oracle's), and the cache file reproduces the choice without
-    timing in a fresh context."""
+    """pd_autotune times candidate (pricing block, walk limit) pairs on sample
+    pairs; the choice is used by later solves of the same size class, which
+    keep their optimum (the oracle's), and the cache file reproduces it
+    without timing in a fresh context."""
     A, B = synth.lowerstar_u8(20000, 1000), synth.lowerstar_u8(20000, 1001)
     cache = str(tmp_path / "tune.txt")
     t = pd.pd_autotune(ctx, [_cuda(A)], [_cuda(B)], 0.05, cache_path=cache)
-    assert t["pairs"] == 1 and t["from_cache"] == 0 and t["ns_block"] in (4096, 8192, 16384, 32768, 65536, 131072)
+    assert t["pairs"] == 1 and t["from_cache"] == 0 and t["ns_block"] in (4096, 8192, 16384, 32768)
+    assert t["ns_walk"] in (0, 8, 32) and t["candidates"] == 12
     assert t["best_ms"] > 0 and t["best_ms"] <= t["default_ms"] * 1.5
     r = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05)
     assert r["opt_quanta"] == oracle.w1_approx(A, B, "u8", eps=0.05)["opt"]
     line = open(cache).read().split()
-    assert int(line[-1]) == t["ns_block"] and int(line[-2]) == t["size_class"]
+    assert (int(line[-3]), int(line[-2]), int(line[-1])) == (t["size_class"], t["ns_block"], t["ns_walk"])
     c2 = pd.pd_create(0)
     try:
         t2 = pd.pd_autotune(c2, [_cuda(A)], [_cuda(B)], 0.05, cache_path=cache)

@@ -234,9 +234,10 @@ def test_mcf_random_networks_match_network_simplex(pd, ctx, seed):
     st, opt, flow, pot = oracle.mcf_arcs(len(net["supply"]), net["tails"], net["head"], net["cost"], net["supply"])
     assert st == 0
     dnet = {k: _cuda(v) for k, v in net.items() if k != "tails"}
-    for blk in (0, 1, 64):  # network simplex, different pricing blocks
-        got, stats = pd.pd_mcf_solve(ctx, dnet, pd.opts(ns_block=blk))
-        assert got == opt and stats["verified"] == 1 and stats["solve_method"] == 1
+    for blk in (0, 1, 64):  # network simplex, different pricing blocks, half-cycles walked or scanned
+        for walk in (0, 2, 512):
+            got, stats = pd.pd_mcf_solve(ctx, dnet, pd.opts(ns_block=blk, ns_walk=walk))
+            assert got == opt and stats["verified"] == 1 and stats["solve_method"] == 1
     for alpha in (2, 8, 16):  # cost scaling
         got, stats = pd.pd_mcf_solve(ctx, dnet, pd.opts(solver=1, alpha=alpha, verify=1))
         assert got == opt and stats["verified"] == 1
@@ -256,17 +257,19 @@ def test_mcf_on_w1_networks(pd, ctx, name):
 
 def _check_w1(pd, ctx, A, B, dt, eps, **kw):
     tree = kw.get("tree", "radix")
-    r = oracle.w1_approx(A, B, dt, eps=eps, tree=tree,
+    kappa, tau = kw.get("kappa", 1), kw.get("tau", 0)
+    r = oracle.w1_approx(A, B, dt, eps=eps, tree=tree, kappa=kappa, tau=tau,
                          **{k: v for k, v in kw.items() if k in ("k", "s_override", "perturb", "seed", "condense")})
     o = pd.opts(verify=1, s_override=kw.get("s_override", 0), perturb=int(kw.get("perturb", True)),
                 seed=kw.get("seed", 0), condense=int(kw.get("condense", True)),
-                coord_shift=kw.get("k", -1) if kw.get("k") is not None else -1, tree=int(tree == "split"))
+                coord_shift=kw.get("k", -1) if kw.get("k") is not None else -1, tree=int(tree == "split"),
+                diag_kappa=kappa, diag_tau=tau)
     g = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), eps, o)
     assert (g["rwmd_A"], g["rwmd_B"]) == (r["LA"], r["LB"])
     # the simplex straight on the sparse network must agree as well
     g2 = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), eps, pd.opts(
         s_override=o.s_override, perturb=o.perturb, seed=o.seed, condense=o.condense, coord_shift=o.coord_shift,
-        ns_transport=0, tree=o.tree))
+        ns_transport=0, tree=o.tree, diag_kappa=kappa, diag_tau=tau))
     assert g2["opt_quanta"] == r["opt"] and g2["solve_method"] == 1
     assert g["s"] == r["s"] and g["cell_quanta"] == r["G"] and g["shift_quanta"] == r["P"]
     assert g["delta"] == r["delta"]
@@ -291,7 +294,11 @@ def test_w1_approx_uniform2k(pd, ctx, eps):
 @pytest.mark.parametrize("eps", [0.1, 0.05, 0.01])
 def test_w1_approx_lowerstar_u8(pd, ctx, eps):
     A, B = synth.lowerstar_u8(20000, 1000), synth.lowerstar_u8(20000, 1001)
-    _check_w1(pd, ctx, A, B, "u8", eps)
+    g, r = _check_w1(pd, ctx, A, B, "u8", eps)
+    # other pricing blocks and walk limits reach the same optimum
+    for walk, blk in ((0, 0), (48, 32768), (512, 4096)):
+        assert pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), eps, pd.opts(ns_walk=walk, ns_block=blk))[
+            "opt_quanta"] == r["opt"]
 
 
 @pytest.mark.parametrize("name,eps", [("uniform2k", 0.1), ("lowerstar20k", 0.05), ("mixture5k", 0.1)])
@@ -301,6 +308,30 @@ def test_w1_approx_on_the_split_tree(pd, ctx, name, eps):
     A, B, dt = PAIRS[name]()
     g, r = _check_w1(pd, ctx, A, B, dt, eps, tree="split")
     assert g["n_arcs"] == int(r["net"]["row_ptr"][-1])
+
+
+@pytest.mark.parametrize("kappa,tau", [(0, 3000), (0, 200000), (1, 5000)])
+def test_w1_approx_unbalanced_transport(pd, ctx, kappa, tau):
+    """The Conclusion's unbalanced transport on R^2: ā and b̄ destroy and
+    create units at kappa * d_diag + tau quanta.  Every integer result equals
+    the oracle's (both solve paths, both trees), one-sided pairs give the sum
+    of the costs, and the nearest-neighbour bounds stay below the optimum."""
+    A, B = synth.uniform_exp(1500, 51), synth.uniform_exp(1200, 52)
+    g, r = _check_w1(pd, ctx, A, B, "f32", 0.1, kappa=kappa, tau=tau)
+    _check_w1(pd, ctx, A, B, "f32", 0.1, kappa=kappa, tau=tau, tree="split")
+    g = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.1, pd.opts(diag_kappa=kappa, diag_tau=tau, solver=1))
+    assert g["opt_quanta"] == r["opt"]
+    E = np.zeros((0, 2), np.float32)
+    ge, re_ = _check_w1(pd, ctx, A, E, "f32", 0.1, kappa=kappa, tau=tau, condense=False)
+    Ah = re_["Ahat"]
+    assert ge["opt_quanta"] == sum(int(c) * oracle.cmake(int(x), int(y), kappa, tau) for x, y, c in zip(*Ah))
+    db = [synth.uniform_exp(int(n), 60 + i) for i, n in enumerate((300, 900, 1500))]
+    pd.pd_db_build(ctx, [_cuda(d) for d in db])
+    nn = pd.pd_nn_search(ctx, _cuda(A), 0.1, pd.opts(diag_kappa=kappa, diag_tau=tau, nn_prune=0))
+    exp = [oracle.w1_approx(A, d, "f32", eps=0.1, kappa=kappa, tau=tau)["opt"] for d in db]
+    assert nn["opt"] == exp and all(lb <= o for lb, o in zip(nn["lb"], exp))
+    with pytest.raises(pd.PDError):
+        pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.1, pd.opts(diag_kappa=2))
 
 
 def test_w1_approx_edge_cases(pd, ctx):

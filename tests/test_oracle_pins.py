@@ -786,3 +786,80 @@ def test_wcd_bound_definition_closed_form_and_below_w1(orc):
     X, Y, c = np.array([1, 4]), np.array([5, 9]), np.array([3, 2])
     pts = np.array([[1, 5]] * 3 + [[4, 9]] * 2, float)
     assert orc.wcd((X, Y, c), (X[:1], Y[:1] + 1, c[:1])) == pytest.approx(orc.wcd(pts, np.array([[1, 6]] * 3, float)))
+
+
+# --------------------------------------------------------------------------
+# unbalanced transport (Conclusion): diagonal arcs reassigned to creation /
+# destruction costs kappa * d_diag + tau
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kappa,tau", [(0, 0.3), (1, 0.25), (0, 5.0)])
+def test_unbalanced_exact_matches_the_augmented_assignment(orc, kappa, tau):
+    """Exact FP64 optimum with creation / destruction cost kappa * d_diag + tau
+    equals the optimal assignment of the augmented bipartite graph (A + B's
+    creation slots against B + A's destruction slots), by scipy's Hungarian."""
+    rng = np.random.default_rng(700 + int(10 * tau))
+    for trial in range(5):
+        A = synth.uniform_exp(int(rng.integers(1, 40)), 900 + trial).astype(np.float64)
+        B = synth.uniform_exp(int(rng.integers(1, 40)), 950 + trial).astype(np.float64)
+        A, B = A[A[:, 0] != A[:, 1]], B[B[:, 0] != B[:, 1]]
+        dc = lambda a: kappa * abs(a[1] - a[0]) / SQ2 + tau
+        ref = _augmented(A, B, lambda a, b: math.hypot(a[0] - b[0], a[1] - b[1]), dc)
+        got = orc.w1_exact(A, B, kappa=kappa, tau=tau)
+        assert abs(got - ref) <= 1e-9 * max(1.0, ref)
+
+
+def test_unbalanced_closed_forms_and_balanced_limit(orc):
+    """One side empty: every unit is destroyed (created), the sum of the
+    costs.  kappa 0 with twice tau above every distance between equal-size
+    sets: nothing is destroyed, the optimum is the balanced assignment (EMD)."""
+    A = synth.uniform_exp(60, 31).astype(np.float64)
+    A = A[A[:, 0] != A[:, 1]]
+    E = np.zeros((0, 2))
+    for kappa, tau in ((0, 0.5), (1, 0.125)):
+        closed = sum(kappa * abs(d - b) / SQ2 + tau for b, d in A)
+        assert abs(orc.w1_exact(A, E, kappa=kappa, tau=tau) - closed) <= 1e-9 * closed
+        assert abs(orc.w1_exact(E, A, kappa=kappa, tau=tau) - closed) <= 1e-9 * closed
+    B = synth.uniform_exp(len(A), 32).astype(np.float64)
+    B = B[B[:, 0] != B[:, 1]][: len(A)]
+    A = A[: len(B)]
+    D = np.hypot(A[:, None, 0] - B[None, :, 0], A[:, None, 1] - B[None, :, 1])
+    r, c = linear_sum_assignment(D)
+    assert abs(orc.w1_exact(A, B, kappa=0, tau=float(D.max())) - D[r, c].sum()) <= 1e-9 * D[r, c].sum()
+    # integer form: single points, min(l2, cost(a) + cost(b))
+    for (x1, y1, x2, y2) in ((0, 10, 3, 14), (0, 1000, 900, 1000), (5, 5000, 7, 5001)):
+        for kappa, tau in ((0, 40), (1, 3), (0, 0)):
+            P = (np.array([x1], np.int32), np.array([y1], np.int32), np.array([1], np.int64))
+            Q = (np.array([x2], np.int32), np.array([y2], np.int32), np.array([1], np.int64))
+            exp = min(orc.cost(x1, y1, x2, y2), orc.cmake(x1, y1, kappa, tau) + orc.cmake(x2, y2, kappa, tau))
+            assert orc.dense_opt_int(P, Q, kappa=kappa, tau=tau) == exp
+            assert orc.cmake(x1, y1, kappa, tau) == kappa * orc.cdiag(x1, y1) + tau
+
+
+@pytest.mark.parametrize("kappa,tau", [(0, 20000), (1, 4000)])
+def test_unbalanced_pipeline_bounds(orc, kappa, tau):
+    """The pipeline with creation / destruction costs: RWMD <= OPT(G_0) on
+    the 0-condensed nodes, the dense limit (s large, no condensation) equals
+    the dense integer optimum, and the (1 +- eps) band holds against the exact
+    FP64 optimum of the same costs."""
+    A, B = _small_pair(300, 410)
+    q = 2.0 ** -16
+    r = orc.w1_approx(A, B, "f32", eps=0.1, k=16, kappa=kappa, tau=tau)
+    opt0 = orc.dense_opt_int(r["Ahat"], r["Bhat"], kappa=kappa, tau=tau)
+    assert r["rwmd"] <= opt0
+    rd = orc.w1_approx(A, B, "f32", k=16, s_override=10**7, condense=False, kappa=kappa, tau=tau)
+    assert rd["opt"] == opt0
+    w = orc.w1_exact(A.astype(np.float64), B.astype(np.float64), kappa=kappa, tau=tau * q)
+    qerr = (r["FA"] + r["FB"]) * q
+    assert (1 - 0.1) * w - qerr <= r["w1"] <= (1 + 0.1) * w + r["slack"] * q + qerr
+    # RWMD against brute force over the 0-condensed nodes, destruction option included
+    Ah, Bh = r["Ahat"], r["Bhat"]
+    def side(P, Q):
+        tot = 0
+        for x, y, c in zip(*P):
+            best = orc.cmake(int(x), int(y), kappa, tau)
+            for x2, y2 in zip(Q[0], Q[1]):
+                best = min(best, orc.cost(int(x), int(y), int(x2), int(y2)))
+            tot += int(c) * best
+        return tot
+    assert (r["LA"], r["LB"]) == (side(Ah, Bh), side(Bh, Ah))
