@@ -5,11 +5,19 @@ lower-star points each (eps = 0.05, WSPD parameter s = 327), in pairs/s.
 One step = one pd_w1_approx_batch call over a batch of distinct pairs (by
 default twice as many pairs as the GPU has SMs): per pair quantise,
 0-condense, RWMD, delta-condense, radix tree, WSPD (arcs counted), diagonal
-arcs, transportation instance; one persistent network simplex launch for the
-whole batch; per pair the optimality certificate against the WSPD.  The plain one-pair path
-(pd_w1_approx, one pair after the other) is timed beside it.
+arcs, transportation instance; then one CUDA graph for the whole batch (the
+persistent network simplex over all pairs and every pair's optimality
+certificate against its WSPD).  The simplex's pricing block and walk limit
+come from the library's autotuner, run on two pool pairs before timing.
+Beside it: the plain one-pair path (pd_w1_approx), the warm starts (coarse
+solve, learned correction, exact potentials) on unseen pairs, the end-to-end
+batch from pinned host buffers, the other configurations (2k uniform, 100k
+lower-star at eps 0.1 and 0.01, continuous mixtures up to their sizes at 1M
+points, nearest-neighbour queries) and the CPU oracle on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --sweep              # the Gaussian empirical-complexity sweep alone
+  python bench.py --stages-only N      # the sparsification stages of one N + N mixture pair alone
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle (the
 plain C restatement of the method) on the same workload, one pair per host

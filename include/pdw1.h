@@ -104,8 +104,9 @@ typedef struct {
                                distance to the diagonal), i.e. the greedy by the saving
                                d(u) + d(v) - c(u, v) of pairing u with v (no network);
                                4 = start from the potentials of an exact solve of the same pair
-                               condensed onto a coarser lattice (cell max(2 G, node box / 64)), each
-                               node taking its nearest coarse node's */
+                               condensed onto a coarser lattice (cell max(2 G, node box / warm_cells)),
+                               mapped to the fine nodes by the coarse optimum's c-transforms
+                               (the midpoint of the upper and lower envelope) */
     int32_t ns_walk;        /* network simplex, trees in shared memory: the two half-cycles of a pivot are
                                followed up the tree by two lanes when neither side is longer than this
                                many nodes, else found by a scan of the whole preorder by the CTA
@@ -118,6 +119,8 @@ typedef struct {
                                diag_kappa * d_diag(p) + diag_tau quanta; 1 and 0 (default) give W1
                                between persistence diagrams, 0 a constant cost diag_tau */
     int64_t diag_tau;       /* >= 0 quanta, < 2^30 */
+    int32_t warm_cells;     /* warm_start 1 and 4: coarse cells along the longer side of the nodes'
+                               bounding box (0 = 64; at most 4096) */
 } pd_opts;
 
 void pd_opts_default(pd_opts* opts);
@@ -181,6 +184,9 @@ typedef struct {
     int32_t warm_used;      /* 1 if the simplex started from a warm-start tree */
     float stage_ms[8];      /* device time of quantize+0-condense, RWMD, delta-condense, tree, WSPD, CSR;
                                host wall time of the solve (incl. certificate) and of the whole call */
+    float warm_ms[2];       /* warm start, host wall time: the potentials (coarse solve and mapping,
+                               network inference), then the start tree; 0 for a cold start */
+    int64_t warm_pivots;    /* pivots of the coarse solve behind the warm start (0 if none) */
 } pd_result;
 
 /*

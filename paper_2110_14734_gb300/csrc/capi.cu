@@ -174,6 +174,7 @@ extern "C" void pd_opts_default(pd_opts* o) {
     o->ns_walk = -1;
     o->diag_kappa = 1;
     o->diag_tau = 0;
+    o->warm_cells = 0;
 }
 
 namespace pd {
@@ -554,14 +555,30 @@ static void fill_result(const Front& f, const SolveStats& ss, pd_result* out) {
 // at once when there are at most this many (before that, rounds of top-k).
 constexpr int64_t WARM_MAX_RESIDUAL = int64_t(1) << 18;
 
-// Warm start of a prepared transportation instance (opts.warm_start): from
-// the network's prediction (1) or from the exact potentials of a cold solve
-// in `c`'s instance record (2).  *used: the start tree was installed.
-static pd_status warm_start(Ctx* c, const Front& f, W1Prep* w, const pd_opts& o, bool* used, cudaStream_t st) {
+static float elapsed_ms(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// What a warm start cost (pd_result.warm_ms, warm_pivots).
+struct WarmStats {
+    float ms[2] = {0.f, 0.f};  // potentials, start tree (host wall time)
+    int64_t coarse_pivots = 0;
+};
+
+// Warm start of a prepared transportation instance (opts.warm_start): the
+// potentials from a coarse solve (4), corrected by the network (1), from the
+// exact potentials of a cold solve (2) or from the distances to the diagonal
+// (3), then the start tree.  `c` does the work; the instance's buffers
+// belong to `tc` (the same context on the one-pair path, the pair's slot in a
+// batch).  *used: the start tree was installed.
+static pd_status warm_start(Ctx* c, Ctx* tc, const Front& f, W1Prep* w, const pd_opts& o, bool* used,
+                            WarmStats* ws, cudaStream_t st) {
     *used = false;
     if (!w->ns.ready || o.warm_start == 0) return PD_OK;
+    const auto t0 = std::chrono::steady_clock::now();
     std::vector<float> pf;
     std::vector<double> p;
+    c->last_coarse_pivots = 0;
     if (o.warm_start == 1) {  // the coarse solve's potentials corrected by the network
         PD_TRY(ws_coarse_potentials(c, f, *w, o, &p, st));
         PD_TRY(ws_predict(c, f.nodes, *w, &pf, st));
@@ -588,11 +605,12 @@ static pd_status warm_start(Ctx* c, const Front& f, W1Prep* w, const pd_opts& o,
         return fail(c, PD_EINVAL, "warm_start must be 0 .. 4");
     }
     if (p.empty()) p.assign(pf.begin(), pf.end());
-    return ns_warm_tree(c, &w->ns, p.data(), WARM_MAX_RESIDUAL, used, st);
-}
-
-static float elapsed_ms(std::chrono::steady_clock::time_point t0) {
-    return std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    ws->coarse_pivots = c->last_coarse_pivots;
+    ws->ms[0] = elapsed_ms(t0);
+    const auto t1 = std::chrono::steady_clock::now();
+    PD_TRY(ns_warm_tree(tc, &w->ns, p.data(), WARM_MAX_RESIDUAL, used, st));
+    ws->ms[1] = elapsed_ms(t1);
+    return PD_OK;
 }
 
 extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double eps, const pd_opts* opts,
@@ -609,6 +627,7 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
     const auto t0 = std::chrono::steady_clock::now();
     Front f;
     bool warm_used = false;
+    WarmStats wst;
     const bool transport = o.solver != 1 && o.ns_transport != 0;
     PD_TRY(front_half(c, A, B, eps, o, &f, st, transport));
     const auto t1 = std::chrono::steady_clock::now();
@@ -620,7 +639,7 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
         if (transport) PD_TRY(ns_prepare_w1(c, f.nodes, f.net.n_arcs, f.h.FB - f.h.FA, o, &w, st));
         if (w.ns.ready) {
             bool used = false;
-            PD_TRY(warm_start(c, f, &w, o, &used, st));
+            PD_TRY(warm_start(c, c, f, &w, o, &used, &wst, st));
             warm_used = used;
             NSInst* d = bufT<NSInst>(c, B_NS_INST, 1);
             if (!d) return PD_ENOMEM;
@@ -655,6 +674,9 @@ extern "C" pd_status pd_w1_approx(pd_ctx* c, pd_diagram A, pd_diagram B, double 
     out->kernel_launches = launch_count_ref() - launches0;
     out->ns_kernel_ms = c->last_ns_ms;
     out->warm_used = warm_used ? 1 : 0;
+    out->warm_ms[0] = wst.ms[0];
+    out->warm_ms[1] = wst.ms[1];
+    out->warm_pivots = wst.coarse_pivots;
     return PD_OK;
 }
 
@@ -688,6 +710,7 @@ struct BatchPair {
     WsTree tree{};      // slot copies of the node coordinates and the WSPD tree
     bool done = false;  // solved during preprocessing (no transportation form)
     bool warm = false;  // starts from a warm-start tree
+    WarmStats wst;
     SolveStats ss;
     float front_ms = 0.f, solve_ms = 0.f;
     long long launches = 0;
@@ -745,22 +768,9 @@ static pd_status batch_prepare(Ctx* work, Ctx* slot, const pd_diagram& A, const 
     if (transport)
         PD_TRY(ns_prepare_w1(slot, bp->f.nodes, bp->f.net.n_arcs, bp->f.h.FB - bp->f.h.FA, o, &bp->w, st));
     if (bp->w.ns.ready) {
-        if (o.warm_start == 1) {  // the coarse solve's potentials corrected by the network
-            std::vector<float> pf;
-            std::vector<double> p;
-            PD_TRY(ws_coarse_potentials(work, bp->f, bp->w, o, &p, st));
-            PD_TRY(ws_predict(work, bp->f.nodes, bp->w, &pf, st));
-            if (p.empty()) p.assign(pf.begin(), pf.end());
-            else
-                for (size_t v = 0; v < p.size() && v < pf.size(); v++) p[v] += pf[v];
-            PD_TRY(ns_warm_tree(slot, &bp->w.ns, p.data(), WARM_MAX_RESIDUAL, &bp->warm, st));
-        } else if (o.warm_start == 4) {
-            std::vector<double> p;
-            PD_TRY(ws_coarse_potentials(work, bp->f, bp->w, o, &p, st));
-            if (!p.empty()) PD_TRY(ns_warm_tree(slot, &bp->w.ns, p.data(), WARM_MAX_RESIDUAL, &bp->warm, st));
-        } else if (o.warm_start != 0) {
+        if (o.warm_start != 0 && o.warm_start != 1 && o.warm_start != 4)
             return fail(work, PD_EINVAL, "the batched solve takes warm_start 0, 1 or 4");
-        }
+        PD_TRY(warm_start(work, slot, bp->f, &bp->w, o, &bp->warm, &bp->wst, st));
         PD_TRY(persist_for_certificate(slot, bp->f, bp, st));
     } else {
         const auto t1 = std::chrono::steady_clock::now();
@@ -948,6 +958,9 @@ pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t 
             res.kernel_launches = p.launches;
             res.ns_kernel_ms = (p.done ? 0.f : wave_ns) + sl->last_ns_ms;
             res.warm_used = p.warm ? 1 : 0;
+            res.warm_ms[0] = p.wst.ms[0];
+            res.warm_ms[1] = p.wst.ms[1];
+            res.warm_pivots = p.wst.coarse_pivots;
         }
     }
     cudaEventDestroy(ready);

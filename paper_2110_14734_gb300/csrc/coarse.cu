@@ -6,8 +6,8 @@
 // cell of G_c >= 2 G) gives that function at the coarse nodes, and the fine
 // nodes take the c-transforms of the coarse optimum (k_ctransform_potential);
 // the error per node is of the order of the coarse cell.  The coarse problem
-// has a few thousand nodes at most (G_c >= the node box / 64), so its simplex
-// is short; its buffers belong to a helper context, so the fine instance, its
+// has a few thousand nodes at most (G_c >= the node box / warm_cells, 64 by
+// default), so its simplex is short; its buffers belong to a helper context, so the fine instance, its
 // nodes and its WSPD tree stay in place.
 #include <math.h>
 #include <string.h>
@@ -22,7 +22,7 @@
 
 namespace pd {
 
-constexpr int64_t COARSE_CELLS = 64;  // coarse cells along the node box's longer side
+constexpr int64_t COARSE_CELLS = 64;  // default coarse cells along the node box's longer side
 
 __global__ void k_node_box(const int32_t* __restrict__ X, const int32_t* __restrict__ Y, int64_t n,
                            int* __restrict__ box) {
@@ -34,15 +34,17 @@ __global__ void k_node_box(const int32_t* __restrict__ X, const int32_t* __restr
     atomicMax(&box[3], Y[i]);
 }
 
-// Fine potentials from the coarse optimum by its c-transforms: a fine source
-// u takes the largest potential the coarse sinks allow, min over coarse sinks
-// w of pi(w) + c(u, w), a fine sink v the smallest the coarse sources allow,
-// max over coarse sources w of pi(w) - c(w, v), with c the transportation
-// cost min(l2, c_make(u) + c_make(w)) and the coarse diagonal node among the
-// coarse sinks (sources) when it is one.  Unlike copying the nearest coarse
-// node's potential, this respects the dual constraints of every coarse node,
-// whatever offsets the coarse tree's components carry.  The fine diagonal
-// node takes the coarse diagonal node's potential.  cpi: the coarse
+// Fine potentials from the coarse optimum by its c-transforms: the largest
+// potential the coarse sinks allow a node at the fine position, min over
+// coarse sinks w of pi(w) + c(u, w), and the smallest the coarse sources
+// allow, max over coarse sources w of pi(w) - c(w, u), with c the
+// transportation cost min(l2, c_make(u) + c_make(w)) and the coarse diagonal
+// node among the coarse sinks (sources) when it is one; the fine node takes
+// the midpoint of the two envelopes (the Lipschitz potential lies between
+// them).  Unlike copying the nearest coarse node's potential, this respects
+// the dual constraints of every coarse node, whatever offsets the coarse
+// tree's components carry.  The fine diagonal node takes the coarse diagonal
+// node's potential.  cpi: the coarse
 // instance's potentials (its sources, sinks, diagonal node); dsup: supply of
 // the diagonal node (|B| - |A|).
 __global__ void k_ctransform_potential(const int32_t* __restrict__ S, const int32_t* __restrict__ T, int64_t nS,
@@ -62,26 +64,30 @@ __global__ void k_ctransform_potential(const int32_t* __restrict__ S, const int3
     const int32_t u = src ? S[v] : T[v - nS];
     const int32_t x = X[u], y = Y[u];
     const int64_t du = cost_make(x, y, dc);
-    int64_t best = src ? INT64_MAX : INT64_MIN;
-    const int64_t q0 = src ? cnS : 0, q1 = src ? cnS + cnT : cnS;  // the other side's coarse nodes
-    for (int64_t q = q0; q < q1; q++) {
+    // upper envelope over the coarse sinks, lower envelope over the coarse sources
+    int64_t up = INT64_MAX, lo = INT64_MIN;
+    for (int64_t q = 0; q < cnS + cnT; q++) {
         const int32_t w = q < cnS ? cS[q] : cT[q - cnS];
         const int64_t l2 = cost_l2(x, y, cX[w], cY[w]);
         const int64_t g = du + cost_make(cX[w], cY[w], dc);
         const int64_t c = l2 < g ? l2 : g;
-        if (src) {
+        if (q >= cnS) {
             const int64_t t = cpi[q] + c;
-            best = t < best ? t : best;
+            up = t < up ? t : up;
         } else {
             const int64_t t = cpi[q] - c;
-            best = t > best ? t : best;
+            lo = t > lo ? t : lo;
         }
     }
     // the diagonal node's arcs: sources -> D when D demands (dsup < 0), D -> sinks when it supplies
-    if (src && dsup < 0) best = min(best, cpi[D] + du);
-    if (!src && dsup > 0) best = max(best, cpi[D] - du);
-    if (best == INT64_MAX || best == INT64_MIN) best = cpi[D];  // no node on the other side
-    p[v] = (double)best;
+    if (dsup < 0) up = min(up, cpi[D] + du);
+    if (dsup > 0) lo = max(lo, cpi[D] - du);
+    double best;
+    if (up == INT64_MAX && lo == INT64_MIN) best = (double)cpi[D];
+    else if (up == INT64_MAX) best = (double)lo;
+    else if (lo == INT64_MIN) best = (double)up;
+    else best = 0.5 * ((double)up + (double)lo);
+    p[v] = best;
 }
 
 static Ctx* coarse_ctx(Ctx* c) {
@@ -95,7 +101,9 @@ static Ctx* coarse_ctx(Ctx* c) {
 pd_status ws_coarse_potentials(Ctx* c, const Front& f, const W1Prep& w, const pd_opts& o, std::vector<double>* p,
                                cudaStream_t st) {
     p->clear();
+    if (o.warm_cells < 0 || o.warm_cells > 4096) return fail(c, PD_EINVAL, "warm_cells must be 0 .. 4096");
     if (!w.ns.ready || f.nodes.n_nodes == 0) return PD_OK;
+    const int64_t cells = o.warm_cells > 0 ? o.warm_cells : COARSE_CELLS;
     int* box = bufT<int>(c, B_CO_BOX, 4);
     if (!box) return PD_ENOMEM;
     const int init[4] = {INT32_MAX, INT32_MIN, INT32_MAX, INT32_MIN};
@@ -108,7 +116,7 @@ pd_status ws_coarse_potentials(Ctx* c, const Front& f, const W1Prep& w, const pd
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     const int64_t side = std::max<int64_t>((int64_t)hb[1] - hb[0], (int64_t)hb[3] - hb[2]);
     const int64_t Gc = std::min<int64_t>(int64_t(1) << 28,
-                                         std::max<int64_t>(2 * f.G, (side + COARSE_CELLS - 1) / COARSE_CELLS));
+                                         std::max<int64_t>(2 * f.G, (side + cells - 1) / cells));
     Ctx* cc = coarse_ctx(c);
     if (!cc) return fail(c, PD_ENOMEM, "cannot create the coarse solve's context");
     cc->err.clear();

@@ -137,7 +137,8 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
         T.set_parent(i, root);
         T.pred[i] = (int32_t)(I.m + i);
         T.set_fu(i, (int32_t)(s >= 0 ? s : -s), s >= 0);
-        T.pi[i] = s >= 0 ? big : -big;  // reduced cost of the artificial arc is 0
+        const int64_t ca = I.art ? big + I.art[i] : big;  // the artificial arc's cost
+        T.pi[i] = s >= 0 ? ca : -ca;                      // its reduced cost is 0
         T.od[1 + i] = (IX)i;
         T.ps[i] = (IX)(1 + i);
         T.sz[i] = (IX)1;

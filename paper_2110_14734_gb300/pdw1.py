@@ -38,7 +38,8 @@ class pd_opts(C.Structure):
                 ("ns_transport", C.c_int32), ("ns_smem", C.c_int32), ("batch_slots", C.c_int32),
                 ("batch_threads", C.c_int32),
                 ("nn_prune", C.c_int32), ("warm_start", C.c_int32), ("ns_walk", C.c_int32),
-                ("tree", C.c_int32), ("diag_kappa", C.c_int32), ("diag_tau", C.c_int64)]
+                ("tree", C.c_int32), ("diag_kappa", C.c_int32), ("diag_tau", C.c_int64),
+                ("warm_cells", C.c_int32)]
 
 
 class pd_nodes(C.Structure):
@@ -62,11 +63,13 @@ class pd_result(C.Structure):
                 ("pivots", C.c_int64), ("degenerate", C.c_int64), ("arcs_priced", C.c_int64),
                 ("solve_method", C.c_int32),
                 ("cert_failures", C.c_int32), ("kernel_launches", C.c_int64), ("ns_kernel_ms", C.c_float),
-                ("warm_used", C.c_int32), ("stage_ms", C.c_float * 8)]
+                ("warm_used", C.c_int32), ("stage_ms", C.c_float * 8), ("warm_ms", C.c_float * 2),
+                ("warm_pivots", C.c_int64)]
 
     def to_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "stage_ms"}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("stage_ms", "warm_ms")}
         d["stage_ms"] = list(self.stage_ms)
+        d["warm_ms"] = list(self.warm_ms)
         return d
 
 

@@ -142,3 +142,15 @@ def test_coarse_solve_start_keeps_the_optimum(pd, ctx, name):
     print("%s pivots cold %d coarse start %d" % (name, cold["pivots"], warm["pivots"]))
     wb = pd.pd_w1_approx_batch(ctx, [_cuda(A), _cuda(B)], [_cuda(B), _cuda(A)], eps, pd.opts(warm_start=4))
     assert [r["opt_quanta"] for r in wb] == [exp, exp]
+
+
+@pytest.mark.parametrize("mode,cells", [(4, 8), (4, 256)])
+def test_coarse_start_cells_keep_the_optimum(pd, ctx, mode, cells):
+    """warm_cells sets the coarse lattice of warm_start = 4 (node box / cells);
+    any level gives the same optimum, and a value out of range is refused."""
+    A, B = synth.lowerstar_u8(20000, 1002), synth.lowerstar_u8(20000, 1003)
+    exp = oracle.w1_approx(A, B, "u8", eps=0.05)["opt"]
+    warm = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05, pd.opts(warm_start=mode, warm_cells=cells))
+    assert warm["warm_used"] == 1 and warm["verified"] == 1 and warm["opt_quanta"] == exp
+    with pytest.raises(pd.PDError):
+        pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05, pd.opts(warm_start=4, warm_cells=5000))
