@@ -3,6 +3,9 @@
 #include "internal.h"
 #include "prims.cuh"
 
+#include <algorithm>
+#include <cmath>
+
 namespace pd {
 
 // small-scalar slots in B_SMALL (int64)
@@ -255,9 +258,260 @@ __global__ void k_rwmd_sum(const int32_t* __restrict__ X, const int32_t* __restr
     }
 }
 
+// ---- the same minima through a uniform grid over each side ----------------
+// Large sides make the all-pairs scan quadratic (about 10^12 distance
+// evaluations at a million nodes a side).  Each side's nodes are bucketed
+// into a grid of about two nodes a cell (a counting sort by cell), and every
+// node of the other side searches square rings of cells around its own cell.
+// After ring K every node not yet seen lies beyond one of the square's sides
+// that are not the grid's border, so its distance is at least LB, the
+// distance from the query to the nearest such side.  The search stops when
+// LB^2 >= the best squared distance found (the minimum is exact), or when
+// LB >= the query's diagonal cost c_make: every unseen node then costs at
+// least c_make, the relaxed flow takes min(c(u, nearest), c_make) either way,
+// and the stored value min(best, c_make^2) gives the same term.  A query that
+// has not stopped after RW_KMAX rings (a far outlier) keeps its best as an
+// upper bound and is finished by the all-pairs scan over the other side.
+
+constexpr int RW_KMAX = 24;
+constexpr int64_t RW_GRID_MIN = int64_t(1) << 28;  // nA * nB from which the grid is used
+
+struct RwGrid {
+    int64_t x0, y0, h;  // origin and cell side (quanta)
+    int32_t gw, gh;     // cells per axis
+    int64_t base;       // first cell of this grid in the shared cell arrays
+};
+
+__global__ void k_rw_box_init(int* box) {
+    if (threadIdx.x < 8) box[threadIdx.x] = (threadIdx.x & 1) ? INT32_MIN : INT32_MAX;
+}
+
+// Bounding box of each side: box[4 s ..] = xmin, xmax, ymin, ymax of side s.
+__global__ void k_rw_box(const int32_t* __restrict__ X, const int32_t* __restrict__ Y, int64_t nA, int64_t n,
+                         int* __restrict__ box) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int v[8];  // per side: -xmin, xmax, -ymin, ymax (maxima of all four)
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = INT32_MIN;
+    if (i < n) {
+        const int s = i < nA ? 0 : 4;
+        v[s + 0] = -X[i];  // coordinates are above -2^30: negation is exact
+        v[s + 1] = X[i];
+        v[s + 2] = -Y[i];
+        v[s + 3] = Y[i];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+        for (int o = 16; o > 0; o >>= 1) v[k] = max(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+    if ((threadIdx.x & 31) == 0)
+        for (int s = 0; s < 8; s += 4)
+            if (v[s + 1] != INT32_MIN) {
+                atomicMin(&box[s + 0], -v[s + 0]);
+                atomicMax(&box[s + 1], v[s + 1]);
+                atomicMin(&box[s + 2], -v[s + 2]);
+                atomicMax(&box[s + 3], v[s + 3]);
+            }
+}
+
+PD_D int32_t rw_cell_axis(int64_t v, int64_t o, int64_t h, int32_t g) {
+    if (v < o) return 0;
+    const int64_t c = (v - o) / h;
+    return c >= g ? g - 1 : (int32_t)c;
+}
+
+// Node i of side s goes into grid s (its cell's count).
+__global__ void k_rw_hist(const int32_t* __restrict__ X, const int32_t* __restrict__ Y, int64_t nA, int64_t n,
+                          RwGrid g0, RwGrid g1, unsigned long long* __restrict__ cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const RwGrid& g = i < nA ? g0 : g1;
+    const int64_t c = g.base + (int64_t)rw_cell_axis(Y[i], g.y0, g.h, g.gh) * g.gw + rw_cell_axis(X[i], g.x0, g.h, g.gw);
+    atomicAdd(&cnt[c], 1ull);
+}
+
+// Nodes placed by cell (order inside a cell is arbitrary: only minima are read).
+__global__ void k_rw_scatter(const int32_t* __restrict__ X, const int32_t* __restrict__ Y, int64_t nA, int64_t n,
+                             RwGrid g0, RwGrid g1, unsigned long long* __restrict__ cur, int2* __restrict__ pts) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const RwGrid& g = i < nA ? g0 : g1;
+    const int64_t c = g.base + (int64_t)rw_cell_axis(Y[i], g.y0, g.h, g.gh) * g.gw + rw_cell_axis(X[i], g.x0, g.h, g.gw);
+    const unsigned long long k = atomicAdd(&cur[c], 1ull);
+    pts[k] = make_int2(X[i], Y[i]);
+}
+
+// Ring search of node i (side s) in the other side's grid; see above.
+// Unfinished queries are listed: side A's from list[0], side B's from
+// list[nA], their counts in nl[0], nl[1].
+__global__ void k_rw_query(const int32_t* __restrict__ X, const int32_t* __restrict__ Y, int64_t nA, int64_t n,
+                           RwGrid g0, RwGrid g1, const unsigned long long* __restrict__ start,
+                           const int2* __restrict__ pts, DiagCost dc, unsigned long long* __restrict__ mind2,
+                           int32_t* __restrict__ list, int* __restrict__ nl) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool sa = i < nA;
+    const RwGrid& g = sa ? g1 : g0;  // the other side's grid
+    const int64_t ux = X[i], uy = Y[i];
+    const int64_t cm = cost_make((int32_t)ux, (int32_t)uy, dc);
+    const int32_t cx = rw_cell_axis(ux, g.x0, g.h, g.gw), cy = rw_cell_axis(uy, g.y0, g.h, g.gh);
+    unsigned long long best = ~0ull;
+    auto visit = [&](int32_t x, int32_t y) {
+        const int64_t c = g.base + (int64_t)y * g.gw + x;
+        const unsigned long long k1 = start[c + 1];
+        for (unsigned long long k = start[c]; k < k1; k++) {
+            const int2 v = pts[k];
+            const long long dx = ux - v.x, dy = uy - v.y;
+            const unsigned long long d2 = (unsigned long long)(dx * dx) + (unsigned long long)(dy * dy);
+            best = d2 < best ? d2 : best;
+        }
+    };
+    int state = 0;  // 0 searching, 1 exact, 2 stopped by the diagonal cost
+    for (int32_t K = 0; K <= RW_KMAX && state == 0; K++) {
+        if (K == 0) {
+            visit(cx, cy);
+        } else {
+            const int32_t xlo = max(cx - K, 0), xhi = min(cx + K, g.gw - 1);
+            if (cy - K >= 0)
+                for (int32_t x = xlo; x <= xhi; x++) visit(x, cy - K);
+            if (cy + K < g.gh)
+                for (int32_t x = xlo; x <= xhi; x++) visit(x, cy + K);
+            const int32_t ylo = max(cy - K + 1, 0), yhi = min(cy + K - 1, g.gh - 1);
+            if (cx - K >= 0)
+                for (int32_t y = ylo; y <= yhi; y++) visit(cx - K, y);
+            if (cx + K < g.gw)
+                for (int32_t y = ylo; y <= yhi; y++) visit(cx + K, y);
+        }
+        // distance to the nearest side of the searched square beyond which nodes may remain
+        int64_t lb = INT64_MAX;
+        if (cx - K > 0) lb = min(lb, ux - (g.x0 + (int64_t)(cx - K) * g.h));
+        if (cx + K < g.gw - 1) lb = min(lb, g.x0 + (int64_t)(cx + K + 1) * g.h - ux);
+        if (cy - K > 0) lb = min(lb, uy - (g.y0 + (int64_t)(cy - K) * g.h));
+        if (cy + K < g.gh - 1) lb = min(lb, g.y0 + (int64_t)(cy + K + 1) * g.h - uy);
+        if (lb == INT64_MAX) {
+            state = 1;  // the whole grid is searched
+        } else {
+            lb = lb < 0 ? 0 : lb;
+            if ((unsigned long long)lb * (unsigned long long)lb >= best) state = 1;
+            else if (lb >= cm) state = 2;
+        }
+    }
+    if (state == 2) {
+        const unsigned long long c2 = (unsigned long long)cm * (unsigned long long)cm;
+        best = c2 < best ? c2 : best;
+    }
+    mind2[i] = best;
+    if (state == 0) {
+        const int k = atomicAdd(&nl[sa ? 0 : 1], 1);
+        list[(sa ? 0 : nA) + k] = (int32_t)(sa ? i : i - nA);
+    }
+}
+
+// The all-pairs scan for listed queries only (indices within their side);
+// blockIdx.z = direction, blockIdx.y splits the other side.
+__global__ void __launch_bounds__(RW_THREADS) k_rwmd_min_list(const int32_t* __restrict__ X,
+                                                              const int32_t* __restrict__ Y, int64_t nA, int64_t nB,
+                                                              const int32_t* __restrict__ list, int nlA, int nlB,
+                                                              int64_t chunk, unsigned long long* __restrict__ mind2) {
+    __shared__ int2 q[RW_TILE];
+    const int dir = blockIdx.z;
+    const int64_t pbase = dir == 0 ? 0 : nA, np = dir == 0 ? nlA : nlB;
+    const int64_t qbase = dir == 0 ? nA : 0, nq = dir == 0 ? nB : nA;
+    const int64_t t = (int64_t)blockIdx.x * RW_THREADS + threadIdx.x;
+    const int64_t q0 = (int64_t)blockIdx.y * chunk, q1 = min(nq, q0 + chunk);
+    if ((int64_t)blockIdx.x * RW_THREADS >= np || q0 >= q1) return;
+    int64_t u = -1;
+    int32_t ux = 0, uy = 0;
+    if (t < np) {
+        u = pbase + list[pbase + t];
+        ux = X[u];
+        uy = Y[u];
+    }
+    unsigned long long best = ~0ull;
+    for (int64_t t0 = q0; t0 < q1; t0 += RW_TILE) {
+        const int tn = (int)min((int64_t)RW_TILE, q1 - t0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < tn; j += RW_THREADS) q[j] = make_int2(X[qbase + t0 + j], Y[qbase + t0 + j]);
+        __syncthreads();
+        for (int j = 0; j < tn; j++) {
+            const int2 v = q[j];
+            const long long dx = (long long)(ux - v.x), dy = (long long)(uy - v.y);
+            const unsigned long long d2 = (unsigned long long)(dx * dx) + (unsigned long long)(dy * dy);
+            best = d2 < best ? d2 : best;
+        }
+    }
+    if (u >= 0) atomicMin(&mind2[u], best);
+}
+
 __global__ void k_fill_u64(unsigned long long* p, int64_t n, unsigned long long v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
+}
+
+// Grid geometry of one side with box b (xmin, xmax, ymin, ymax) and n nodes:
+// about two nodes a cell, at most 4 n + 64 cells.
+static RwGrid rw_grid(const int* b, int64_t n, int64_t base) {
+    RwGrid g{};
+    const int64_t W = (int64_t)b[1] - b[0], H = (int64_t)b[3] - b[2];
+    const double cells = (double)std::max<int64_t>(1, n / 2);
+    int64_t hs = (int64_t)ceil(sqrt((double)(W + 1) * (double)(H + 1) / cells));
+    hs = std::max<int64_t>(hs, 1);
+    for (;;) {
+        const int64_t gw = W / hs + 1, gh = H / hs + 1;
+        if (gw * gh <= 4 * n + 64) {
+            g.gw = (int32_t)gw;
+            g.gh = (int32_t)gh;
+            break;
+        }
+        hs *= 2;
+    }
+    g.x0 = b[0];
+    g.y0 = b[2];
+    g.h = hs;
+    g.base = base;
+    return g;
+}
+
+// Exact minima of both directions through the grids (see k_rw_query), the
+// queries the rings did not finish completed by the all-pairs scan.
+static pd_status rwmd_grid(Ctx* c, const Hats& h, DiagCost dc, unsigned long long* mind2, int64_t chunk, int64_t gy,
+                           cudaStream_t st) {
+    const int64_t n = h.nA + h.nB;
+    int* box = bufT<int>(c, B_RW_BOX, 8);
+    int* nl = bufT<int>(c, B_RW_NL, 2);
+    if (!box || !nl) return PD_ENOMEM;
+    k_rw_box_init<<<1, 32, 0, st>>>(box); pd::count_launch();
+    k_rw_box<<<grid_for(n, 256), 256, 0, st>>>(h.X, h.Y, h.nA, n, box); pd::count_launch();
+    int hb[8];
+    PD_TRY_CUDA(c, cudaMemcpyAsync(hb, box, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    const RwGrid g0 = rw_grid(hb, h.nA, 0);
+    const RwGrid g1 = rw_grid(hb + 4, h.nB, (int64_t)g0.gw * g0.gh);
+    const int64_t cells = g1.base + (int64_t)g1.gw * g1.gh;
+    unsigned long long* start = bufT<unsigned long long>(c, B_RW_START, cells + 1);
+    unsigned long long* cur = bufT<unsigned long long>(c, B_RW_CUR, cells + 1);
+    unsigned long long* part = bufT<unsigned long long>(c, B_SCAN_PART, scan_tiles(cells + 1) + 1);
+    int2* pts = bufT<int2>(c, B_RW_PTS, n);
+    int32_t* list = bufT<int32_t>(c, B_RW_LIST, n);
+    if (!start || !cur || !part || !pts || !list) return PD_ENOMEM;
+    PD_TRY_CUDA(c, cudaMemsetAsync(start, 0, sizeof(unsigned long long) * (cells + 1), st));
+    PD_TRY_CUDA(c, cudaMemsetAsync(nl, 0, 2 * sizeof(int), st));
+    k_rw_hist<<<grid_for(n, 256), 256, 0, st>>>(h.X, h.Y, h.nA, n, g0, g1, start); pd::count_launch();
+    PD_TRY_CUDA(c, exclusive_scan<unsigned long long>(start, start, cells + 1, part, nullptr, st));
+    PD_TRY_CUDA(c, cudaMemcpyAsync(cur, start, sizeof(unsigned long long) * (cells + 1), cudaMemcpyDeviceToDevice, st));
+    k_rw_scatter<<<grid_for(n, 256), 256, 0, st>>>(h.X, h.Y, h.nA, n, g0, g1, cur, pts); pd::count_launch();
+    k_rw_query<<<grid_for(n, 128), 128, 0, st>>>(h.X, h.Y, h.nA, n, g0, g1, start, pts, dc, mind2, list, nl); pd::count_launch();
+    PD_TRY_CUDA(c, cudaGetLastError());
+    int hn[2];
+    PD_TRY_CUDA(c, cudaMemcpyAsync(hn, nl, sizeof(hn), cudaMemcpyDeviceToHost, st));
+    PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+    c->last_rw_unfinished = (int64_t)hn[0] + hn[1];
+    if (hn[0] + hn[1] > 0) {
+        const int64_t gx = (std::max(hn[0], hn[1]) + RW_THREADS - 1) / RW_THREADS;
+        k_rwmd_min_list<<<dim3((unsigned)gx, (unsigned)gy, 2), RW_THREADS, 0, st>>>(h.X, h.Y, h.nA, h.nB, list, hn[0],
+                                                                                    hn[1], chunk, mind2); pd::count_launch();
+        PD_TRY_CUDA(c, cudaGetLastError());
+    }
+    return PD_OK;
 }
 
 pd_status stage_rwmd(Ctx* c, const Hats& h, int64_t L[3], DiagCost dc, cudaStream_t st) {
@@ -277,8 +531,11 @@ pd_status stage_rwmd(Ctx* c, const Hats& h, int64_t L[3], DiagCost dc, cudaStrea
         if (chunk < 256) chunk = 256;
         gy = (nqmax + chunk - 1) / chunk;
         if (gy < 1) gy = 1;
-        if (gx > 0 && h.nA > 0 && h.nB > 0)
+        if (h.nA > 0 && h.nB > 0 && h.nA * h.nB >= RW_GRID_MIN) {
+            PD_TRY(rwmd_grid(c, h, dc, mind2, chunk, gy, st));
+        } else if (gx > 0 && h.nA > 0 && h.nB > 0) {
             k_rwmd_min<<<dim3((unsigned)gx, (unsigned)gy, 2), RW_THREADS, 0, st>>>(h.X, h.Y, h.nA, h.nB, chunk, mind2); pd::count_launch();
+        }
         k_rwmd_sum<<<grid_for(n, 256), 256, 0, st>>>(h.X, h.Y, h.cnt, h.nA, n, mind2, dc, sm + S_L0); pd::count_launch();
         PD_TRY_CUDA(c, cudaGetLastError());
     }

@@ -39,6 +39,7 @@ enum Buf : int {
     B_SP_BB, B_SP_REPK, B_SP_REPN, B_SP_FLAG, B_SP_RANK, B_SP_X, B_SP_Y, B_SP_CA, B_SP_CB, B_SP_CODE, B_SP_POS,
     B_CO_BOX, B_CO_P, B_CO_P2,      // coarse-solve warm start
     B_NS_JOBS, B_NS_CERT,           // batched certificate
+    B_RW_BOX, B_RW_START, B_RW_CUR, B_RW_PTS, B_RW_LIST, B_RW_NL,  // RWMD grid
     B_SMALL,                        // small device scalars
     B_COUNT
 };
@@ -79,6 +80,7 @@ struct Ctx {
     Ctx* parent = nullptr;
     Ctx* coarse = nullptr;            // helper context of the coarse solve (warm_start 4)
     int64_t last_coarse_pivots = 0;   // pivots of the last coarse solve
+    int64_t last_rw_unfinished = 0;   // RWMD grid queries finished by the all-pairs scan
     // the batch's wave as a CUDA graph (ns_run_wave): pinned staging, the
     // captured executable and what it was captured with
     void* wave_pin = nullptr;

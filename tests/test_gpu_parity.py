@@ -433,3 +433,28 @@ def test_w1_certificate_on_coarse_decompositions(pd, ctx):
         if g["cert_failures"] > 0:
             assert g["solve_method"] == 1
     assert fails > 0
+
+
+@pytest.mark.parametrize("kappa,tau", [(1, 0), (0, 5000), (1, 1000)])
+def test_rwmd_grid_matches_oracle(pd, ctx, kappa, tau):
+    """Sides whose product of node counts is at least 2^28 take the grid
+    search (rings of cells, stopped by the best distance or by the diagonal
+    cost); a few far outliers in both diagrams leave the rings unfinished and
+    go through the all-pairs scan.  L_A, L_B are the oracle's brute force."""
+    A, B = synth.mixture_f32(25000, 41), synth.mixture_f32(22000, 42)
+    far = np.array([[0.9, 9.5], [0.1, 7.0], [3.0, 3.2]], np.float32)
+    A = np.concatenate([A, far])
+    B = np.concatenate([B, far[:2] + np.float32(0.25)])
+    Ah, Bh = _oracle_hats(A, B, "f32", 20)
+    assert len(Ah[0]) * len(Bh[0]) >= 1 << 28
+    o = pd.opts(diag_kappa=kappa, diag_tau=tau)
+    assert pd.pd_rwmd_lower_bound(ctx, _cuda(A), _cuda(B), o) == oracle.rwmd(Ah, Bh, kappa, tau)
+    assert pd.pd_rwmd_lower_bound(ctx, _cuda(B), _cuda(A), o) == oracle.rwmd(Bh, Ah, kappa, tau)
+
+
+def test_rwmd_grid_lowerstar_100k(pd, ctx):
+    """The 100k lower-star pair of the benchmark (lattice coordinates, many
+    equal distances) through whichever RWMD path its sizes select."""
+    A, B = synth.lowerstar_u8(100000, 1000), synth.lowerstar_u8(100000, 1001)
+    Ah, Bh = _oracle_hats(A, B, "u8", 12)
+    assert pd.pd_rwmd_lower_bound(ctx, _cuda(A), _cuda(B)) == oracle.rwmd(Ah, Bh)
