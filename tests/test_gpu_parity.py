@@ -458,3 +458,21 @@ def test_rwmd_grid_lowerstar_100k(pd, ctx):
     A, B = synth.lowerstar_u8(100000, 1000), synth.lowerstar_u8(100000, 1001)
     Ah, Bh = _oracle_hats(A, B, "u8", 12)
     assert pd.pd_rwmd_lower_bound(ctx, _cuda(A), _cuda(B)) == oracle.rwmd(Ah, Bh)
+
+
+@pytest.mark.parametrize("tree", [0, 1])
+def test_wspd_count_matches_oracle_10k_nodes(pd, ctx, tree):
+    """About 10,000 continuous nodes at s = 40 (a pair frontier of about a
+    million pairs at its widest level), both trees: the counted WSPD equals
+    the arcs of the oracle's network."""
+    A, B = synth.mixture_f32(5200, 51), synth.mixture_f32(4800, 52)
+    Ah, Bh = _oracle_hats(A, B, "f32", 20)
+    nodes = oracle.condense_delta(Ah, Bh, 16, 0, 3)
+    assert len(nodes["X"]) > 9000
+    if tree == 1:
+        perm, t = oracle.split_tree(nodes)
+        nodes_t = oracle.reorder(nodes, perm)
+    else:
+        nodes_t, t = nodes, oracle.radix_tree(nodes)
+    exp = oracle.build_network(nodes_t, *oracle.wspd(nodes_t, t, 40))
+    assert pd.pd_wspd_count(ctx, _upload_nodes(nodes), 40, tree) == int(exp["row_ptr"][-1])
