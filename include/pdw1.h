@@ -391,7 +391,7 @@ pd_status pd_tuned_block(const pd_ctx* ctx, int64_t arcs_and_nodes, int64_t* blo
 
 /* ---- learned warm start (no counterpart in the paper) ----------------------
  *
- * A network of 68 -> 128 -> 128 -> 1 units (ReLU) predicts, per node of the
+ * A network of 72 -> 128 -> 128 -> 1 units (ReLU) predicts, per node of the
  * transportation form, the correction from the potentials of a coarse solve
  * of the same pair (pd_opts warm_start = 4) to its optimal potential (up to a
  * common offset); the simplex then starts from a greedy flow on the arcs of
@@ -399,18 +399,22 @@ pd_status pd_tuned_block(const pd_ctx* ctx, int64_t arcs_and_nodes, int64_t* blo
  * root at its predicted potential, instead of the all-artificial tree
  * (pd_opts warm_start = 1).  Weights are stored in bf16, products accumulate in
  * float32; the float32 master parameters (PD_WS_NPARAMS floats) are laid out
- * as W1[68][128], b1[128], W2[128][128], b2[128], w3[128], b3 (W[k][j] is the
- * weight from input k to unit j).  Features of a node (68): its coordinates
- * relative to the pair's node box and divided by the box's larger side,
- * log(1 + cntA), log(1 + cntB), and an 8 x 8 window (offsets -4..3) of a
+ * as W1[72][128], b1[128], W2[128][128], b2[128], w3[128], b3 (W[k][j] is the
+ * weight from input k to unit j); w3 and b3 start at 0, so an untrained
+ * network gives the coarse start unchanged.  Features of a node (72): its
+ * coordinates relative to the pair's node box and divided by the box's larger
+ * side, log(1 + cntA), log(1 + cntB), an 8 x 8 window (offsets -4..3) of a
  * 64 x 64 grid over the box holding sign(s) log(1 + |s|) of the summed supply
- * s = cntA - cntB of the nodes in each cell.  Target: ((potential of the node
- * in the optimal tree - the mean potential of the tree's largest component
- * below the root) - (the same for the coarse solve's potentials)) / the box's
- * side, for the nodes of that component.
+ * s = cntA - cntB of the nodes in each cell, half the gap between the coarse
+ * optimum's upper and lower c-transform envelopes at the node over the coarse
+ * cell Gc (at most 16), +1 / -1 for a source / sink, and the node's offset
+ * from its coarse lattice point over Gc.  Target: ((potential of the node in
+ * the optimal tree - the mean potential of the tree's largest component below
+ * the root) - (the same for the coarse solve's potentials)) / Gc, for the
+ * nodes of that component.
  */
-#define PD_WS_NFEAT 68
-#define PD_WS_NPARAMS 25473
+#define PD_WS_NFEAT 72
+#define PD_WS_NPARAMS 25985
 
 typedef struct {
     int64_t rows;        /* training rows (transportation nodes) collected */
@@ -421,11 +425,19 @@ typedef struct {
     float collect_ms;    /* host wall time of the cold solves and feature extraction */
     float train_ms;      /* host wall time of the optimisation */
     int64_t cold_pivots; /* pivots of the cold solves */
+    int64_t val_rows;    /* rows of the held-out pairs */
+    int32_t val_pairs;   /* held-out pairs: the last n_pairs / 8 (at least one) when n_pairs >= 4, else 0 */
+    int32_t best_epoch;  /* epoch whose weights are kept (0: the initial ones, i.e. no correction) */
+    float val_loss_zero; /* held-out mean squared error of predicting no correction */
+    float val_loss;      /* held-out mean squared error of the kept weights */
 } pd_ws_stats;
 
 /* Trains the context's network (initialised from `seed` on first use) on the
  * potentials of cold solves of the n_pairs pairs (A[i], B[i]) at eps/opts:
- * `epochs` passes of Adam (lr) over minibatches of 2048 rows, on the device. */
+ * `epochs` passes of Adam (lr) over minibatches of 2048 rows drawn in a
+ * seeded random order, on the device.  The last pairs are held out (see
+ * pd_ws_stats.val_pairs); the weights of the epoch with the smallest held-out
+ * error are kept, the initial ones (no correction) when no epoch beats them. */
 pd_status pd_ws_train(pd_ctx* ctx, const pd_diagram* A, const pd_diagram* B, int64_t n_pairs, double eps,
                       const pd_opts* opts, int32_t epochs, float lr, uint64_t seed, pd_ws_stats* out,
                       void* stream);

@@ -1,13 +1,13 @@
 """Oracle of the warm-start network (test infrastructure only: the product
 path never imports it).  Plain numpy in float64 of what the device computes:
-68 -> 128 -> 128 -> 1 with ReLU, weight matrices rounded to bf16, biases as
+72 -> 128 -> 128 -> 1 with ReLU, weight matrices rounded to bf16, biases as
 given, features rounded to bf16; loss sum(mask (y - t)^2) / n and its
-gradient by the chain rule.  Parameter layout: W1[68][128], b1[128],
+gradient by the chain rule.  Parameter layout: W1[72][128], b1[128],
 W2[128][128], b2[128], w3[128], b3.  Pinned against central finite
 differences in tests/test_oracle_pins.py."""
 import numpy as np
 
-NIN, NH = 68, 128
+NIN, NH = 72, 128
 OFF_W1 = 0
 OFF_B1 = OFF_W1 + NIN * NH
 OFF_W2 = OFF_B1 + NH

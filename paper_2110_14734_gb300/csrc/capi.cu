@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <random>
 #include <atomic>
 #include <chrono>
 #include <mutex>
@@ -991,8 +992,13 @@ extern "C" pd_status pd_ws_train(pd_ctx* c, const pd_diagram* A, const pd_diagra
         return PD_ENOMEM;
     c->ws_cap = cap;
     c->ws_rows = 0;
+    // the last eighth of the pairs (at least one, with four or more pairs)
+    // is held out: its rows pick the epoch whose weights are kept
+    const int64_t n_val = n_pairs >= 4 ? std::max<int64_t>(1, n_pairs / 8) : 0;
+    int64_t r_train = 0;
     const auto t0 = std::chrono::steady_clock::now();
     for (int64_t i = 0; i < n_pairs; i++) {
+        if (i == n_pairs - n_val) r_train = c->ws_rows;
         Front f;
         PD_TRY(front_half(c, A[i], B[i], eps, o, &f, st, true));
         W1Prep w;
@@ -1011,33 +1017,72 @@ extern "C" pd_status pd_ws_train(pd_ctx* c, const pd_diagram* A, const pd_diagra
         r.pairs++;
         r.cold_pivots += rec.pivots;
     }
+    if (n_val == 0) r_train = c->ws_rows;
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     r.collect_ms = elapsed_ms(t0);
     r.rows = c->ws_rows;
+    r.val_rows = c->ws_rows - r_train;
+    r.val_pairs = (int32_t)n_val;
     const auto t1 = std::chrono::steady_clock::now();
     float* g = bufT<float>(c, B_MLP_G, WS_PART);
-    if (!g) return PD_ENOMEM;
-    const int64_t R = c->ws_rows, bs = 2048;
-    const __nv_bfloat16* F = (const __nv_bfloat16*)c->ptr[B_WS_DF];
-    const float* T = (const float*)c->ptr[B_WS_DT];
-    const float* M = (const float*)c->ptr[B_WS_DM];
+    int32_t* didx = bufT<int32_t>(c, B_WS_IDX, std::max<int64_t>(r_train, 1));
+    if (!g || !didx) return PD_ENOMEM;
+    const int64_t R = r_train, bs = 2048;
+    // held-out loss of predicting no correction (the coarse start itself)
+    if (r.val_rows > 0) {
+        std::vector<float> ht((size_t)r.val_rows), hm((size_t)r.val_rows);
+        PD_TRY_CUDA(c, cudaMemcpyAsync(ht.data(), (const float*)c->ptr[B_WS_DT] + r_train, sizeof(float) * r.val_rows,
+                                       cudaMemcpyDeviceToHost, st));
+        PD_TRY_CUDA(c, cudaMemcpyAsync(hm.data(), (const float*)c->ptr[B_WS_DM] + r_train, sizeof(float) * r.val_rows,
+                                       cudaMemcpyDeviceToHost, st));
+        PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+        double ls = 0.0, ms = 0.0;
+        for (size_t q = 0; q < ht.size(); q++) {
+            ls += (double)hm[q] * (double)ht[q] * (double)ht[q];
+            ms += hm[q];
+        }
+        r.val_loss_zero = (float)(ms > 0.0 ? ls / ms : 0.0);
+        double l0 = 0.0;
+        PD_TRY(mlp_loss(c, r_train, c->ws_rows, &l0, st));
+        r.val_loss = (float)l0;
+        PD_TRY(mlp_snapshot(c, false, st));
+    }
+    std::mt19937_64 rng(seed ^ 0x5DEECE66Dull);
+    std::vector<int32_t> perm((size_t)R);
+    for (int64_t q = 0; q < R; q++) perm[(size_t)q] = (int32_t)q;
     for (int32_t e = 0; e < epochs && R > 0; e++) {
+        std::shuffle(perm.begin(), perm.end(), rng);
+        PD_TRY_CUDA(c, cudaMemcpyAsync(didx, perm.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, st));
         for (int64_t r0 = 0; r0 < R; r0 += bs) {
             const int64_t nb = std::min<int64_t>(bs, R - r0);
-            PD_TRY(mlp_grad(c, F + r0 * WS_IN, T + r0, M + r0, nb, 1.f / (float)nb, g, st));
+            __nv_bfloat16* F;
+            float *T, *M;
+            PD_TRY(mlp_gather_rows(c, didx + r0, nb, &F, &T, &M, st));
+            PD_TRY(mlp_grad(c, F, T, M, nb, 1.f / (float)nb, g, st));
             const bool first = r.steps == 0, last = e == epochs - 1 && r0 + bs >= R;
             if (first || last) {
                 float lm[2];
                 PD_TRY_CUDA(c, cudaMemcpyAsync(lm, g + WS_NPARAMS, sizeof(lm), cudaMemcpyDeviceToHost, st));
                 PD_TRY_CUDA(c, cudaStreamSynchronize(st));
-                const float l = lm[0] / (float)nb;
+                const float l = lm[1] > 0.f ? lm[0] / lm[1] : 0.f;
                 if (first) r.loss_first = l;
                 if (last) r.loss_last = l;
             }
             PD_TRY(mlp_adam(c, g, lr, st));
             r.steps++;
         }
+        PD_TRY_CUDA(c, cudaStreamSynchronize(st));  // perm is rewritten next epoch
+        if (r.val_rows > 0) {
+            double lv = 0.0;
+            PD_TRY(mlp_loss(c, r_train, c->ws_rows, &lv, st));
+            if (lv < (double)r.val_loss) {
+                r.val_loss = (float)lv;
+                r.best_epoch = e + 1;
+                PD_TRY(mlp_snapshot(c, false, st));
+            }
+        }
     }
+    if (r.val_rows > 0) PD_TRY(mlp_snapshot(c, true, st));  // the held-out best (epoch 0: no correction)
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     r.train_ms = elapsed_ms(t1);
     *out = r;

@@ -44,20 +44,22 @@ __global__ void k_node_box(const int32_t* __restrict__ X, const int32_t* __restr
 // them).  Unlike copying the nearest coarse node's potential, this respects
 // the dual constraints of every coarse node, whatever offsets the coarse
 // tree's components carry.  The fine diagonal node takes the coarse diagonal
-// node's potential.  cpi: the coarse
-// instance's potentials (its sources, sinks, diagonal node); dsup: supply of
-// the diagonal node (|B| - |A|).
+// node's potential.  gap: half the distance between the envelopes (0 where
+// one of them is missing), a feature of the learned correction.  cpi: the
+// coarse instance's potentials (its sources, sinks, diagonal node); dsup:
+// supply of the diagonal node (|B| - |A|).
 __global__ void k_ctransform_potential(const int32_t* __restrict__ S, const int32_t* __restrict__ T, int64_t nS,
                                        int64_t nT, const int32_t* __restrict__ X, const int32_t* __restrict__ Y,
                                        const int32_t* __restrict__ cS, const int32_t* __restrict__ cT, int64_t cnS,
                                        int64_t cnT, const int32_t* __restrict__ cX, const int32_t* __restrict__ cY,
                                        const int64_t* __restrict__ cpi, int64_t dsup, DiagCost dc,
-                                       double* __restrict__ p) {
+                                       double* __restrict__ p, double* __restrict__ gap) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v > nS + nT) return;
     const int64_t D = cnS + cnT;  // the coarse diagonal node
     if (v == nS + nT) {
         p[v] = (double)cpi[D];
+        gap[v] = 0.0;
         return;
     }
     const bool src = v < nS;
@@ -82,12 +84,16 @@ __global__ void k_ctransform_potential(const int32_t* __restrict__ S, const int3
     // the diagonal node's arcs: sources -> D when D demands (dsup < 0), D -> sinks when it supplies
     if (dsup < 0) up = min(up, cpi[D] + du);
     if (dsup > 0) lo = max(lo, cpi[D] - du);
-    double best;
+    double best, half = 0.0;
     if (up == INT64_MAX && lo == INT64_MIN) best = (double)cpi[D];
     else if (up == INT64_MAX) best = (double)lo;
     else if (lo == INT64_MIN) best = (double)up;
-    else best = 0.5 * ((double)up + (double)lo);
+    else {
+        best = 0.5 * ((double)up + (double)lo);
+        half = 0.5 * ((double)up - (double)lo);
+    }
     p[v] = best;
+    gap[v] = half;
 }
 
 static Ctx* coarse_ctx(Ctx* c) {
@@ -101,6 +107,7 @@ static Ctx* coarse_ctx(Ctx* c) {
 pd_status ws_coarse_potentials(Ctx* c, const Front& f, const W1Prep& w, const pd_opts& o, std::vector<double>* p,
                                cudaStream_t st) {
     p->clear();
+    c->last_coarse_cell = 0;
     if (o.warm_cells < 0 || o.warm_cells > 4096) return fail(c, PD_EINVAL, "warm_cells must be 0 .. 4096");
     if (!w.ns.ready || f.nodes.n_nodes == 0) return PD_OK;
     const int64_t cells = o.warm_cells > 0 ? o.warm_cells : COARSE_CELLS;
@@ -137,16 +144,18 @@ pd_status ws_coarse_potentials(Ctx* c, const Front& f, const W1Prep& w, const pd
     if (e != PD_OK) return fail(c, e, "coarse solve: " + cc->err);
     const int64_t nt = w.nt;
     double* dp = bufT<double>(c, B_CO_P, nt);
-    if (!dp) return PD_ENOMEM;
+    double* dg = bufT<double>(c, B_CO_GAP, nt);
+    if (!dp || !dg) return PD_ENOMEM;
     k_ctransform_potential<<<grid_for(nt, 128), 128, 0, st>>>(w.S, w.T, w.nS, w.nT, f.nodes.X, f.nodes.Y, wc.S,
                                                                wc.T, wc.nS, wc.nT, cn.X, cn.Y, r.pi,
-                                                               f.h.FB - f.h.FA, w.dc, dp);
+                                                               f.h.FB - f.h.FA, w.dc, dp, dg);
     pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     p->resize((size_t)nt);
     PD_TRY_CUDA(c, cudaMemcpyAsync(p->data(), dp, sizeof(double) * nt, cudaMemcpyDeviceToHost, st));
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
     c->last_coarse_pivots = r.pivots;
+    c->last_coarse_cell = Gc;
     return PD_OK;
 }
 

@@ -37,7 +37,8 @@ enum Buf : int {
     B_WS_P, B_WS_ROWK, B_WS_COLK, B_WS_ARCS, B_WS_COST, B_WS_RS, B_WS_RT, B_WS_RC, B_WS_COMP, B_WS_CSIZE, B_WS_CSUM,
     B_SP_ORD, B_SP_ORD2, B_SP_SEG, B_SP_SEG2, B_SP_HI, B_SP_HI2, B_SP_NUM, B_SP_NUM2,  // split tree
     B_SP_BB, B_SP_REPK, B_SP_REPN, B_SP_FLAG, B_SP_RANK, B_SP_X, B_SP_Y, B_SP_CA, B_SP_CB, B_SP_CODE, B_SP_POS,
-    B_CO_BOX, B_CO_P, B_CO_P2,      // coarse-solve warm start
+    B_CO_BOX, B_CO_P, B_CO_P2, B_CO_GAP,  // coarse-solve warm start
+    B_MLP_BEST, B_WS_BF, B_WS_BT, B_WS_BM, B_WS_IDX,  // network training: best weights, shuffled batch
     B_NS_JOBS, B_NS_CERT,           // batched certificate
     B_RW_BOX, B_RW_START, B_RW_CUR, B_RW_PTS, B_RW_LIST, B_RW_NL,  // RWMD grid
     B_SMALL,                        // small device scalars
@@ -80,6 +81,7 @@ struct Ctx {
     Ctx* parent = nullptr;
     Ctx* coarse = nullptr;            // helper context of the coarse solve (warm_start 4)
     int64_t last_coarse_pivots = 0;   // pivots of the last coarse solve
+    int64_t last_coarse_cell = 0;     // its lattice cell (quanta; 0: no coarse solve)
     int64_t last_rw_unfinished = 0;   // RWMD grid queries finished by the all-pairs scan
     // the batch's wave as a CUDA graph (ns_run_wave): pinned staging, the
     // captured executable and what it was captured with

@@ -11,9 +11,15 @@
 //   4..67  an 8 x 8 window of a 64 x 64 grid over the box around the node's
 //          grid cell (offsets -4..3 on each axis): per cell the signed supply
 //          sum(cntA - cntB) of the nodes in it, as sign * log(1 + |sum|)
-// Target / output: (potential of the node - mean potential of the largest
-// component of the optimal simplex tree) / ext, potentials in cost units
-// (nodes outside that component are left out of the loss).
+//   68     half the gap between the coarse optimum's two c-transform
+//          envelopes at the node, over the coarse cell Gc (at most 16)
+//   69     +1 for a source, -1 for a sink
+//   70, 71 offset of the node from its coarse lattice point, over Gc
+//          (in [-1/2, 1/2]); 68, 70, 71 are 0 without a coarse solve
+// Target / output: the correction from the coarse solve's potential to the
+// optimal one (each less its mean over the largest component of the optimal
+// simplex tree), over Gc (the box's side without a coarse solve); nodes
+// outside that component are left out of the loss.
 #include <math.h>
 
 #include <algorithm>
@@ -74,7 +80,7 @@ __global__ void k_features(const int32_t* __restrict__ X, const int32_t* __restr
                            const int64_t* __restrict__ cntA, const int64_t* __restrict__ cntB,
                            const int32_t* __restrict__ S, const int32_t* __restrict__ T, int64_t nS, int64_t nT,
                            const long long* __restrict__ box, const float* __restrict__ grid,
-                           __nv_bfloat16* __restrict__ F) {
+                           const double* __restrict__ gap, int64_t Gc, __nv_bfloat16* __restrict__ F) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nS + nT) return;
     const int32_t u = r < nS ? S[r] : T[r - nS];
@@ -92,6 +98,18 @@ __global__ void k_features(const int32_t* __restrict__ X, const int32_t* __restr
             if (cx >= 0 && cx < WS_GRID && cy >= 0 && cy < WS_GRID) v = grid[cx * WS_GRID + cy];
             f[4 + dx * 8 + dy] = __float2bfloat16(v < 0.f ? -log1pf(-v) : log1pf(v));
         }
+    float g = 0.f, ox = 0.f, oy = 0.f;
+    if (Gc > 0) {
+        g = gap ? (float)fmin(gap[r] / (double)Gc, 16.0) : 0.f;
+        // the coarse lattice point of Algorithm 2's snapping: floor((2X + Gc) / (2 Gc)) Gc
+        const int64_t cx = floor_div(2 * (int64_t)X[u] + Gc, 2 * Gc), cy = floor_div(2 * (int64_t)Y[u] + Gc, 2 * Gc);
+        ox = (float)((double)((int64_t)X[u] - cx * Gc) / (double)Gc);
+        oy = (float)((double)((int64_t)Y[u] - cy * Gc) / (double)Gc);
+    }
+    f[68] = __float2bfloat16(g);
+    f[69] = __float2bfloat16(r < nS ? 1.f : -1.f);
+    f[70] = __float2bfloat16(ox);
+    f[71] = __float2bfloat16(oy);
 }
 
 // The child of the root above node v in the solved tree (its component).
@@ -128,13 +146,15 @@ __global__ void k_component_sum(const int64_t* __restrict__ pi, const int32_t* _
 // matter to the start (only differences enter reduced costs).
 // Target of row r: its optimal potential minus the anchor component's mean,
 // less the same for the base potentials (a coarse solve's) when given, over
-// the node box's side; rows outside the anchor component are masked out.
+// `scale` (the coarse cell; the node box's side when 0); rows outside the
+// anchor component are masked out.
 __global__ void k_targets(const int64_t* __restrict__ pi, const int32_t* __restrict__ comp, int64_t n,
                           int32_t anchor, double mean, const double* __restrict__ base, double base_mean,
-                          const long long* __restrict__ box, float* __restrict__ t, float* __restrict__ mask) {
+                          const long long* __restrict__ box, int64_t scale, float* __restrict__ t,
+                          float* __restrict__ mask) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    const long long ext = max(max(box[2] - box[0], box[3] - box[1]), 1LL);
+    const long long ext = scale > 0 ? (long long)scale : max(max(box[2] - box[0], box[3] - box[1]), 1LL);
     const bool ok = comp[r] == anchor;
     const double b = base ? base[r] - base_mean : 0.0;
     t[r] = ok ? (float)(((double)pi[r] - mean - b) / (double)ext) : 0.f;
@@ -374,11 +394,27 @@ __global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict
     if (t < WS_NPARAMS) wb[t] = __float2bfloat16(p[t]);
 }
 
+// Rows idx[0..n) of the data set (features, targets, mask) into a batch.
+__global__ void k_gather_rows(const __nv_bfloat16* __restrict__ F, const float* __restrict__ T,
+                              const float* __restrict__ M, const int32_t* __restrict__ idx, int64_t n,
+                              __nv_bfloat16* __restrict__ Fo, float* __restrict__ To, float* __restrict__ Mo) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * WS_IN) return;
+    const int64_t r = t / WS_IN, k = t - r * WS_IN;
+    const int64_t src = idx[r];
+    Fo[t] = F[src * WS_IN + k];
+    if (k == 0) {
+        To[r] = T[src];
+        Mo[r] = M[src];
+    }
+}
+
+// Outputs in cost units: times the coarse cell (scale > 0) or the box's side.
 __global__ void k_scale_out(const float* __restrict__ y, int64_t n, const long long* __restrict__ box,
-                            float* __restrict__ p) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                            int64_t scale, float* __restrict__ p) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r > n) return;
-    const long long ext = max(max(box[2] - box[0], box[3] - box[1]), 1LL);
+    const long long ext = scale > 0 ? (long long)scale : max(max(box[2] - box[0], box[3] - box[1]), 1LL);
     p[r] = r < n ? y[r] * (float)ext : 0.f;  // row n: the diagonal node, potential 0
 }
 
@@ -400,8 +436,8 @@ static size_t backward_smem() {
     return sizeof(float) * (WS_TILE * WS_IN + 2 * WS_TILE * WS_H + WS_TILE + WS_IN * WS_H + WS_H * WS_H + 3 * WS_H + 3);
 }
 
-// Parameters: allocated and initialised once per context (He-uniform from a
-// SplitMix64 stream of `seed`, biases 0).
+// Parameters: allocated and initialised once per context (hidden layers
+// He-uniform from a SplitMix64 stream of `seed`, output layer and biases 0).
 pd_status mlp_init(Ctx* c, uint64_t seed, bool force, cudaStream_t st) {
     if (c->mlp_ready && !force) return PD_OK;
     float* p = bufT<float>(c, B_MLP_P, WS_NPARAMS);
@@ -419,10 +455,11 @@ pd_status mlp_init(Ctx* c, uint64_t seed, bool force, cudaStream_t st) {
         x ^= x >> 31;
         return (double)(x >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
     };
-    const double a1 = std::sqrt(6.0 / WS_IN), a2 = std::sqrt(6.0 / WS_H), a3 = std::sqrt(3.0 / WS_H);
+    const double a1 = std::sqrt(6.0 / WS_IN), a2 = std::sqrt(6.0 / WS_H);
     for (int t = 0; t < WS_IN * WS_H; t++) h[WS_OFF_W1 + t] = (float)(a1 * unif());
     for (int t = 0; t < WS_H * WS_H; t++) h[WS_OFF_W2 + t] = (float)(a2 * unif());
-    for (int t = 0; t < WS_H; t++) h[WS_OFF_W3 + t] = (float)(a3 * unif());
+    // the output layer starts at 0: the untrained network predicts no
+    // correction, so the start is the coarse solve's until training moves it
     PD_TRY(mlp_set(c, h.data(), st));
     c->mlp_steps = 0;
     return PD_OK;
@@ -490,6 +527,60 @@ pd_status mlp_adam(Ctx* c, const float* g, float lr, cudaStream_t st) {
     return PD_OK;
 }
 
+pd_status mlp_gather_rows(Ctx* c, const int32_t* idx, int64_t n, __nv_bfloat16** F, float** T, float** M,
+                          cudaStream_t st) {
+    __nv_bfloat16* Fo = bufT<__nv_bfloat16>(c, B_WS_BF, std::max<int64_t>(n, 1) * WS_IN);
+    float* To = bufT<float>(c, B_WS_BT, std::max<int64_t>(n, 1));
+    float* Mo = bufT<float>(c, B_WS_BM, std::max<int64_t>(n, 1));
+    if (!Fo || !To || !Mo) return PD_ENOMEM;
+    if (n > 0) {
+        k_gather_rows<<<grid_for(n * WS_IN, 256), 256, 0, st>>>((const __nv_bfloat16*)c->ptr[B_WS_DF],
+                                                                 (const float*)c->ptr[B_WS_DT],
+                                                                 (const float*)c->ptr[B_WS_DM], idx, n, Fo, To, Mo); pd::count_launch();
+        PD_TRY_CUDA(c, cudaGetLastError());
+    }
+    *F = Fo;
+    *T = To;
+    *M = Mo;
+    return PD_OK;
+}
+
+// Master parameters to the snapshot (restore false) or back from it, with
+// the bf16 copies and the optimiser state left as they are.
+pd_status mlp_snapshot(Ctx* c, bool restore, cudaStream_t st) {
+    float* p = (float*)c->ptr[B_MLP_P];
+    float* b = bufT<float>(c, B_MLP_BEST, WS_NPARAMS);
+    if (!p || !b) return PD_ENOMEM;
+    PD_TRY_CUDA(c, cudaMemcpyAsync(restore ? p : b, restore ? b : p, sizeof(float) * WS_NPARAMS,
+                                   cudaMemcpyDeviceToDevice, st));
+    if (restore) {
+        k_to_bf16<<<grid_for(WS_NPARAMS, 256), 256, 0, st>>>(p, (__nv_bfloat16*)c->ptr[B_MLP_WB]); pd::count_launch();
+        PD_TRY_CUDA(c, cudaGetLastError());
+    }
+    return PD_OK;
+}
+
+// Mean squared error (over the masked rows) of data-set rows [r0, r1).
+pd_status mlp_loss(Ctx* c, int64_t r0, int64_t r1, double* loss, cudaStream_t st) {
+    float* g = bufT<float>(c, B_MLP_G, WS_PART);
+    if (!g) return PD_ENOMEM;
+    const __nv_bfloat16* F = (const __nv_bfloat16*)c->ptr[B_WS_DF];
+    const float* T = (const float*)c->ptr[B_WS_DT];
+    const float* M = (const float*)c->ptr[B_WS_DM];
+    double ls = 0.0, ms = 0.0;
+    for (int64_t a = r0; a < r1; a += 2048) {
+        const int64_t nb = std::min<int64_t>(2048, r1 - a);
+        PD_TRY(mlp_grad(c, F + a * WS_IN, T + a, M + a, nb, 1.f, g, st));
+        float lm[2];
+        PD_TRY_CUDA(c, cudaMemcpyAsync(lm, g + WS_NPARAMS, sizeof(lm), cudaMemcpyDeviceToHost, st));
+        PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+        ls += lm[0];
+        ms += lm[1];
+    }
+    *loss = ms > 0.0 ? ls / ms : 0.0;
+    return PD_OK;
+}
+
 // Features of a prepared transportation instance (rows: its sources then its
 // sinks), written to F (device, (nS + nT) x WS_IN bf16); box (device, 4).
 pd_status ws_features(Ctx* c, const pd_nodes& nodes, const W1Prep& w, __nv_bfloat16* F, long long* box,
@@ -505,9 +596,12 @@ pd_status ws_features(Ctx* c, const pd_nodes& nodes, const W1Prep& w, __nv_bfloa
         k_box<<<grid_for(N, 256), 256, 0, st>>>(nodes.X, nodes.Y, N, box); pd::count_launch();
         k_grid<<<grid_for(N, 256), 256, 0, st>>>(nodes.X, nodes.Y, nodes.cntA, nodes.cntB, N, box, grid); pd::count_launch();
     }
+    // the coarse solve's envelope gaps and cell, when one ran on this context for this instance
+    const int64_t Gc = c->last_coarse_cell;
+    const double* gap = Gc > 0 ? (const double*)c->ptr[B_CO_GAP] : nullptr;
     if (w.nS + w.nT > 0)
         k_features<<<grid_for(w.nS + w.nT, 128), 128, 0, st>>>(nodes.X, nodes.Y, nodes.cntA, nodes.cntB, w.S, w.T,
-                                                                w.nS, w.nT, box, grid, F); pd::count_launch();
+                                                                w.nS, w.nT, box, grid, gap, Gc, F); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));  // h_small + 24 is reused
     return PD_OK;
@@ -524,7 +618,7 @@ pd_status ws_predict(Ctx* c, const pd_nodes& nodes, const W1Prep& w, std::vector
     if (!F || !y || !ps || !box) return PD_ENOMEM;
     PD_TRY(ws_features(c, nodes, w, F, box, st));
     PD_TRY(mlp_forward(c, F, n, y, st));
-    k_scale_out<<<grid_for(n + 1, 256), 256, 0, st>>>(y, n, box, ps); pd::count_launch();
+    k_scale_out<<<grid_for(n + 1, 256), 256, 0, st>>>(y, n, box, c->last_coarse_cell, ps); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     p->resize((size_t)(n + 1));
     PD_TRY_CUDA(c, cudaMemcpyAsync(p->data(), ps, sizeof(float) * (n + 1), cudaMemcpyDeviceToHost, st));
@@ -582,7 +676,8 @@ pd_status ws_collect(Ctx* c, const pd_nodes& nodes, const W1Prep& w, const NSIns
         if (!db) return PD_ENOMEM;
         PD_TRY_CUDA(c, cudaMemcpyAsync(db, base->data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
     }
-    k_targets<<<grid_for(n, 256), 256, 0, st>>>(r.pi, comp, n, anchor, mean, db, bmean, box, T + have, M + have); pd::count_launch();
+    k_targets<<<grid_for(n, 256), 256, 0, st>>>(r.pi, comp, n, anchor, mean, db, bmean, box,
+                                                db ? c->last_coarse_cell : 0, T + have, M + have); pd::count_launch();
     PD_TRY_CUDA(c, cudaGetLastError());
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));  // the base copy's host memory belongs to the caller
     (void)d_res;

@@ -12,7 +12,7 @@
 
 namespace pd {
 
-constexpr int WS_IN = 68;    // features per node
+constexpr int WS_IN = 72;    // features per node
 constexpr int WS_H = 128;    // hidden width (both layers)
 constexpr int WS_TILE = 32;  // nodes per block step
 constexpr int WS_GRID = 64;  // density grid per axis
@@ -33,6 +33,14 @@ pd_status mlp_forward(Ctx* c, const __nv_bfloat16* F, int64_t n, float* y, cudaS
 pd_status mlp_grad(Ctx* c, const __nv_bfloat16* F, const float* t, const float* mask, int64_t n, float inv_norm,
                    float* g, cudaStream_t st);
 pd_status mlp_adam(Ctx* c, const float* g, float lr, cudaStream_t st);
+// Rows idx[0..n) (device) of the context's data set gathered into a batch
+// (context-owned buffers, valid until the next gather).
+pd_status mlp_gather_rows(Ctx* c, const int32_t* idx, int64_t n, __nv_bfloat16** F, float** T, float** M,
+                          cudaStream_t st);
+// Master parameters saved to (restore false) or restored from the snapshot.
+pd_status mlp_snapshot(Ctx* c, bool restore, cudaStream_t st);
+// Masked mean squared error of data-set rows [r0, r1).
+pd_status mlp_loss(Ctx* c, int64_t r0, int64_t r1, double* loss, cudaStream_t st);
 pd_status ws_features(Ctx* c, const pd_nodes& nodes, const W1Prep& w, __nv_bfloat16* F, long long* box,
                       cudaStream_t st);
 pd_status ws_predict(Ctx* c, const pd_nodes& nodes, const W1Prep& w, std::vector<float>* p, cudaStream_t st);

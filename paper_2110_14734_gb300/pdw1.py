@@ -82,14 +82,15 @@ class pd_nn_result(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-WS_NFEAT = 68
-WS_NPARAMS = 25473
+WS_NFEAT = 72
+WS_NPARAMS = 25985
 
 
 class pd_ws_stats(C.Structure):
     _fields_ = [("rows", C.c_int64), ("pairs", C.c_int32), ("steps", C.c_int32), ("loss_first", C.c_float),
                 ("loss_last", C.c_float), ("collect_ms", C.c_float), ("train_ms", C.c_float),
-                ("cold_pivots", C.c_int64)]
+                ("cold_pivots", C.c_int64), ("val_rows", C.c_int64), ("val_pairs", C.c_int32),
+                ("best_epoch", C.c_int32), ("val_loss_zero", C.c_float), ("val_loss", C.c_float)]
 
     def to_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

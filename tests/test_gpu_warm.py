@@ -87,32 +87,40 @@ def test_exact_potentials_start_keeps_the_optimum_and_saves_pivots(pd, ctx, name
 
 
 def test_trained_network_start_keeps_the_optimum_and_reports_its_gain(pd, ctx):
-    """Training lowers the loss; a start from the coarse solve's potentials
-    corrected by the trained network keeps the optimum on seen and unseen
-    pairs and saves pivots against the cold start on the pairs it was trained
-    on (the gain on unseen pairs is printed; the benchmark reports it at the
-    full size)."""
-    train = [(synth.lowerstar_u8(20000, 3000 + 2 * i), synth.lowerstar_u8(20000, 3001 + 2 * i)) for i in range(3)]
+    """Training on seeded pairs with the last ones held out keeps the weights
+    of the epoch with the smallest held-out error, never worse than no
+    correction; the start from the coarse solve corrected by the trained
+    network keeps the optimum, saves pivots against the cold start on unseen
+    pairs, and its gain over the coarse start alone is printed (the benchmark
+    reports it at the full size)."""
+    train = [(synth.lowerstar_u8(20000, 3000 + 2 * i), synth.lowerstar_u8(20000, 3001 + 2 * i)) for i in range(8)]
+    ctx = pd.pd_create(0)  # a fresh network: earlier tests left other parameters in the module's context
     st = pd.pd_ws_train(ctx, [_cuda(a) for a, _ in train], [_cuda(b) for _, b in train], 0.05,
-                        epochs=1500, lr=5e-4, seed=1)
-    assert st["pairs"] == 3 and st["rows"] > 0 and st["loss_last"] < 0.05 * st["loss_first"]
+                        epochs=20, lr=3e-4, seed=1)
+    assert st["pairs"] == 8 and st["val_pairs"] == 1 and st["rows"] > st["val_rows"] > 0
+    assert st["val_loss"] <= st["val_loss_zero"] * (1 + 1e-5) + 1e-12
+    assert 0 <= st["best_epoch"] <= 20
+    print("held-out mse: no correction %.4g, kept weights %.4g (epoch %d)" % (
+        st["val_loss_zero"], st["val_loss"], st["best_epoch"]))
     seen = train[0]
     unseen = (synth.lowerstar_u8(20000, 5000), synth.lowerstar_u8(20000, 5001))
     gains = {}
     for name, (A, B) in (("seen", seen), ("unseen", unseen)):
         cold = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05)
+        coarse = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05, pd.opts(warm_start=4))
         warm = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05, pd.opts(warm_start=1))
-        assert warm["opt_quanta"] == cold["opt_quanta"] and warm["verified"] == 1
+        assert warm["opt_quanta"] == cold["opt_quanta"] == coarse["opt_quanta"] and warm["verified"] == 1
         assert warm["warm_used"] == 1
-        gains[name] = (cold["pivots"], warm["pivots"])
-    print("pivots (cold, warm): seen %s unseen %s" % (gains["seen"], gains["unseen"]))
-    assert gains["seen"][1] < gains["seen"][0]
+        gains[name] = (cold["pivots"], coarse["pivots"], warm["pivots"])
+    print("pivots (cold, coarse start, coarse + network): seen %s unseen %s" % (gains["seen"], gains["unseen"]))
+    assert gains["unseen"][2] < gains["unseen"][0]
     # the batched solve with the same network gives the same optima
     wb = pd.pd_w1_approx_batch(ctx, [_cuda(seen[0]), _cuda(unseen[0])], [_cuda(seen[1]), _cuda(unseen[1])], 0.05,
                                pd.opts(warm_start=1))
     for (a, b), r in zip((seen, unseen), wb):
         assert r["warm_used"] == 1
         assert r["opt_quanta"] == pd.pd_w1_approx(ctx, _cuda(a), _cuda(b), 0.05)["opt_quanta"]
+    ctx.close()
 
 
 def test_cost_greedy_start_keeps_the_optimum(pd, ctx):
