@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--plain-pairs", type=int, default=3, help="pairs timed through the one-pair path")
     ap.add_argument("--threads", type=int, default=0, help="host threads preprocessing pairs (0 = library default)")
     ap.add_argument("--warm-pairs", type=int, default=2, help="pairs timed with the learned warm start (0 = skip)")
-    ap.add_argument("--train-pairs", type=int, default=16, help="seeded pairs the warm-start network is trained on")
+    ap.add_argument("--train-pairs", type=int, default=48, help="seeded pairs the warm-start network is trained on")
     ap.add_argument("--train-epochs", type=int, default=30)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -503,17 +503,18 @@ def run_ours(args):
     # ---- warm start (one pair per call, on pool pairs the network has not
     # seen): cold start; the potentials of a coarse solve of the same pair
     # (warm_start 4); those corrected by the network (1), trained on cold
-    # solves of other seeded pairs of 20k-100k points; and, as the ceiling,
+    # solves of other seeded pairs of 20k-60k points (the last eighth held
+    # out to pick the epoch); and, as the ceiling,
     # the exact potentials (2, timed without the cold solve it needs) -------
     warm = None
     if args.warm_pairs > 0:
         import numpy as np
         from paper_2110_14734_gb300 import synth as _s
         rng = np.random.default_rng(77)
-        sizes = [int(x) for x in rng.integers(20000, args.n + 1, args.train_pairs)]
+        sizes = [int(x) for x in rng.integers(20000, min(60000, args.n) + 1, args.train_pairs)]
         trA = [torch.from_numpy(_s.lowerstar_u8(k, 40000 + 2 * t)).to(dev) for t, k in enumerate(sizes)]
         trB = [torch.from_numpy(_s.lowerstar_u8(k, 40001 + 2 * t)).to(dev) for t, k in enumerate(sizes)]
-        st = pdw1.pd_ws_train(ctx, trA, trB, args.eps, epochs=args.train_epochs, lr=1e-3, seed=1)
+        st = pdw1.pd_ws_train(ctx, trA, trB, args.eps, epochs=args.train_epochs, lr=3e-4, seed=1)
         del trA, trB
         rows = []
         for q in range(args.warm_pairs):
@@ -546,6 +547,8 @@ def run_ours(args):
                 "same_optimum": same, "train_pairs": st["pairs"], "train_rows": st["rows"],
                 "train_points_per_diagram": [min(sizes), max(sizes)], "train_epochs": args.train_epochs,
                 "train_loss_first": st["loss_first"], "train_loss_last": st["loss_last"],
+                "heldout_pairs": st["val_pairs"], "heldout_mse_no_correction": st["val_loss_zero"],
+                "heldout_mse": st["val_loss"], "best_epoch": st["best_epoch"],
                 "train_s": (st["collect_ms"] + st["train_ms"]) / 1000.0}
 
     # ---- end to end through the C ABI with pinned host buffers -------------
