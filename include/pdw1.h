@@ -121,6 +121,8 @@ typedef struct {
     int64_t diag_tau;       /* >= 0 quanta, < 2^30 */
     int32_t warm_cells;     /* warm_start 1 and 4: coarse cells along the longer side of the nodes'
                                bounding box (0 = 64; at most 4096) */
+    int32_t nn_wave0;       /* pd_nn_search: pairs of its first wave; later waves double up to
+                               batch_slots (0 = 16 with pruning, batch_slots without) */
 } pd_opts;
 
 void pd_opts_default(pd_opts* opts);

@@ -55,16 +55,24 @@ pd_status cuda_fail(Ctx* c, cudaError_t e, const char* where) {
 void* buf(Ctx* c, Buf id, size_t bytes) {
     if (bytes == 0) bytes = 1;
     if (c->bytes[id] >= bytes) return c->ptr[id];
-    size_t want = bytes + bytes / 8;
-    if (c->cap && c->held - c->bytes[id] + want > c->cap) {
+    // growth slack: an eighth, or a half where a grow would be deferred
+    size_t want = bytes + (c->defer_free ? bytes / 2 : bytes / 8);
+    if (c->cap && c->held + c->retired_bytes - c->bytes[id] + want > c->cap) {
         want = bytes;
-        if (c->held - c->bytes[id] + want > c->cap) {
+        if (c->held + c->retired_bytes - c->bytes[id] + want > c->cap) {
             c->err = "device memory cap of the context reached";
             return nullptr;
         }
     }
     if (c->ptr[id]) {
-        cudaFree(c->ptr[id]);
+        if (c->defer_free) {
+            // cudaFree waits for the whole device: a context that works beside
+            // other threads' kernels keeps the old block until ctx_release
+            c->retired.push_back(c->ptr[id]);
+            c->retired_bytes += c->bytes[id];
+        } else {
+            cudaFree(c->ptr[id]);
+        }
         c->held -= c->bytes[id];
         c->ptr[id] = nullptr;
         c->bytes[id] = 0;
@@ -176,6 +184,7 @@ extern "C" void pd_opts_default(pd_opts* o) {
     o->diag_kappa = 1;
     o->diag_tau = 0;
     o->warm_cells = 0;
+    o->nn_wave0 = 0;
 }
 
 namespace pd {
@@ -213,9 +222,19 @@ static void wave_free(Ctx* c) {
     c->wave_pin = nullptr;
 }
 
+// Frees the blocks a deferring context retired (and its helpers' ones).
+void ctx_release(Ctx* c) {
+    if (!c) return;
+    for (void* p : c->retired) cudaFree(p);
+    c->retired.clear();
+    c->retired_bytes = 0;
+    ctx_release(c->coarse);
+}
+
 void ctx_free(Ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
+    ctx_release(c);
     wave_free(c);
     ctx_free(c->coarse);
     c->coarse = nullptr;
@@ -811,6 +830,7 @@ pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t 
         Ctx* sl = ctx_new(c->device, c->cap);
         if (!sl) return fail(c, PD_ECUDA, "cannot create the buffers of a batch slot");
         sl->parent = c;
+        sl->defer_free = true;
         c->slots.push_back(sl);
     }
     while ((int)c->workers.size() < nthr) {
@@ -822,6 +842,7 @@ pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t 
             return fail(c, PD_ECUDA, "cannot create a batch worker stream");
         }
         wk->parent = c;
+        wk->defer_free = true;
         c->workers.push_back(wk);
     }
     for (Ctx* wk : c->workers) wk->mlp_owner = c;  // predictions use this context's network
@@ -965,6 +986,10 @@ pd_status batch_solve(Ctx* c, const pd_diagram* A, const pd_diagram* B, int64_t 
         }
     }
     cudaEventDestroy(ready);
+    // the blocks the slots and workers outgrew: freed now that their work is done
+    cudaStreamSynchronize(st);
+    for (Ctx* sl : c->slots) ctx_release(sl);
+    for (Ctx* wk : c->workers) ctx_release(wk);
     return status;
 }
 

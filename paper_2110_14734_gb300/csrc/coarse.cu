@@ -99,7 +99,10 @@ __global__ void k_ctransform_potential(const int32_t* __restrict__ S, const int3
 static Ctx* coarse_ctx(Ctx* c) {
     if (!c->coarse) {
         c->coarse = ctx_new(c->device, c->cap);
-        if (c->coarse) c->coarse->parent = c->parent ? c->parent : c;
+        if (c->coarse) {
+            c->coarse->parent = c->parent ? c->parent : c;
+            c->coarse->defer_free = c->defer_free;
+        }
     }
     return c->coarse;
 }

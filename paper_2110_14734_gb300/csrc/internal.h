@@ -49,6 +49,9 @@ struct Ctx {
     int device = 0;
     size_t cap = 0;
     size_t held = 0;
+    bool defer_free = false;         // retire grown-out blocks instead of freeing them (batch threads)
+    std::vector<void*> retired;      // blocks waiting for ctx_release
+    size_t retired_bytes = 0;
     std::string err;
     void* ptr[B_COUNT] = {};
     size_t bytes[B_COUNT] = {};
@@ -96,6 +99,7 @@ struct Ctx {
 
 Ctx* ctx_new(int device, size_t cap);  // nullptr on failure
 void ctx_free(Ctx* c);
+void ctx_release(Ctx* c);  // frees the blocks a deferring context retired
 
 // Returns a device buffer of at least `bytes` bytes (contents undefined), or
 // nullptr (ctx->err set) when allocation fails or the cap is reached.

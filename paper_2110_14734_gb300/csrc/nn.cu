@@ -302,6 +302,7 @@ extern "C" pd_status pd_nn_search(pd_ctx* cx, pd_diagram query, double eps, cons
     if (opts) o = *opts;
     if (!(eps > 0.0) && o.s_override <= 0) return fail(c, PD_EINVAL, "eps must be > 0 (or set s_override)");
     if (o.solver == 1) return fail(c, PD_EINVAL, "the search runs the network simplex only");
+    if (o.nn_wave0 < 0) return fail(c, PD_EINVAL, "nn_wave0 must be >= 0");
     PD_TRY(check_diag_cost(c, o));
     PD_TRY(check_diag(c, query));
     const int64_t n_db = (int64_t)c->db.size();
@@ -412,7 +413,11 @@ extern "C" pd_status pd_nn_search(pd_ctx* cx, pd_diagram query, double eps, cons
     std::vector<int64_t> order((size_t)n_db), opt((size_t)n_db, -1);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return lb[(size_t)x] < lb[(size_t)y]; });
+    // waves grow from nn_wave0 pairs, doubling up to the batch size: the pairs
+    // of smallest bound are solved first, so their optimum can prune the rest
+    // before a wide wave is spent on pairs it would have ruled out
     const int64_t W = o.batch_slots > 0 ? o.batch_slots : 2 * std::max(c->sm_count, 1);
+    int64_t wsize = std::min<int64_t>(W, o.nn_wave0 > 0 ? o.nn_wave0 : (o.nn_prune != 0 ? 16 : W));
     int64_t best = INT64_MAX, best_i = -1, pos = 0;
     std::vector<pd_diagram> qa, db;
     std::vector<pd_result> res;
@@ -422,7 +427,7 @@ extern "C" pd_status pd_nn_search(pd_ctx* cx, pd_diagram query, double eps, cons
         qa.clear();
         db.clear();
         std::vector<int64_t> wave;
-        while (pos < n_db && (int64_t)wave.size() < W) {
+        while (pos < n_db && (int64_t)wave.size() < wsize) {
             const int64_t i = order[(size_t)pos];
             if (o.nn_prune != 0 && lb[(size_t)i] > best) break;
             wave.push_back(i);
@@ -433,6 +438,7 @@ extern "C" pd_status pd_nn_search(pd_ctx* cx, pd_diagram query, double eps, cons
         res.assign(wave.size(), pd_result{});
         PD_TRY(batch_solve(c, qa.data(), db.data(), (int64_t)wave.size(), eps, o, res.data(), st));
         r.waves++;
+        wsize = std::min<int64_t>(W, 2 * wsize);
         for (size_t q = 0; q < wave.size(); q++) {
             const int64_t i = wave[q], v = res[q].opt_quanta;
             opt[(size_t)i] = v;

@@ -39,7 +39,7 @@ class pd_opts(C.Structure):
                 ("batch_threads", C.c_int32),
                 ("nn_prune", C.c_int32), ("warm_start", C.c_int32), ("ns_walk", C.c_int32),
                 ("tree", C.c_int32), ("diag_kappa", C.c_int32), ("diag_tau", C.c_int64),
-                ("warm_cells", C.c_int32)]
+                ("warm_cells", C.c_int32), ("nn_wave0", C.c_int32)]
 
 
 class pd_nodes(C.Structure):

@@ -51,6 +51,16 @@ def test_nn_matches_oracle_with_and_without_pruning(pd, ctx):
     assert pr["solved"] + pr["pruned"] == len(db)
     assert all(o_p in (-1, o) for o_p, o in zip(pr["opt"], opts))
     assert pr["lb"] == full["lb"]
+    # growing waves from 1 and 3 pairs (and the default 16, above 20 pairs
+    # here: one wave) reach the same answer; a pair is skipped only when its
+    # bound exceeds an optimum already found
+    for w0 in (1, 3):
+        g = pd.pd_nn_search(ctx, _cuda(q), eps, pd.opts(nn_wave0=w0, batch_slots=8))
+        assert g["nn_index"] == idx and g["nn_opt_quanta"] == opts[idx]
+        assert all(o_p in (-1, o) for o_p, o in zip(g["opt"], opts))
+        assert all(opts[i] == g["opt"][i] or g["lb"][i] > opts[idx] for i in range(len(db)))
+    with pytest.raises(pd.PDError):
+        pd.pd_nn_search(ctx, _cuda(q), eps, pd.opts(nn_wave0=-1))
 
 
 def test_nn_duplicate_of_the_query_wins_at_its_lowest_index(pd, ctx):
