@@ -95,7 +95,10 @@ typedef struct {
     int32_t batch_threads;  /* pd_w1_approx_batch: host threads preprocessing pairs (0 = 8) */
     int32_t nn_prune;       /* pd_nn_search: 1 = skip pairs whose lower bound exceeds the best optimum
                                (default); 0 = solve every pair */
-    int32_t warm_start;     /* network simplex on the transportation form: 0 = cold start (default);
+    int32_t warm_start;     /* network simplex on the transportation form: -1 = automatic (default):
+                               4 for instances of at least 4,096 transportation nodes in pd_w1_approx
+                               and pd_nn_search, else 0; pd_w1_approx_batch starts cold;
+                               0 = cold start;
                                1 = start from the coarse solve's potentials (as 4) corrected by the
                                context's network (pd_ws_train / pd_ws_load); 2 = start from the exact
                                potentials of a

@@ -180,6 +180,7 @@ extern "C" void pd_opts_default(pd_opts* o) {
     o->ns_transport = 1;
     o->ns_smem = 1;
     o->nn_prune = 1;
+    o->warm_start = -1;
     o->ns_walk = -1;
     o->diag_kappa = 1;
     o->diag_tau = 0;
@@ -574,6 +575,9 @@ static void fill_result(const Front& f, const SolveStats& ss, pd_result* out) {
 // The warm start's greedy takes all arcs between the still unbalanced nodes
 // at once when there are at most this many (before that, rounds of top-k).
 constexpr int64_t WARM_MAX_RESIDUAL = int64_t(1) << 18;
+// warm_start -1: transportation instances of at least this many nodes start
+// from the coarse solve (below it the cold start is about as fast)
+constexpr int64_t WARM_AUTO_NODES = 4096;
 
 static float elapsed_ms(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -591,10 +595,15 @@ struct WarmStats {
 // (3), then the start tree.  `c` does the work; the instance's buffers
 // belong to `tc` (the same context on the one-pair path, the pair's slot in a
 // batch).  *used: the start tree was installed.
-static pd_status warm_start(Ctx* c, Ctx* tc, const Front& f, W1Prep* w, const pd_opts& o, bool* used,
+static pd_status warm_start(Ctx* c, Ctx* tc, const Front& f, W1Prep* w, const pd_opts& oi, bool* used,
                             WarmStats* ws, cudaStream_t st) {
     *used = false;
-    if (!w->ns.ready || o.warm_start == 0) return PD_OK;
+    if (!w->ns.ready || oi.warm_start == 0) return PD_OK;
+    pd_opts o = oi;
+    if (o.warm_start == -1) {  // automatic: the coarse solve's start for large instances
+        if (w->nt < WARM_AUTO_NODES) return PD_OK;
+        o.warm_start = 4;
+    }
     const auto t0 = std::chrono::steady_clock::now();
     std::vector<float> pf;
     std::vector<double> p;
@@ -622,7 +631,7 @@ static pd_status warm_start(Ctx* c, Ctx* tc, const Front& f, W1Prep* w, const pd
         PD_TRY(ws_coarse_potentials(c, f, *w, o, &p, st));
         if (p.empty()) return PD_OK;  // nothing to solve at the coarse level: cold start
     } else {
-        return fail(c, PD_EINVAL, "warm_start must be 0 .. 4");
+        return fail(c, PD_EINVAL, "warm_start must be -1 .. 4");
     }
     if (p.empty()) p.assign(pf.begin(), pf.end());
     ws->coarse_pivots = c->last_coarse_pivots;
@@ -788,8 +797,8 @@ static pd_status batch_prepare(Ctx* work, Ctx* slot, const pd_diagram& A, const 
     if (transport)
         PD_TRY(ns_prepare_w1(slot, bp->f.nodes, bp->f.net.n_arcs, bp->f.h.FB - bp->f.h.FA, o, &bp->w, st));
     if (bp->w.ns.ready) {
-        if (o.warm_start != 0 && o.warm_start != 1 && o.warm_start != 4)
-            return fail(work, PD_EINVAL, "the batched solve takes warm_start 0, 1 or 4");
+        if (o.warm_start != 0 && o.warm_start != 1 && o.warm_start != 4 && o.warm_start != -1)
+            return fail(work, PD_EINVAL, "the batched solve takes warm_start -1, 0, 1 or 4");
         PD_TRY(warm_start(work, slot, bp->f, &bp->w, o, &bp->warm, &bp->wst, st));
         PD_TRY(persist_for_certificate(slot, bp->f, bp, st));
     } else {
@@ -812,6 +821,10 @@ extern "C" pd_status pd_w1_approx_batch(pd_ctx* c, const pd_diagram* A, const pd
     if (count < 0 || (count > 0 && (!A || !B || !out))) return fail(c, PD_EINVAL, "bad batch arguments");
     if (count == 0) return PD_OK;
     pd_opts o = resolve_opts(opts);
+    // automatic warm start: cold here -- with a wave of pairs per launch the
+    // per-pair coarse solves and start trees on the host cost more than the
+    // pivots they save
+    if (o.warm_start == -1) o.warm_start = 0;
     return pd::batch_solve(c, A, B, count, eps, o, out, (cudaStream_t)stream);
 }
 

@@ -93,7 +93,8 @@ struct Tree {
 constexpr int NS_LMAX = 512;     // half-cycle entries kept in shared memory
 constexpr int NS_PR = 8;         // cost-matrix loads in flight per thread while pricing
 constexpr int NS_SEGSM = 65;     // re-hang segments kept in shared memory (paths shorter than 32)
-constexpr int NS_REGS = 9;       // shared-memory layout: at most 9 * 1024 nodes (re-hang buffered in registers)
+constexpr int NS_REGS = 9;       // re-hang buffered in registers when it moves at most 9 * 1024 positions
+constexpr int NS_SCAN_IT = 16;   // shared-memory layouts: at most 16 * 1024 nodes (ballot words per warp)
 
 template <typename IX>
 __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
@@ -109,7 +110,7 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
     __shared__ int32_t s_wkey[2][32];    // per-warp pricing minima (clamped), double-buffered
     __shared__ uint32_t s_widx[2][32];
     __shared__ int64_t s_wval[2][32];    // exact reduced cost of each warp's winner
-    __shared__ uint32_t s_mask[2][32][NS_REGS];  // path discovery ballots, i-side and j-side
+    __shared__ uint32_t s_mask[2][32][NS_SCAN_IT];  // path discovery ballots, i-side and j-side
     __shared__ int32_t s_cnt[2][32];
     __shared__ int64_t s_dpi;
     __shared__ int32_t s_go, s_status, s_scan;
@@ -314,7 +315,7 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
                 // (so matches come out ordered from the apex down); ballots are kept
                 // for the second pass, which writes each match at its rank.
                 const int32_t pi_ = T.ps[i], pj = T.ps[j];
-                const int32_t C = (((N1 + 31) / 32) + 31) & ~31;  // positions per warp, <= 32 * NS_REGS
+                const int32_t C = (((N1 + 31) / 32) + 31) & ~31;  // positions per warp, <= 32 * NS_SCAN_IT
                 const int32_t x0 = wid * C;
                 // an ancestor's position is at most the descendant's: no warp looks
                 // past max(pos(i), pos(j))
@@ -626,7 +627,7 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
             // new order of [lo, hi) computed from the old one, then written; the
             // next pricing reads only potentials (final before the barrier), and
             // every later reader of the order passes a pricing barrier first
-            if constexpr (sizeof(IX) == 2) {
+            if (sizeof(IX) == 2 && hi - lo <= NS_REGS * NS_THREADS) {
                 int32_t vals[NS_REGS];
 #pragma unroll
                 for (int r2 = 0; r2 < NS_REGS; r2++) {
@@ -642,7 +643,7 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
                         T.ps[vals[r2]] = (IX)x;
                     }
                 }
-            } else {
+            } else {  // a longer move: the new order goes through global memory
                 for (int32_t x = lo + tid; x < hi; x += NS_THREADS) I.tmp[x] = new_node(x);
                 __syncthreads();
                 for (int32_t x = lo + tid; x < hi; x += NS_THREADS) {
@@ -658,8 +659,9 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
     for (int32_t v = tid; v < N1; v += NS_THREADS) {
         G.pi[v] = T.pi[v];
         G.pred[v] = T.pred[v];
-        G.flow[v] = T.flow(v);
-        G.up[v] = T.up(v) ? 1 : 0;
+        const uint32_t w = T.fu[v];  // read once: outside the compact layout it is G.flow's own word
+        G.flow[v] = (int32_t)(w & 0x7fffffffu);
+        G.up[v] = (w >> 31) ? 1 : 0;
         G.parent[v] = T.parent(v);
         G.size[v] = (int32_t)T.sz[v];
         G.pos[v] = (int32_t)T.ps[v];
@@ -696,15 +698,23 @@ __device__ __forceinline__ void ns_instance(NSInst& G) {
     NSInst I = G;
     const int32_t N1 = I.n + 1;
     if (I.smem_nodes) {
+        // 1: every node array in shared memory (24 B a node); 2: pred and the
+        // packed flow in global memory (only the pivot's paths touch them), the
+        // arrays every pivot scans in shared memory (16 B a node)
         extern __shared__ __align__(16) unsigned char dyn[];
         unsigned char* p = dyn;
         Tree<uint16_t> T;
         T.pi = (int64_t*)p;
         p += sizeof(int64_t) * N1;
-        T.pred = (int32_t*)p;
-        p += sizeof(int32_t) * N1;
-        T.fu = (uint32_t*)p;
-        p += sizeof(uint32_t) * N1;
+        if (I.smem_nodes == 1) {
+            T.pred = (int32_t*)p;
+            p += sizeof(int32_t) * N1;
+            T.fu = (uint32_t*)p;
+            p += sizeof(uint32_t) * N1;
+        } else {
+            T.pred = I.pred;
+            T.fu = (uint32_t*)I.flow;  // packed while solving, unpacked on exit
+        }
         T.par = (uint16_t*)p;
         p += sizeof(uint16_t) * N1;
         T.sz = (uint16_t*)p;
@@ -742,17 +752,24 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, const 
     }
 }
 
-// Bytes of dynamic shared memory for the compact node arrays of N1 nodes.
-size_t ns_smem_bytes(int64_t N1) { return (size_t)N1 * (8 + 4 + 4 + 2 + 2 + 2 + 2) + 64; }
+// Bytes of dynamic shared memory for the node arrays of N1 nodes in layout
+// 1 (all of them) or 2 (all but pred and the packed flow).
+size_t ns_smem_bytes(int64_t N1, int layout) {
+    return (size_t)N1 * (layout == 2 ? 8 + 2 + 2 + 2 + 2 : 8 + 4 + 4 + 2 + 2 + 2 + 2) + 64;
+}
 
-bool ns_smem_fits(int64_t N1, int max_optin) {
-    if (N1 > (int64_t)NS_REGS * NS_THREADS) return false;
+// The shared-memory layout N1 nodes can use: 1, else 2, else 0 (global).
+// Both keep 16-bit node indices and at most NS_SCAN_IT * 1024 nodes.
+int ns_smem_layout(int64_t N1, int max_optin) {
+    if (N1 > (int64_t)NS_SCAN_IT * NS_THREADS) return 0;
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, k_netsimplex) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return fa.sharedSizeBytes + ns_smem_bytes(N1) <= (size_t)max_optin;
+    for (int layout = 1; layout <= 2; layout++)
+        if (fa.sharedSizeBytes + ns_smem_bytes(N1, layout) <= (size_t)max_optin) return layout;
+    return 0;
 }
 
 // The dynamic shared memory limit of a kernel is one attribute per device for
@@ -775,7 +792,7 @@ cudaError_t ns_kernel_setup() {
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, k_netsimplex);
     if (e != cudaSuccess) return e;
-    const size_t most = std::min((size_t)max_optin - fa.sharedSizeBytes, ns_smem_bytes((int64_t)NS_REGS * NS_THREADS));
+    const size_t most = (size_t)max_optin - fa.sharedSizeBytes;
     e = cudaFuncSetAttribute(k_netsimplex, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     if (e != cudaSuccess) return e;
     done[dev] = true;
@@ -865,8 +882,8 @@ pd_status ns_prepare_arcs(Ctx* c, int32_t n, int64_t m, int64_t mst, int64_t nS,
     h.big = N1 * (cmax + 1) + 1;
     int max_optin = 0;
     PD_TRY_CUDA(c, cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    h.smem_nodes = (o.ns_smem != 0 && ns_smem_fits(N1, max_optin)) ? 1 : 0;
-    p->smem = h.smem_nodes ? ns_smem_bytes(N1) : 0;
+    h.smem_nodes = o.ns_smem != 0 ? ns_smem_layout(N1, max_optin) : 0;
+    p->smem = h.smem_nodes ? ns_smem_bytes(N1, h.smem_nodes) : 0;
     p->ready = true;
     return PD_OK;
 }

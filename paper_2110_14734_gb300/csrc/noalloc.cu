@@ -156,9 +156,8 @@ extern "C" pd_status pd_mcf_solve_noalloc(const pd_network* net, int64_t* opt_ou
     int dev = 0, max_optin = 0;
     NA_TRY(cudaGetDevice(&dev));
     NA_TRY(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    size_t smem = ns_smem_bytes(N1);
-    h.smem_nodes = ns_smem_fits(N1, max_optin) ? 1 : 0;
-    if (!h.smem_nodes) smem = 0;
+    h.smem_nodes = ns_smem_layout(N1, max_optin);
+    const size_t smem = h.smem_nodes ? ns_smem_bytes(N1, h.smem_nodes) : 0;
     NA_TRY(ns_kernel_setup());
     NA_TRY(cudaMemcpyAsync(dinst, &h, sizeof(NSInst), cudaMemcpyHostToDevice, st));
     int32_t* order = (int32_t*)(flags + 4);  // zeroed with the flags: order = {0}, next = 0

@@ -162,3 +162,19 @@ def test_coarse_start_cells_keep_the_optimum(pd, ctx, mode, cells):
     assert warm["warm_used"] == 1 and warm["verified"] == 1 and warm["opt_quanta"] == exp
     with pytest.raises(pd.PDError):
         pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05, pd.opts(warm_start=4, warm_cells=5000))
+
+
+def test_automatic_warm_start(pd, ctx):
+    """The default warm_start (-1): pd_w1_approx starts from the coarse solve
+    on an instance of at least 4,096 transportation nodes and cold below it;
+    the batched solve starts cold; every optimum is the oracle's."""
+    A, B = synth.lowerstar_u8(100000, 1004), synth.lowerstar_u8(100000, 1005)
+    exp = oracle.w1_approx(A, B, "u8", eps=0.05)["opt"]
+    auto = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05)
+    cold = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05, pd.opts(warm_start=0))
+    assert auto["opt_quanta"] == cold["opt_quanta"] == exp
+    assert auto["warm_used"] == 1 and cold["warm_used"] == 0 and auto["pivots"] < cold["pivots"]
+    small = pd.pd_w1_approx(ctx, _cuda(synth.uniform_exp(2000, 1000)), _cuda(synth.uniform_exp(2000, 1001)), 0.1)
+    assert small["warm_used"] == 0
+    wb = pd.pd_w1_approx_batch(ctx, [_cuda(A)], [_cuda(B)], 0.05)
+    assert wb[0]["warm_used"] == 0 and wb[0]["opt_quanta"] == exp
