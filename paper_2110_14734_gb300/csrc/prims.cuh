@@ -123,6 +123,35 @@ __global__ void k_tile_scan(const T* in, T* out, int64_t n, const T* __restrict_
 
 inline int64_t scan_tiles(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE; }
 
+// One block of 1024 threads scans in[0..n) into out (exclusive; in == out
+// allowed: every element is read before the barrier that precedes its
+// write), 4 consecutive elements a thread per step.  For short arrays, where
+// the three-launch scan is all launch overhead.
+constexpr int64_t SCAN_SMALL_MAX = int64_t(1) << 14;
+template <typename T>
+__global__ void __launch_bounds__(1024) k_scan_small(const T* in, T* out, int64_t n, T* total) {
+    T carry = 0;
+    for (int64_t base = 0; base < n; base += 4 * (int64_t)blockDim.x) {
+        const int64_t i0 = base + 4 * (int64_t)threadIdx.x;
+        T v[4];
+        T s = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            v[j] = i0 + j < n ? in[i0 + j] : T(0);
+            s += v[j];
+        }
+        T tot;
+        T ex = block_excl_scan(s, &tot) + carry;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (i0 + j < n) out[i0 + j] = ex;
+            ex += v[j];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
 // out[i] = sum of in[0..i-1]; in == out allowed.  part: scan_tiles(n) + 1
 // elements of scratch; *total_dev (device, may be NULL) gets the sum.
 template <typename T>
@@ -130,6 +159,10 @@ cudaError_t exclusive_scan(const T* in, T* out, int64_t n, T* part, T* total_dev
     if (n <= 0) {
         if (total_dev) return cudaMemsetAsync(total_dev, 0, sizeof(T), st);
         return cudaSuccess;
+    }
+    if (n <= SCAN_SMALL_MAX) {
+        k_scan_small<T><<<1, 1024, 0, st>>>(in, out, n, total_dev); pd::count_launch();
+        return cudaGetLastError();
     }
     int64_t nb = scan_tiles(n);
     k_tile_sum<T><<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, part); pd::count_launch();

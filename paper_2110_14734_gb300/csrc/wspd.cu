@@ -356,6 +356,105 @@ __global__ void k_ws_count_split(const int2* __restrict__ F, int64_t nf, const i
     }
 }
 
+// Count-only, three levels per launch: the pair F[i] is tested, its two
+// children, then their up to four children, all in registers (the same test
+// and split rule as k_ws_count_split); separated pairs are counted and the up
+// to eight great-grandchildren go to the next frontier at slots taken with
+// block-aggregated atomics.  Equivalent to three launches of
+// k_ws_count_split, with a third of the launches, host syncs and frontier
+// traffic.  Slots at or above `cap` are not written and lv[2] records it (with
+// cap = 8 nf it cannot happen).
+// lv[0] += separated pairs, lv[1] = size of the next frontier.
+PD_D void ws_split(const TNode& u, const TNode& v, int2 p, int2* c0, int2* c1) {
+    if (max_side(u) > max_side(v)) {
+        *c0 = make_int2(u.l, p.y);
+        *c1 = make_int2(u.r, p.y);
+    } else {
+        *c0 = make_int2(p.x, v.l);
+        *c1 = make_int2(p.x, v.r);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ws_count_split3(const int2* __restrict__ F, int64_t nf,
+                                                         const int32_t* __restrict__ X,
+                                                         const int32_t* __restrict__ Y, const int4* __restrict__ bb,
+                                                         const int32_t* __restrict__ rep,
+                                                         const int32_t* __restrict__ left,
+                                                         const int32_t* __restrict__ right, int64_t s,
+                                                         int2* __restrict__ Fn, unsigned long long cap,
+                                                         unsigned long long* __restrict__ lv) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned cnt = 0;
+    int2 L1[2], L2[4], L3[8];
+    unsigned m1 = 0, m2 = 0, m3 = 0;  // which entries of each level are live
+    if (i < nf) {
+        const int2 p = F[i];
+        const TNode u = load_tnode(p.x, X, Y, bb, rep, left, right);
+        const TNode v = load_tnode(p.y, X, Y, bb, rep, left, right);
+        if (well_separated(u, v, s)) cnt++;
+        else {
+            ws_split(u, v, p, &L1[0], &L1[1]);
+            m1 = 3u;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+        if (m1 >> q & 1u) {
+            const TNode u = load_tnode(L1[q].x, X, Y, bb, rep, left, right);
+            const TNode v = load_tnode(L1[q].y, X, Y, bb, rep, left, right);
+            if (well_separated(u, v, s)) cnt++;
+            else {
+                ws_split(u, v, L1[q], &L2[2 * q], &L2[2 * q + 1]);
+                m2 |= 3u << (2 * q);
+            }
+        }
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        if (m2 >> q & 1u) {
+            const TNode u = load_tnode(L2[q].x, X, Y, bb, rep, left, right);
+            const TNode v = load_tnode(L2[q].y, X, Y, bb, rep, left, right);
+            if (well_separated(u, v, s)) cnt++;
+            else {
+                ws_split(u, v, L2[q], &L3[2 * q], &L3[2 * q + 1]);
+                m3 |= 3u << (2 * q);
+            }
+        }
+    // counts and slots: warp sums and prefixes, then one atomic per block
+    __shared__ unsigned s_ws[32], s_sp[32];
+    __shared__ unsigned long long s_base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const unsigned k = __popc(m3);
+    unsigned incl = k, wc = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    for (int o = 16; o > 0; o >>= 1) wc += __shfl_xor_sync(0xffffffffu, wc, o);
+    if (lane == 31) s_sp[wid] = incl;
+    if (lane == 0) s_ws[wid] = wc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long tw = 0, ts = 0;
+        for (int w = 0; w < nw; w++) {
+            tw += s_ws[w];
+            const unsigned c = s_sp[w];
+            s_sp[w] = (unsigned)ts;  // exclusive prefix of the warps' outputs
+            ts += c;
+        }
+        if (tw) atomicAdd(&lv[0], tw);
+        s_base = ts ? atomicAdd(&lv[1], ts) : 0ull;
+        if (ts && s_base + ts > cap) atomicOr(&lv[2], 1ull);
+    }
+    __syncthreads();
+    unsigned long long slot = s_base + s_sp[wid] + (incl - k);
+#pragma unroll
+    for (int q = 0; q < 8; q++)
+        if (m3 >> q & 1u) {
+            if (slot < cap) Fn[slot] = L3[q];
+            slot++;
+        }
+}
+
 // Diagonal arcs: u -> ā if u holds A mass, b̄ -> u if u holds B mass, and
 // b̄ -> ā; absent arcs become the all-ones key, which sorts last.
 __global__ void k_diag_arcs(int64_t N, const int64_t* __restrict__ cntA, const int64_t* __restrict__ cntB, int hb,
@@ -546,15 +645,31 @@ pd_status stage_network(Ctx* c, const pd_nodes& nodes, int64_t s, pd_network* ou
     uint64_t* arcs = nullptr;
     int fb = 0;
     int64_t* h = c->h_small;
+    // count only: three levels per launch into a next frontier of 8 nf pairs
+    // (at most 2^32, and only if that much memory can be had), else one level
+    // into 2 nf
     while (count_only && nf > 0) {
         unsigned long long* lv = cnts + 12;
-        int2* Fn = bufT<int2>(c, fb ? B_F0 : B_F1, 2 * nf);
-        if (!Fn) return PD_ENOMEM;
-        PD_TRY_CUDA(c, cudaMemsetAsync(lv, 0, 2 * sizeof(unsigned long long), st));
-        k_ws_count_split<<<grid_for(nf, 256), 256, 0, st>>>(F, nf, nodes.X, nodes.Y, bb, rep, left, right, s, Fn, lv); pd::count_launch();
+        const Buf nid = fb ? B_F0 : B_F1;
+        int2* Fn = nullptr;
+        if (8 * nf <= (int64_t(1) << 32)) {
+            Fn = bufT<int2>(c, nid, 8 * nf);
+            if (!Fn) c->err.clear();
+        }
+        PD_TRY_CUDA(c, cudaMemsetAsync(lv, 0, 3 * sizeof(unsigned long long), st));
+        if (Fn) {
+            k_ws_count_split3<<<grid_for(nf, 256), 256, 0, st>>>(F, nf, nodes.X, nodes.Y, bb, rep, left, right, s, Fn,
+                                                                 (unsigned long long)(8 * nf), lv); pd::count_launch();
+        } else {
+            Fn = bufT<int2>(c, nid, 2 * nf);
+            if (!Fn) return PD_ENOMEM;
+            k_ws_count_split<<<grid_for(nf, 256), 256, 0, st>>>(F, nf, nodes.X, nodes.Y, bb, rep, left, right, s, Fn,
+                                                                lv); pd::count_launch();
+        }
         PD_TRY_CUDA(c, cudaGetLastError());
-        PD_TRY_CUDA(c, cudaMemcpyAsync(h, lv, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        PD_TRY_CUDA(c, cudaMemcpyAsync(h, lv, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         PD_TRY_CUDA(c, cudaStreamSynchronize(st));
+        if (h[2]) return fail(c, PD_ECUDA, "WSPD count: frontier slots overflowed");  // cannot happen: 8 per pair
         narcs += 2 * h[0];
         nf = h[1];
         F = Fn;

@@ -79,7 +79,7 @@ def test_exact_potentials_start_keeps_the_optimum_and_saves_pivots(pd, ctx, name
         A, B, dt, eps = synth.uniform_exp(2000, 1000), synth.uniform_exp(2000, 1001), "f32", 0.1
     else:
         A, B, dt, eps = synth.lowerstar_u8(20000, 1000), synth.lowerstar_u8(20000, 1001), "u8", 0.05
-    cold = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), eps)
+    cold = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), eps, pd.opts(warm_start=0))
     warm = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), eps, pd.opts(warm_start=2))
     assert warm["warm_used"] == 1 and warm["verified"] == 1
     assert warm["opt_quanta"] == cold["opt_quanta"] == oracle.w1_approx(A, B, dt, eps=eps)["opt"]
@@ -106,7 +106,7 @@ def test_trained_network_start_keeps_the_optimum_and_reports_its_gain(pd, ctx):
     unseen = (synth.lowerstar_u8(20000, 5000), synth.lowerstar_u8(20000, 5001))
     gains = {}
     for name, (A, B) in (("seen", seen), ("unseen", unseen)):
-        cold = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05)
+        cold = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05, pd.opts(warm_start=0))
         coarse = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05, pd.opts(warm_start=4))
         warm = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05, pd.opts(warm_start=1))
         assert warm["opt_quanta"] == cold["opt_quanta"] == coarse["opt_quanta"] and warm["verified"] == 1
@@ -125,7 +125,7 @@ def test_trained_network_start_keeps_the_optimum_and_reports_its_gain(pd, ctx):
 
 def test_cost_greedy_start_keeps_the_optimum(pd, ctx):
     A, B = synth.lowerstar_u8(20000, 1000), synth.lowerstar_u8(20000, 1001)
-    cold = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05)
+    cold = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05, pd.opts(warm_start=0))
     z = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), 0.05, pd.opts(warm_start=3))
     assert z["warm_used"] == 1 and z["opt_quanta"] == cold["opt_quanta"] and z["verified"] == 1
 
@@ -143,7 +143,7 @@ def test_coarse_solve_start_keeps_the_optimum(pd, ctx, name):
     else:
         A, B, dt, eps = synth.mixture_f32(5000, 7), synth.mixture_f32(4000, 8), "f32", 0.1
     exp = oracle.w1_approx(A, B, dt, eps=eps)["opt"]
-    cold = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), eps)
+    cold = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), eps, pd.opts(warm_start=0))
     warm = pd.pd_w1_approx(ctx, _cuda(A), _cuda(B), eps, pd.opts(warm_start=4))
     assert warm["warm_used"] == 1 and warm["verified"] == 1
     assert warm["opt_quanta"] == cold["opt_quanta"] == exp
