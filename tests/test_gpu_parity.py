@@ -396,8 +396,9 @@ def test_w1_approx_full_size_lowerstar_100k(pd, ctx, eps):
 def test_w1_approx_continuous_mixture(pd, ctx, n):
     """Continuous float32 coordinates with few duplicates (birth U[0,1],
     persistence 0.95 Exp(0.01) + 0.05 U[0, 0.5]) at eps = 0.1: about 2n
-    condensed nodes, more than the shared-memory tree holds, so the simplex
-    keeps its tree in global memory; 10k points per diagram is the largest
+    condensed nodes, more than the all-shared-memory tree holds (the 5k pair
+    takes the layout with pred and flow in global memory, the 10k pair keeps
+    the whole tree in global memory); 10k points per diagram is the largest
     size of this shape the CPU oracle solves within a test's time.  At 5k
     the result is also checked against the exact FP64 W1 (the (1 +- eps) band
     of the approximation bound)."""
