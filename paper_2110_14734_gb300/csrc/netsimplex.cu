@@ -94,7 +94,6 @@ constexpr int NS_LMAX = 512;     // half-cycle entries kept in shared memory
 constexpr int NS_PR = 8;         // cost-matrix loads in flight per thread while pricing
 constexpr int NS_SEGSM = 65;     // re-hang segments kept in shared memory (paths shorter than 32)
 constexpr int NS_REGS = 9;       // re-hang buffered in registers when it moves at most 9 * 1024 positions
-constexpr int NS_SCAN_IT = 16;   // shared-memory layouts: at most 16 * 1024 nodes (ballot words per warp)
 
 template <typename IX>
 __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
@@ -110,7 +109,6 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
     __shared__ int32_t s_wkey[2][32];    // per-warp pricing minima (clamped), double-buffered
     __shared__ uint32_t s_widx[2][32];
     __shared__ int64_t s_wval[2][32];    // exact reduced cost of each warp's winner
-    __shared__ uint32_t s_mask[2][32][NS_SCAN_IT];  // path discovery ballots, i-side and j-side
     __shared__ int32_t s_cnt[2][32];
     __shared__ int64_t s_dpi;
     __shared__ int32_t s_go, s_status, s_scan;
@@ -312,17 +310,17 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
                 // whole CTA: a node is on i's side iff it is an ancestor of i (or i)
                 // and not of j, by the preorder test pos(v) <= pos(x) < pos(v) +
                 // size(v).  Each warp scans a contiguous range of preorder positions
-                // (so matches come out ordered from the apex down); ballots are kept
-                // for the second pass, which writes each match at its rank.
+                // (so matches come out ordered from the apex down) and counts its
+                // matches; the few warps with matches scan their range again and
+                // write each match at its rank.
                 const int32_t pi_ = T.ps[i], pj = T.ps[j];
-                const int32_t C = (((N1 + 31) / 32) + 31) & ~31;  // positions per warp, <= 32 * NS_SCAN_IT
+                const int32_t C = (((N1 + 31) / 32) + 31) & ~31;  // positions per warp
                 const int32_t x0 = wid * C;
                 // an ancestor's position is at most the descendant's: no warp looks
                 // past max(pos(i), pos(j))
                 const int32_t xmax = pi_ > pj ? pi_ : pj;
                 const int32_t iters = xmax < x0 ? 0 : min(C >> 5, ((xmax - x0) >> 5) + 1);
-                int32_t cI = 0, cJ = 0;
-                for (int32_t it = 0; it < iters; it++) {
+                auto sides = [&](int32_t it, uint32_t* bI, uint32_t* bJ) {
                     const int32_t x = x0 + (it << 5) + lane;
                     bool inI = false, inJ = false;
                     if (x < N1) {
@@ -331,11 +329,13 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
                         inI = ai && !aj;
                         inJ = aj && !ai;
                     }
-                    const uint32_t bI = __ballot_sync(FULL, inI), bJ = __ballot_sync(FULL, inJ);
-                    if (lane == 0) {
-                        s_mask[0][wid][it] = bI;
-                        s_mask[1][wid][it] = bJ;
-                    }
+                    *bI = __ballot_sync(FULL, inI);
+                    *bJ = __ballot_sync(FULL, inJ);
+                };
+                int32_t cI = 0, cJ = 0;
+                for (int32_t it = 0; it < iters; it++) {
+                    uint32_t bI, bJ;
+                    sides(it, &bI, &bJ);
                     cI += __popc(bI);
                     cJ += __popc(bJ);
                 }
@@ -349,9 +349,10 @@ __device__ __forceinline__ void ns_body(NSInst& G, NSInst& I, Tree<IX>& T) {
                 int32_t oJ = __reduce_add_sync(FULL, lane < wid ? mJ : 0);
                 const int32_t la = __reduce_add_sync(FULL, mI), lb = __reduce_add_sync(FULL, mJ);
                 const uint32_t below = (1u << lane) - 1u;
-                const int32_t iters2 = (s_cnt[0][wid] + s_cnt[1][wid]) > 0 ? iters : 0;  // warps without a match skip
+                const int32_t iters2 = (cI + cJ) > 0 ? iters : 0;  // warps without a match skip
                 for (int32_t it = 0; it < iters2; it++) {
-                    const uint32_t bI = s_mask[0][wid][it], bJ = s_mask[1][wid][it];
+                    uint32_t bI, bJ;
+                    sides(it, &bI, &bJ);
                     if ((bI | bJ) == 0) continue;
                     const int32_t x = x0 + (it << 5) + lane;
                     if ((bI >> lane) & 1u) {
@@ -700,12 +701,18 @@ __device__ __forceinline__ void ns_instance(NSInst& G) {
     if (I.smem_nodes) {
         // 1: every node array in shared memory (24 B a node); 2: pred and the
         // packed flow in global memory (only the pivot's paths touch them), the
-        // arrays every pivot scans in shared memory (16 B a node)
+        // arrays every pivot scans in shared memory (16 B a node); 3: the
+        // potentials in global memory too, the four 16-bit arrays (parent,
+        // size, position, order) in shared memory (8 B a node)
         extern __shared__ __align__(16) unsigned char dyn[];
         unsigned char* p = dyn;
         Tree<uint16_t> T;
-        T.pi = (int64_t*)p;
-        p += sizeof(int64_t) * N1;
+        if (I.smem_nodes == 3) {
+            T.pi = I.pi;
+        } else {
+            T.pi = (int64_t*)p;
+            p += sizeof(int64_t) * N1;
+        }
         if (I.smem_nodes == 1) {
             T.pred = (int32_t*)p;
             p += sizeof(int32_t) * N1;
@@ -753,21 +760,23 @@ __global__ void __launch_bounds__(NS_THREADS) k_netsimplex(NSInst* insts, const 
 }
 
 // Bytes of dynamic shared memory for the node arrays of N1 nodes in layout
-// 1 (all of them) or 2 (all but pred and the packed flow).
+// 1 (all of them), 2 (all but pred and the packed flow) or 3 (the four
+// 16-bit arrays).
 size_t ns_smem_bytes(int64_t N1, int layout) {
-    return (size_t)N1 * (layout == 2 ? 8 + 2 + 2 + 2 + 2 : 8 + 4 + 4 + 2 + 2 + 2 + 2) + 64;
+    const size_t per = layout == 1 ? 8 + 4 + 4 + 2 + 2 + 2 + 2 : layout == 2 ? 8 + 2 + 2 + 2 + 2 : 2 + 2 + 2 + 2;
+    return (size_t)N1 * per + 64;
 }
 
-// The shared-memory layout N1 nodes can use: 1, else 2, else 0 (global).
-// Both keep 16-bit node indices and at most NS_SCAN_IT * 1024 nodes.
+// The shared-memory layout N1 nodes can use: 1, else 2, else 3, else 0 (global).
+// All three keep 16-bit node indices.
 int ns_smem_layout(int64_t N1, int max_optin) {
-    if (N1 > (int64_t)NS_SCAN_IT * NS_THREADS) return 0;
+    if (N1 >= 65535) return 0;  // 16-bit indices, 65535 marks "no parent"
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, k_netsimplex) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    for (int layout = 1; layout <= 2; layout++)
+    for (int layout = 1; layout <= 3; layout++)
         if (fa.sharedSizeBytes + ns_smem_bytes(N1, layout) <= (size_t)max_optin) return layout;
     return 0;
 }

@@ -36,7 +36,7 @@ struct NSInst {
     int32_t* seg;      // 3 * (2n + 3) scratch: segment start, length, output offset
     int64_t block;     // pricing block (arcs)
     int64_t big;       // cost of the artificial arcs (more than any path cost)
-    int32_t smem_nodes; // node arrays: 1 all in shared memory, 2 all but pred / flow, 0 global
+    int32_t smem_nodes; // node arrays: 1 all in shared memory, 2 all but pred / flow, 3 the 16-bit ones, 0 global
     int32_t walk;      // shared-memory layout: longest half-cycle side followed by the two-lane walk (longer: the scan)
     int32_t init_tree;  // 1: pi, pred, parent, flow, up, ord, pos, size hold a strongly feasible start
     int32_t pad1;
@@ -55,14 +55,15 @@ struct NSInst {
 // device counter); results are written back into the records.
 __global__ void k_netsimplex(NSInst* insts, const int32_t* __restrict__ order, int32_t count,
                              int32_t* __restrict__ next);
-// Dynamic shared memory of N1 nodes in shared-memory layout 1 or 2.
+// Dynamic shared memory of N1 nodes in shared-memory layout 1, 2 or 3.
 size_t ns_smem_bytes(int64_t N1, int layout);
 // Raises the kernel's dynamic shared memory limit on the current device once,
 // to the most any instance can use (thread-safe; never lowers it).
 cudaError_t ns_kernel_setup();
 // The layout N1 nodes get beside the kernel's static shared memory
 // (max_optin: the device's opt-in limit per CTA): 1 all node arrays in shared
-// memory, 2 all but pred and the packed flow, 0 none (global memory).
+// memory, 2 all but pred and the packed flow, 3 only the four 16-bit arrays,
+// 0 none (global memory).
 int ns_smem_layout(int64_t N1, int max_optin);
 __global__ void k_i64_to_i32_cost(const int64_t* __restrict__ c, int64_t m, int32_t* __restrict__ o,
                                   unsigned long long* __restrict__ bad);
