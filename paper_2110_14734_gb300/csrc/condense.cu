@@ -504,7 +504,6 @@ static pd_status rwmd_grid(Ctx* c, const Hats& h, DiagCost dc, unsigned long lon
     int hn[2];
     PD_TRY_CUDA(c, cudaMemcpyAsync(hn, nl, sizeof(hn), cudaMemcpyDeviceToHost, st));
     PD_TRY_CUDA(c, cudaStreamSynchronize(st));
-    c->last_rw_unfinished = (int64_t)hn[0] + hn[1];
     if (hn[0] + hn[1] > 0) {
         const int64_t gx = (std::max(hn[0], hn[1]) + RW_THREADS - 1) / RW_THREADS;
         k_rwmd_min_list<<<dim3((unsigned)gx, (unsigned)gy, 2), RW_THREADS, 0, st>>>(h.X, h.Y, h.nA, h.nB, list, hn[0],

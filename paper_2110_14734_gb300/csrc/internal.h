@@ -85,7 +85,6 @@ struct Ctx {
     Ctx* coarse = nullptr;            // helper context of the coarse solve (warm_start 4)
     int64_t last_coarse_pivots = 0;   // pivots of the last coarse solve
     int64_t last_coarse_cell = 0;     // its lattice cell (quanta; 0: no coarse solve)
-    int64_t last_rw_unfinished = 0;   // RWMD grid queries finished by the all-pairs scan
     // the batch's wave as a CUDA graph (ns_run_wave): pinned staging, the
     // captured executable and what it was captured with
     void* wave_pin = nullptr;
